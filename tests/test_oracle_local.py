@@ -1,0 +1,133 @@
+"""Pins of the oracle's per-particle operators and of the assembled right-hand side
+of Eq. 4-5: the Vreman eddy viscosity (hand-computed cases), the stretching term,
+particle strength exchange against the closed-form Gaussian-smoothed Laplacian of
+a plane wave, and conservation of total vorticity by the transposed scheme."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "vreman_cases.txt")
+
+
+def _vreman_cases():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        f = line.split()
+        rows.append((f[0], float(f[1]), float(f[2]), np.array([float(v) for v in f[3:12]]).reshape(3, 3),
+                     float(f[12])))
+    return rows
+
+
+@pytest.mark.parametrize("case", _vreman_cases(), ids=lambda c: c[0])
+def test_vreman_hand_cases(case):
+    name, delta, cv, J, ref = case
+    nu = oracle.vreman(J[None], delta, cv)[0]
+    assert nu == pytest.approx(ref, rel=1e-14, abs=1e-18)
+
+
+def test_vreman_zero_gradient_and_scale():
+    assert oracle.vreman(np.zeros((1, 3, 3)), 0.1)[0] == 0.0
+    rng = np.random.default_rng(0)
+    J = rng.normal(size=(8, 3, 3))
+    a = oracle.vreman(J, 0.1)
+    b = oracle.vreman(3.0 * J, 0.1)  # nu_t is homogeneous of degree one in the gradient
+    np.testing.assert_allclose(b, 3.0 * a, rtol=1e-13)
+
+
+def test_stretching_forms():
+    J = np.array([[0.0, 2.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])  # du0/dx1 = 2
+    G = np.array([[0.0, 1.0, 0.0, 0.0]])
+    # classic (Gamma . grad) u = J Gamma = (2, 0, 0); transposed J^T Gamma = (0, 0, 0)
+    np.testing.assert_array_equal(oracle.stretch(J[None], G, classic=True)[0], [2.0, 0, 0])
+    np.testing.assert_array_equal(oracle.stretch(J[None], G, classic=False)[0], [0.0, 0, 0])
+    G2 = np.array([[1.0, 0.0, 0.0, 0.0]])
+    np.testing.assert_array_equal(oracle.stretch(J[None], G2, classic=False)[0], [0.0, 2.0, 0])
+
+
+def _lattice(h, half):
+    k = np.arange(-half, half + 1) * h
+    X, Y, Z = np.meshgrid(k, k, k, indexing="ij")
+    return np.c_[X.ravel(), Y.ravel(), Z.ravel()]
+
+
+def test_pse_equals_gaussian_smoothed_laplacian_of_plane_wave():
+    """For omega = cos(k x) z on a fine lattice, the exchange sum equals its continuum
+    limit (2/sigma^2)(exp(-k^2 sigma^2/2) - 1) v omega at the centre particle; that
+    limit tends to the Laplacian -k^2 omega as k sigma -> 0."""
+    sigma, h, half = 0.1, 0.05, 10
+    P = _lattice(h, half)
+    v = h ** 3
+    k = 3.0
+    om = np.cos(k * P[:, 0])
+    G = np.c_[np.zeros_like(om), np.zeros_like(om), v * om]
+    nu = 2e-3
+    p = oracle.pse(np.c_[P, np.full(len(P), v)], np.c_[G, np.zeros(len(P))], None, sigma, nu)
+    c = len(P) // 2
+    assert np.allclose(P[c], 0)
+    ref = nu * v * (2 / sigma ** 2) * (np.exp(-0.5 * (k * sigma) ** 2) - 1.0)
+    assert p[c, 2] == pytest.approx(ref, rel=2e-4)
+    assert p[c, 2] == pytest.approx(-nu * v * k ** 2, rel=0.03)
+    # eddy viscosity enters as nu + (nu_t,i + nu_t,j)/2
+    p2 = oracle.pse(np.c_[P, np.full(len(P), v)], np.c_[G, np.zeros(len(P))], np.full(len(P), 4e-3), sigma, nu)
+    assert p2[c, 2] == pytest.approx(p[c, 2] * (nu + 4e-3) / nu, rel=1e-12)
+
+
+def test_pse_uniform_field_is_stationary():
+    rng = np.random.default_rng(1)
+    P = rng.uniform(-0.2, 0.2, size=(200, 3))
+    v = 1e-4
+    G = np.tile([0.3 * v, -0.1 * v, 0.2 * v], (200, 1))
+    p = oracle.pse(np.c_[P, np.full(200, v)], np.c_[G, np.zeros(200)], rng.uniform(0, 1e-3, 200), 0.05, 1e-3)
+    assert np.abs(p).max() < 1e-14 * v
+
+
+@pytest.mark.parametrize("with_segments", [False, True])
+def test_total_vorticity_conserved_by_transposed_scheme(with_segments):
+    """sum_i dGamma_i/dt = 0: the transposed pair term is antisymmetric in (i, j) and
+    so is particle strength exchange.  Segments are external sources, so with them
+    only the particle-particle part is required to cancel; it is checked without."""
+    rng = np.random.default_rng(2)
+    n = 300
+    P = rng.uniform(-0.3, 0.3, size=(n, 3))
+    G = rng.normal(size=(n, 3)) * 1e-3
+    pos = np.c_[P, np.full(n, 0.05 ** 3)]
+    strn = np.c_[G, np.zeros(n)]
+    sa = sb = None
+    if with_segments:
+        sa = np.array([[-0.5, 0.0, 0.4, 1.0]])
+        sb = np.array([[0.5, 0.0, 0.4, 0.0]])
+    dx, dG, nut = oracle.rhs(pos, strn, sa, sb, 0.05, nu=1e-3)
+    scale = np.abs(dG).sum()
+    if not with_segments:
+        assert np.abs(dG.sum(axis=0)).max() < 1e-13 * scale
+        dx_c, dG_c, _ = oracle.rhs(pos, strn, None, None, 0.05, nu=1e-3, classic=True)
+        assert np.abs(dG_c.sum(axis=0)).max() > 1e-4 * np.abs(dG_c).sum()  # classic form does not conserve
+    assert np.all(nut >= 0)
+
+
+def test_rhs_is_assembled_from_its_parts():
+    rng = np.random.default_rng(4)
+    n = 120
+    P = rng.uniform(-0.3, 0.3, size=(n, 3))
+    G = rng.normal(size=(n, 3)) * 1e-3
+    pos = np.c_[P, np.full(n, 0.04 ** 3)]
+    strn = np.c_[G, np.zeros(n)]
+    sa = np.array([[-0.5, 0.0, 0.1, 0.7], [0.5, 0.0, 0.1, -0.2]])
+    sb = np.array([[0.5, 0.0, 0.1, 0.0], [0.5, 0.3, 0.1, 0.0]])
+    uinf = (1.0, -2.0, 0.5)
+    dx, dG, nut = oracle.rhs(pos, strn, sa, sb, 0.04, nu=1e-3, c_v=0.07, seg_core=0.02, u_inf=uinf)
+    u, J = oracle.p2p(pos, strn, pos, 0.04)
+    us, Js = oracle.segments(sa, sb, pos, 0.02, 2)
+    Jt = J + Js
+    np.testing.assert_allclose(dx, u + us + np.array(uinf), rtol=1e-14, atol=1e-15)
+    nu_ref = oracle.vreman(Jt, 0.04, 0.07)
+    np.testing.assert_allclose(nut, nu_ref, rtol=1e-13)
+    s = oracle.stretch(Jt, strn)
+    p = oracle.pse(pos, strn, nu_ref, 0.04, 1e-3)
+    np.testing.assert_allclose(dG, s + p, rtol=1e-13, atol=1e-16)
