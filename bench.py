@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Throughput of the vortex-particle hot path on GB300.
+
+One step = one pass of the whole hot path over the 4-blade hover wake
+(100,000 particles, 5,120 blade segments, 1,280 control points, sigma = 0.01 R):
+  pack the FP64 state to FP32, induced velocity at the control points, AIC build
+  and FP32-LU/FP64-refined solve, one low-storage RK3 step (three right-hand
+  sides, each a particle + segment u + grad u sweep, Vreman, stretching, PSE,
+  stage update), and the adjoint of the downwash loss at the control points.
+Metric: particle-particle u + grad u pair interactions per second (3 N (N - 1) per
+step), compensated FP32.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "VPM pair interactions/s (u+∇u), compensated FP32 vs FP64 form at stated error"
+UNIT = "pair-interactions/s"
+FLOPS_P2P = 54   # u + grad u, far-field operation tree, FFMA = 2 flops
+FLOPS_SEG = 120  # Vatistas segment u + grad u, same counting convention
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--particles", type=int, default=None, help="override the particle count (testing only)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_desc(w):
+    return (f"{w.name}: {w.meta.get('blades')}-blade rotor wake, {w.n:,} Gaussian particles (sigma {w.sigma:g} R), "
+            f"{w.m:,} Vatistas blade segments, {w.n_ctrl:,} control points")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(w, seconds, cores):
+    """P2P u + grad u pair interactions/s of the FP64 oracle on a bounded sample of
+    targets against all sources (sized to take about `seconds`)."""
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    import oracle
+    from paper_2511_11430_gb300 import synth
+
+    oracle.build()
+    n = w.n
+    k = 64
+    while True:
+        idx = synth.sample_targets(7, n, k)
+        t0 = time.perf_counter()
+        oracle.p2p(w.pos, w.strength, w.pos[idx], w.sigma)
+        dt = time.perf_counter() - t0
+        if dt >= seconds * 0.5 or k >= n:
+            rate = k * (n - 1) / dt
+            return rate, k, dt
+        k = min(n, int(k * max(2.0, seconds / max(dt, 1e-3) * 0.6)))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    from paper_2511_11430_gb300 import synth
+
+    w = synth.make(args.config) if args.particles is None else synth.make(args.config, n=args.particles)
+    cores = host_cores()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, k, dt = oracle_rate(w, per_step, cores)
+        if i >= args.warmup:
+            rates.append((r, k, dt))
+    value = float(np.mean([r for r, _, _ in rates]))
+    k = rates[-1][1]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean([d for _, _, d in rates]) * 1e3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "reference": "FP64 CPU oracle (plain direct sum) on host cores",
+                   "sample": f"{k} targets x {w.n - 1:,} sources per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{k} sampled targets x all {w.n:,} sources, P2P u + grad u in FP64"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2511_11430_gb300 import _lib, api, build, synth
+
+    ws_n, rank, local = dist_info()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if ws_n > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    w = synth.make(args.config) if args.particles is None else synth.make(args.config, n=args.particles)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    n, m, K = w.n, w.m, w.n_ctrl
+    x0 = np.ascontiguousarray(w.pos[:, :3].astype(np.float64).T)
+    G0 = np.ascontiguousarray(w.strength[:, :3].astype(np.float64).T)
+    vol = T(w.pos[:, 3].copy())
+    sa, sb = T(w.seg_a), T(w.seg_b)
+    rings, colloc, normal, vrel = T(w.rings), T(w.colloc), T(w.normal), T(w.v_rel)
+    nrm = normal[:, :3].t().contiguous()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def make_state():
+        return T(x0), T(G0)
+
+    def hot_path_step(state, prm, wsb):
+        x, G = state
+        pos, strn = api.pack_state(x, G, vol, wsb["pos"], wsb["str"])
+        u_c = api.induce(pos, strn, colloc, w.sigma, compensated=prm.compensated, grad=False, ws=wsb["ws"])
+        A, b = api.aic_build(rings, colloc, normal, w.seg_core, 2, v_rel=vrel, w_ind=u_c)
+        gam, it, be = api.aic_solve(A, b, tol=1e-12, max_iter=30, ws=wsb["ws"])
+        api.step(x, G, vol, sa, sb, prm, w.dt, ws=wsb["ws"])
+        g = 2.0 * (u_c * nrm).sum(0, keepdim=True) * nrm  # d/du of sum_k (u_k . n_k)^2
+        dx, dG = api.induce_backward(pos, strn, colloc, w.sigma, g.contiguous(), compensated=prm.compensated,
+                                     ws=wsb["ws"])
+        return gam, dx, dG
+
+    def new_bufs():
+        return {"ws": api.Workspace(dev), "pos": torch.empty((n, 4), dtype=torch.float32, device=dev),
+                "str": torch.empty((n, 4), dtype=torch.float32, device=dev)}
+
+    def timed(prm, steps, warmup, trace=False):
+        state = make_state()
+        bufs = new_bufs()
+        for _ in range(warmup):
+            hot_path_step(state, prm, bufs)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        if trace:
+            api.trace_enable(True)
+            api.trace_reset()
+        st = torch.cuda.current_stream()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            hot_path_step(state, prm, bufs)
+            e1.record(st)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        tr = None
+        if trace:
+            tr = {k: api.trace_read(k) for k in (_lib.VPM_TRACE_ALL, _lib.VPM_TRACE_SWEEP, _lib.VPM_TRACE_ADJOINT,
+                                                 _lib.VPM_TRACE_PSE, _lib.VPM_TRACE_SWEEP_VEL)}
+            api.trace_enable(False)
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), tr
+
+    prm_c = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=True)
+    prm_p = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=False)
+    pairs_step = 3 * n * (n - 1)
+    seg_pairs_step = 3 * n * m
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    total_ms, tr = timed(prm_c, args.steps, args.warmup, trace=True)
+    clk = clocks.stop() if clocks else None
+    ms_step = total_ms / args.steps
+    value = ws_n * pairs_step * args.steps / (total_ms * 1e-3)
+
+    plain = None
+    if not args.no_plain:
+        pm, _ = timed(prm_p, max(3, args.steps // 2), 1)
+        plain = {"value": ws_n * pairs_step * max(3, args.steps // 2) / (pm * 1e-3), "unit": UNIT,
+                 "ms_per_step": pm / max(3, args.steps // 2), "dtype": "f32 (plain accumulation)"}
+
+    # roofline of the dominant kernel: the particle + segment u + grad u sweep
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = 2070.0
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x FFMA x max SM clock, TFLOP/s
+    nl, sms_ms = tr[_lib.VPM_TRACE_SWEEP]
+    avg_ms = sms_ms / max(nl, 1)
+    flops_launch = FLOPS_P2P * n * (n - 1) + FLOPS_SEG * n * m
+    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "sweep_kernel<grad, compensated>", "launches": nl,
+            "avg_launch_ms": avg_ms, "flops_per_launch": flops_launch,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {sm_max:.0f} MHz (fallback-free derivation)"}
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x0).pin_memory()
+        Gh = torch.from_numpy(G0).pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        Go = torch.empty_like(Gh).pin_memory()
+        gho = torch.empty((K,), dtype=torch.float64).pin_memory()
+        dxo = torch.empty((3, n), dtype=torch.float32).pin_memory()
+        dGo = torch.empty((3, n), dtype=torch.float32).pin_memory()
+        volh = torch.from_numpy(w.pos[:, 3].copy()).pin_memory()
+        host_in = [torch.from_numpy(a).pin_memory() for a in (w.seg_a, w.seg_b, w.rings, w.colloc, w.normal,
+                                                              w.v_rel)]
+        bufs = new_bufs()
+        x_d, G_d = torch.empty_like(xh, device=dev), torch.empty_like(Gh, device=dev)
+        dev_in = [torch.empty_like(h, device=dev) for h in host_in]
+        vol_d = torch.empty_like(volh, device=dev)
+
+        def e2e_step():
+            x_d.copy_(xh, non_blocking=True)
+            G_d.copy_(Gh, non_blocking=True)
+            vol_d.copy_(volh, non_blocking=True)
+            for d_, h_ in zip(dev_in, host_in):
+                d_.copy_(h_, non_blocking=True)
+            gam, dx, dG = hot_path_step((x_d, G_d), prm_c, bufs)
+            xo.copy_(x_d, non_blocking=True)
+            Go.copy_(G_d, non_blocking=True)
+            gho.copy_(gam, non_blocking=True)
+            dxo.copy_(dx, non_blocking=True)
+            dGo.copy_(dG, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(2, args.steps // 2)
+        e0.record(st)
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(st)
+        e1.synchronize()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        h2d = (xh.numel() + Gh.numel()) * 8 + volh.numel() * 4 + sum(h.numel() * 4 for h in host_in)
+        d2h = (xo.numel() + Go.numel() + gho.numel()) * 8 + (dxo.numel() + dGo.numel()) * 4
+        e2e = {"value": ws_n * pairs_step * ksteps / (float(t.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": float(t.item()) / ksteps}
+
+    # error at the stated tolerance, on a sample (outside every timed region)
+    err = None
+    if rank == 0:
+        try:
+            import oracle
+
+            idx = synth.sample_targets(11, n, 96)
+            pos, strn = api.pack_state(*make_state(), vol)
+            u, gr = api.induce(pos, strn, pos, w.sigma, compensated=True)
+            up, gp = api.induce(pos, strn, pos, w.sigma, compensated=False)
+            ru, rJ = oracle.p2p(w.pos, w.strength, w.pos[idx], w.sigma)
+            rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            U = lambda t: t[:, idx].double().cpu().numpy().T
+            Jm = lambda t: t[:, idx].double().cpu().numpy().T.reshape(-1, 3, 3)
+            err = {"sample_targets": len(idx), "compensated": {"u": rel(U(u), ru), "grad_u": rel(Jm(gr), rJ)},
+                   "plain": {"u": rel(U(up), ru), "grad_u": rel(Jm(gp), rJ)}, "tolerance": {"compensated": 2e-6,
+                                                                                              "plain": 1e-4}}
+        except Exception as ex:  # the error report is informative, never fatal
+            err = {"unavailable": str(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        rate, k, dt = oracle_rate(w, args.cpu_seconds, cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{k} sampled targets x all {n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)"}
+
+    if dist is not None:
+        dist.barrier()
+    if rank == 0:
+        launches_total = tr[_lib.VPM_TRACE_ALL][0]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(w), "particles": n, "segments": m, "control_points": K,
+                       "pairs_per_step": pairs_step, "segment_pairs_per_step": seg_pairs_step,
+                       "precision": "compensated FP32 pair sums, FP64 state/refinement",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                       "parallelism": "replicas" if ws_n > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_total),
+            "clocks": clk, "plain": plain, "error": err,
+            "kernel_ms": {"sweep_grad": [nl, sms_ms], "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
+                          "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL])},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

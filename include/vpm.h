@@ -1,0 +1,213 @@
+/*
+ * vpm.h -- C ABI of the GB300 (sm_103a) vortex-particle hot path of the
+ * NL-UVLM-VPM rotor-wake method (Fu & Laurendeau, arXiv 2511.11430).
+ *
+ * The library evaluates the Gaussian-regularised Biot-Savart velocity u and
+ * velocity gradient grad u on vortex particles (Sec. II.B, Eq. 2-4) from all
+ * other particles and from Vatistas-cored straight vortex segments (Sec. II.A),
+ * the vortex-particle right-hand side of Eq. 4-5 (stretching, PSE diffusion with
+ * the Vreman eddy viscosity), one low-storage third-order Runge-Kutta step, the
+ * blade influence-coefficient (AIC) system with FP32 LU and FP64 iterative
+ * refinement, and the adjoint of the particle-to-point velocity.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named *_d are DEVICE pointers on the current CUDA device; the
+ *    caller owns every buffer.  The library allocates nothing and frees nothing;
+ *    scratch memory is the caller's `ws` of at least vpm_workspace_size() bytes.
+ *  - float4-packed arrays are `const float*` with 4 floats per item, 16-byte
+ *    aligned:  particles  pos[n][4] = (x, y, z, volume)   str[n][4] = (Gx, Gy, Gz, -)
+ *              targets    tgt[n][4] = (x, y, z, -)
+ *              segments   seg_a[m][4] = (ax, ay, az, circulation)   seg_b[m][4] = (bx, by, bz, -)
+ *    The 4th lane marked "-" is ignored.
+ *  - Outputs are planar: u[3][n] (u[a*n + i]), grad_u[9][n] with
+ *    grad_u[(3*a+b)*n + i] = d u_a / d x_b at target i.
+ *  - SI units as in the paper: lengths in m, particle strength Gamma in m^3/s,
+ *    segment circulation in m^2/s.
+ *  - A pair at zero distance contributes nothing, so a particle never induces
+ *    velocity on itself when the targets are the particles.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Entry points are asynchronous on that stream unless stated otherwise.
+ *  - Return codes report argument errors (nothing is launched) and launch
+ *    errors.  Faults found by kernels (a bounded wait that timed out, a
+ *    non-finite output when VPM_CHECK_FINITE is set) are latched in a device
+ *    word read by vpm_device_error().
+ *  - Calls on different streams must not share a workspace.
+ */
+#ifndef VPM_H
+#define VPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vpm_status {
+    VPM_OK = 0,
+    VPM_ERR_INVALID_ARG = -1,   /* bad size, NULL or misaligned pointer, sigma <= 0 ... */
+    VPM_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+    VPM_ERR_NONFINITE = -3,     /* a kernel saw a non-finite value (device word) */
+    VPM_ERR_NOT_CONVERGED = -4, /* aic_solve: backward error above tol after max_iter */
+    VPM_ERR_WORKSPACE = -5,     /* ws NULL or smaller than vpm_workspace_size() */
+    VPM_ERR_LIMIT = -6          /* a size above the library's limits */
+} vpm_status;
+
+/* flags (bitwise or) */
+#define VPM_COMPENSATED 0x1     /* compensated FP32 accumulation (two-sum per source tile) */
+#define VPM_STRETCH_CLASSIC 0x2 /* stretching (Gamma . grad) u = J Gamma (Eq. 1) instead of
+                                   the transposed (Gamma . grad^T) u = J^T Gamma of Eq. 5 */
+#define VPM_CHECK_FINITE 0x4    /* scan outputs for NaN/Inf and latch VPM_ERR_NONFINITE */
+
+/* operation codes for vpm_workspace_size */
+#define VPM_OP_INDUCE 1
+#define VPM_OP_SEGMENTS 2
+#define VPM_OP_RHS 3
+#define VPM_OP_STEP 4
+#define VPM_OP_AIC_SOLVE 5
+#define VPM_OP_BACKWARD 6
+
+/* Largest particle / target / segment count accepted (int32 indexing). */
+#define VPM_MAX_ITEMS (1 << 30)
+/* Largest AIC order accepted by aic_solve. */
+#define VPM_MAX_AIC 8192
+
+/* Parameters of the vortex-particle right-hand side (Sec. II.B). */
+typedef struct vpm_params {
+    float sigma;      /* particle core size sigma of Eq. 3 [m], > 0 */
+    float nu;         /* kinematic viscosity [m^2/s], >= 0 */
+    float c_v;        /* Vreman coefficient (the paper uses 0.07), >= 0 */
+    float seg_core;   /* Vatistas core radius of the segments [m], >= 0 */
+    float u_inf[3];   /* free-stream velocity added to dx/dt [m/s] */
+    int vatistas_n;   /* Vatistas exponent n, 1 or 2 */
+    int flags;        /* VPM_COMPENSATED | VPM_STRETCH_CLASSIC | VPM_CHECK_FINITE */
+} vpm_params;
+
+/* Message of the last error returned on the calling host thread ("" if none). */
+const char* vpm_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int vpm_version(void);
+
+/* Reads and clears the device error word of the current device (synchronises the
+ * device).  *code receives 0, VPM_ERR_NONFINITE, or VPM_ERR_LIMIT (a bounded wait
+ * inside a kernel timed out).  Returns VPM_ERR_CUDA if the read itself fails. */
+vpm_status vpm_device_error(int* code);
+
+/* Bytes of scratch an operation needs on the current device.
+ *   VPM_OP_INDUCE:    n_src particles -> n_tgt targets            (m_seg ignored)
+ *   VPM_OP_SEGMENTS:  m_seg segments -> n_tgt targets             (n_src ignored)
+ *   VPM_OP_RHS, VPM_OP_STEP: n_src particles, m_seg segments       (n_tgt ignored)
+ *   VPM_OP_AIC_SOLVE: order n_tgt                                  (others ignored)
+ *   VPM_OP_BACKWARD:  n_src particles, n_tgt targets
+ * `flags` as passed to the operation.  Host-only; does not launch. */
+vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_seg, int flags, size_t* bytes);
+
+/* ---- Eq. 2-4: Gaussian-particle velocity and velocity gradient -----------
+ * u(x) = sum_j K(r) Gamma_j x r,  r = x - x_j,  K = g(|r|/sigma) / (4 pi |r|^3),
+ * g(rho) = erf(rho/sqrt2) - sqrt(2/pi) rho exp(-rho^2/2) the vorticity fraction of
+ * a Gaussian blob (Eq. 3) inside radius rho*sigma; grad_u is its exact gradient.
+ *   src_pos_d, src_str_d  [n_src][4]   sources (volume lane unused here)
+ *   tgt_d                 [n_tgt][4]   evaluation points (may alias src_pos_d)
+ *   u_d                   [3][n_tgt]   output velocity
+ *   grad_u_d              [9][n_tgt]   output gradient, or NULL for velocity only
+ *   flags: VPM_COMPENSATED, VPM_CHECK_FINITE.
+ * n_src == 0 writes zeros; n_tgt == 0 does nothing. */
+vpm_status vpm_induce(const float* src_pos_d, const float* src_str_d, int64_t n_src, const float* tgt_d,
+                      int64_t n_tgt, float sigma, int flags, float* u_d, float* grad_u_d, void* ws_d,
+                      size_t ws_bytes, void* stream);
+
+/* ---- Sec. II.A: straight vortex segments with a Vatistas core ------------
+ * The finite-segment Biot-Savart law with |r1 x r2|^2 replaced by
+ * (|r1 x r2|^(2n) + (core |b - a|)^(2n))^(1/n), n = vatistas_n in {1, 2}, and its
+ * exact gradient.  Points within 1e-10 |b-a| (or 1e-15 m) of an end point, and
+ * points on the line when core == 0, receive nothing from that segment.
+ *   seg_a_d, seg_b_d [m][4] (circulation in seg_a's 4th lane); tgt_d [n_tgt][4];
+ *   u_d [3][n_tgt]; grad_u_d [9][n_tgt] or NULL.  flags: VPM_COMPENSATED. */
+vpm_status vpm_segments_induce(const float* seg_a_d, const float* seg_b_d, int64_t m, const float* tgt_d,
+                               int64_t n_tgt, float core, int vatistas_n, int flags, float* u_d, float* grad_u_d,
+                               void* ws_d, size_t ws_bytes, void* stream);
+
+/* ---- Eq. 4-5: vortex-particle right-hand side -----------------------------
+ * For every particle i (targets = sources = the n particles):
+ *   u_i, J_i   from all other particles (Eq. 2-4) plus the m segments
+ *   nu_t,i     Vreman (2004): c_V sqrt(B_beta / alpha:alpha), alpha = J^T,
+ *              beta = sigma^2 J J^T (filter width = sigma)
+ *   dx/dt      = u_i + u_inf
+ *   dGamma/dt  = J_i^T Gamma_i (or J_i Gamma_i with VPM_STRETCH_CLASSIC)
+ *              + (2/sigma^2) sum_j nu_ij (v_i Gamma_j - v_j Gamma_i) zeta_sigma(r_ij)
+ *                with nu_ij = nu + (nu_t,i + nu_t,j)/2 (particle strength exchange,
+ *                pairs beyond 7 sigma skipped: zeta there is below 3e-11 of its peak)
+ *   pos_d, str_d [n][4] (volume v_i in pos's 4th lane); seg_a_d/seg_b_d may be NULL if m == 0.
+ *   dxdt_d, dGdt_d [3][n]; nu_t_d [n] or NULL. */
+vpm_status vpm_rhs(const float* pos_d, const float* str_d, int64_t n, const float* seg_a_d, const float* seg_b_d,
+                   int64_t m, const vpm_params* prm, float* dxdt_d, float* dGdt_d, float* nu_t_d, void* ws_d,
+                   size_t ws_bytes, void* stream);
+
+/* ---- FP64 master state -> FP32 packed particles (the RK state of Sec. II.B) ---
+ *   x_d, G_d [3][n] double; vol_d [n] float  ->  pos_d [n][4] = (x, y, z, vol),
+ *   str_d [n][4] = (Gx, Gy, Gz, 0), each value rounded to nearest float. */
+vpm_status vpm_pack_state(const double* x_d, const double* G_d, const float* vol_d, int64_t n, float* pos_d,
+                          float* str_d, void* stream);
+
+/* ---- one time step: low-storage RK3 of Williamson (1980) -------------------
+ * for k = 1..3:  q <- A_k q + dt f(y);  y <- y + B_k q,
+ * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15), y = (x, Gamma) in FP64, the
+ * right-hand side f evaluated by vpm_rhs on the state rounded to FP32.  Segments
+ * stay frozen during the step.
+ *   x_d, G_d [3][n] double, updated in place; vol_d [n] float particle volumes. */
+vpm_status vpm_step(double* x_d, double* G_d, const float* vol_d, int64_t n, const float* seg_a_d,
+                    const float* seg_b_d, int64_t m, const vpm_params* prm, double dt, void* ws_d, size_t ws_bytes,
+                    void* stream);
+
+/* ---- Sec. II.A: blade influence-coefficient system -------------------------
+ * A[k][l] = u(ring l, unit circulation)(y_k) . n_k with ring l the four segments
+ * c0->c1->c2->c3->c0 of its corners (Vatistas core `core`, exponent vatistas_n),
+ * and, when b_d is not NULL, b[k] = -(v_rel[k] + w_ind[k]) . n_k (Neumann condition).
+ *   rings_d [n][4][4] corners (xyz, -); colloc_d, normal_d, v_rel_d [n][4];
+ *   w_ind_d [3][n] or NULL; A_d [n][n] float row-major; b_d [n] double or NULL. */
+vpm_status aic_build(const float* rings_d, const float* colloc_d, const float* normal_d, int n, float core,
+                     int vatistas_n, const float* v_rel_d, const float* w_ind_d, float* A_d, double* b_d,
+                     void* stream);
+
+/* Solves A x = b with A factored once in FP32 (partial pivoting) and iterative
+ * refinement whose residual r = b - A x is formed in FP64 from the FP32 matrix.
+ * Stops when the normwise backward error ||b - A x||_inf / (||A||_inf ||x||_inf +
+ * ||b||_inf) <= tol, or after max_iter corrections (then VPM_ERR_NOT_CONVERGED with
+ * the best x written).  Synchronises `stream` once per refinement step.
+ *   A_d [n][n] float row-major (not modified); b_d, x_d [n] double;
+ *   iters_out, berr_out host pointers or NULL. */
+vpm_status aic_solve(const float* A_d, const double* b_d, double* x_d, int n, double tol, int max_iter,
+                     int* iters_out, double* berr_out, void* ws_d, size_t ws_bytes, void* stream);
+
+/* ---- adjoint of the particle -> point velocity ----------------------------
+ * Given g_k = dL/du_k at the targets, returns for every source particle j
+ *   dL/dGamma_j = sum_k K(r) (r x g_k)
+ *   dL/dx_j     = sum_k [K(r) (Gamma_j x g_k) - H(r) ((Gamma_j x r) . g_k) r]
+ * with r = y_k - x_j, H = K'(r)/r.  Pair terms are recomputed, nothing stored.
+ *   grad_out_d [3][n_tgt]; dL_dx_d, dL_dG_d [3][n_src].  flags: VPM_COMPENSATED. */
+vpm_status vpm_induce_backward(const float* src_pos_d, const float* src_str_d, int64_t n_src, const float* tgt_d,
+                               int64_t n_tgt, float sigma, int flags, const float* grad_out_d, float* dL_dx_d,
+                               float* dL_dG_d, void* ws_d, size_t ws_bytes, void* stream);
+
+/* ---- launch tracing (not part of the method; for measurement) ------------
+ * Every kernel the library launches increments a host-side counter.  With
+ * vpm_trace_enable(1) the pair-sweep kernels are also bracketed by CUDA events
+ * recorded on their launch stream; vpm_trace_read synchronises on those events and
+ * returns how many launches of `kind` were timed and their summed device time.
+ * kind VPM_TRACE_ALL returns the total launch count of every kernel since the
+ * last reset (and the summed time of all timed kinds).  Thread-safe. */
+#define VPM_TRACE_ALL 0
+#define VPM_TRACE_SWEEP 1     /* forward particle + segment pair sweep with gradient */
+#define VPM_TRACE_ADJOINT 2   /* adjoint pair sweep */
+#define VPM_TRACE_PSE 3       /* particle strength exchange */
+#define VPM_TRACE_SWEEP_VEL 4 /* forward pair sweep, velocity only */
+vpm_status vpm_trace_enable(int timing);
+vpm_status vpm_trace_reset(void);
+vpm_status vpm_trace_read(int kind, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPM_H */

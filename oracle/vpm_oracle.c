@@ -167,8 +167,8 @@ void orc_p2p(const double* pos, const double* str, int64_t n_src, const double* 
 /* h^2 by (h^(2n) + rc^(2n))^(1/n), i.e. the denominator becomes               */
 /*   D = (|r1 x r2|^(2n) + (rc |r0|)^(2n))^(1/n).                              */
 /* The gradient is the analytic x-derivative of that expression.  Points      */
-/* within 1e-12 |r0| of an end point get zero, as does D == 0 (no core, on   */
-/* the line).                                                                 */
+/* within 1e-10 |r0| (or 1e-15 m) of an end point get zero, as does D == 0   */
+/* (no core, on the line).                                                    */
 /* ------------------------------------------------------------------------- */
 static void segment_uJ(const double* A, const double* B, double Gs, const double* x, double rc, int vn,
                        double* u, double* J)
@@ -182,7 +182,7 @@ static void segment_uJ(const double* A, const double* B, double Gs, const double
     for (int k = 0; k < 3; ++k) u[k] = 0.0;
     if (J)
         for (int k = 0; k < 9; ++k) J[k] = 0.0;
-    if (L == 0.0 || n1 < 1e-12 * L || n2 < 1e-12 * L) return;
+    if (L == 0.0 || n1 <= 1e-10 * L || n2 <= 1e-10 * L || n1 <= 1e-15 || n2 <= 1e-15) return;
 
     double c[3];
     cross(r1, r2, c);

@@ -1,0 +1,109 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "vpm.h"
+#include "vpm_common.cuh"
+
+namespace vpm {
+
+constexpr int TPB = 256;          // threads per sweep block (8 warps)
+constexpr int TGT_TILE = 512;     // targets per target tile: two per thread
+constexpr int SRC_TILE = 128;     // sources per particle or segment tile
+constexpr int P_F4 = 5;           // float4 per packed particle source
+constexpr int S_F4 = 6;           // float4 per packed segment source
+constexpr int T_F4 = 4;           // float4 per packed adjoint target (control point)
+constexpr float RHO_FAR = 7.0f;   // beyond 7 sigma the blob is a point vortex in FP32
+constexpr int UNIT_W_P = 10;      // stream-K cost of a particle tile
+constexpr int UNIT_W_S_GRAD = 28; // ... of a segment tile with gradient
+constexpr int UNIT_W_S_VEL = 20;  // ... of a segment tile, velocity only
+
+// Workspace carving: 256-byte aligned sub-buffers.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+int sm_count();
+int* dev_err_ptr();          // device error word of the current device
+int sweep_blocks(bool grad, bool comp);  // resident sweep blocks on the current device
+int adjoint_blocks(bool comp);
+
+struct SweepPlan {
+    int n_tgt = 0, n_src = 0, m_seg = 0;
+    int TT = 0, SP = 0, SS = 0;
+    bool grad = false, comp = false;
+    int ncomp = 0;  // logical accumulator rows (3 or 14)
+    StreamK sk{};
+    size_t off_psrc = 0, off_pbox = 0, off_ssrc = 0, off_part = 0, bytes = 0;
+};
+
+// Plans a particle + segment sweep onto `n_tgt` targets starting at offset `base`
+// of a workspace carve; fills sk and the sub-buffer offsets.
+SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv);
+
+// Launches packing, the sweep and the reduction/epilogue.
+struct EpilogueOut {
+    int mode = 0;  // 0: velocity (+gradient) outputs; 1: right-hand side
+    float* u = nullptr;
+    float* grad_u = nullptr;
+    const float* str = nullptr;  // particle strengths (rhs)
+    float sigma = 0.f, c_v = 0.f, uinf[3] = {0, 0, 0};
+    int classic = 0;
+    float* dxdt = nullptr;
+    float* dGdt = nullptr;
+    float* nu_t = nullptr;
+    int check_finite = 0;
+};
+
+cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const float* src_pos, const float* src_str,
+                      const float* seg_a, const float* seg_b, float sigma, float seg_core, int vatistas_n,
+                      const EpilogueOut& out, cudaStream_t st);
+
+// Particle strength exchange added into dGdt (uses the particle tile boxes of the plan).
+cudaError_t run_pse(const SweepPlan& p, char* ws, const float* pos, const float* str, const float* nu_t, int n,
+                    float sigma, float nu, float* dGdt, cudaStream_t st);
+
+// Time step kernels.
+cudaError_t run_cast_state(const double* x, const double* G, const float* vol, int n, float* pos, float* str,
+                           cudaStream_t st);
+cudaError_t run_rk3_stage(int k, double dt, double* x, double* G, double* qx, double* qG, const float* dxdt,
+                          const float* dGdt, const float* vol, int n, float* pos, float* str, cudaStream_t st);
+
+// Adjoint sweep.
+size_t backward_workspace(int64_t n_src, int64_t n_tgt, bool comp);
+cudaError_t run_backward(char* ws, size_t ws_bytes, const float* src_pos, const float* src_str, int n_src,
+                         const float* tgt, int n_tgt, float sigma, bool comp, const float* g, float* dx, float* dG,
+                         cudaStream_t st);
+
+// AIC build and solve.
+cudaError_t run_aic_build(const float* rings, const float* colloc, const float* normal, int n, float core, int vn,
+                          const float* v_rel, const float* w_ind, float* A, double* b, cudaStream_t st);
+size_t aic_workspace(int n);
+vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, double tol, int max_iter, int* iters,
+                         double* berr, char* ws, cudaStream_t st, const char** msg);
+
+// Launch tracing (vpm_trace_*): count launches; time the bracketed kernels.
+constexpr int TRACE_KINDS = 5;
+void trace_launch(int count = 1);
+class TraceScope {
+  public:
+    TraceScope(int kind, cudaStream_t st);
+    ~TraceScope();
+
+  private:
+    int kind_;
+    cudaStream_t st_;
+    void* a_ = nullptr;
+    void* b_ = nullptr;
+};
+
+}  // namespace vpm

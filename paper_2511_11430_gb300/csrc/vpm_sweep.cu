@@ -1,0 +1,823 @@
+// Pair sweeps of the vortex-particle hot path on sm_103a.
+//
+//  * Gaussian-particle velocity and gradient (Eq. 2-4): u = sum_j K (Gamma_j x r),
+//    J = [S x]/(4 pi) + sum_j H (Gamma_j x r) (x) r with S = sum_j K Gamma_j.
+//  * Vatistas-cored straight segments (Sec. II.A), their velocity and exact gradient.
+//  * The stream-K reduction of per-block partial sums and the per-target epilogue:
+//    the velocity/gradient outputs, or the right-hand side of Eq. 4-5 (Vreman eddy
+//    viscosity, stretching) computed in FP64 from the reduced sums.
+//  * Particle strength exchange (the nu lap(Gamma) term of Eq. 5).
+//
+// Kernel organisation.  A thread owns two targets, kept in the two lanes of packed
+// float2 registers so that each FFMA2/FADD2/FMUL2 advances two pair interactions.
+// Sources are packed once per call into 128-source tiles (duplicated into both
+// lanes, negated copies included so that every subtraction is an add) and staged
+// into shared memory by one thread with the 1-D bulk-copy engine
+// (cp.async.bulk + mbarrier, double-buffered); every lane of every warp reads the
+// same source (broadcast).  Work is split stream-K over (target tile, source
+// tile) pairs so that every SM gets the same cost however few targets there are.
+// Far from the targets of a warp (tile bounding boxes more than 7 sigma apart) the
+// blob kernel equals the point-vortex kernel to FP32 precision, so far tiles run
+// the 1/r^3 form with a single rsqrt; near tiles evaluate the regularised kernel
+// exactly per pair.
+#include <math.h>
+
+#include <mutex>
+
+#include "vpm_common.cuh"
+#include "vpm_internal.h"
+#include "vpm_kernel.cuh"
+
+namespace vpm {
+
+// ---------------------------------------------------------------------------
+// Accumulators of one thread (two targets per f2): u, S and the 8 independent
+// entries of G' = sum h (Gamma x r) (x) r (its trace vanishes pair by pair, so
+// G'_zz = -G'_xx - G'_yy).  J = ([S x] - 3 G') / (4 pi), u = u / (4 pi).
+// ---------------------------------------------------------------------------
+template <bool GRAD>
+struct Acc {
+    f2 u[3];
+    f2 S[3];
+    f2 G[8];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[i] = zero2();
+        if (GRAD) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) S[i] = zero2();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) G[i] = zero2();
+        }
+    }
+    __device__ __forceinline__ f2& at(int i) { return i < 3 ? u[i] : (i < 6 ? S[i - 3] : G[i - 6]); }
+};
+
+template <bool GRAD>
+__device__ __forceinline__ void accum_particle(Acc<GRAD>& a, f2 K, f2 h, f2 rx, f2 ry, f2 rz, f2 gx, f2 gy, f2 gz,
+                                               f2 ngx, f2 ngy, f2 ngz)
+{
+    const f2 cx = fma2(gy, rz, mul2(ngz, ry));
+    const f2 cy = fma2(gz, rx, mul2(ngx, rz));
+    const f2 cz = fma2(gx, ry, mul2(ngy, rx));
+    a.u[0] = fma2(K, cx, a.u[0]);
+    a.u[1] = fma2(K, cy, a.u[1]);
+    a.u[2] = fma2(K, cz, a.u[2]);
+    if (GRAD) {
+        a.S[0] = fma2(K, gx, a.S[0]);
+        a.S[1] = fma2(K, gy, a.S[1]);
+        a.S[2] = fma2(K, gz, a.S[2]);
+        const f2 hx = mul2(h, cx), hy = mul2(h, cy), hz = mul2(h, cz);
+        a.G[0] = fma2(hx, rx, a.G[0]);
+        a.G[1] = fma2(hx, ry, a.G[1]);
+        a.G[2] = fma2(hx, rz, a.G[2]);
+        a.G[3] = fma2(hy, rx, a.G[3]);
+        a.G[4] = fma2(hy, ry, a.G[4]);
+        a.G[5] = fma2(hy, rz, a.G[5]);
+        a.G[6] = fma2(hz, rx, a.G[6]);
+        a.G[7] = fma2(hz, ry, a.G[7]);
+    }
+}
+
+// Packed particle source (5 float4, both lanes equal):
+//   (-x,-x,-y,-y) (-z,-z,gx,gx) (gy,gy,gz,gz) (-gx,-gx,-gy,-gy) (-gz,-gz,0,0)
+template <bool GRAD, bool NEAR>
+__device__ __forceinline__ void particle_tile(Acc<GRAD>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y, f2 Z,
+                                              const NearConst& nc)
+{
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+        const float4* e = s + j * P_F4;
+        const float4 q0 = e[0], q1 = e[1], q2 = e[2], q3 = e[3], q4 = e[4];
+        const f2 rx = add2(X, make_float2(q0.x, q0.y));
+        const f2 ry = add2(Y, make_float2(q0.z, q0.w));
+        const f2 rz = add2(Z, make_float2(q1.x, q1.y));
+        const f2 r2 = fma2(rz, rz, fma2(ry, ry, mul2(rx, rx)));
+        f2 K, h;
+        if (NEAR) {
+            near_kh(r2.x, nc, K.x, h.x);
+            near_kh(r2.y, nc, K.y, h.y);
+        } else {
+            const f2 rs = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const f2 i2 = mul2(rs, rs);
+            K = mul2(i2, rs);
+            h = GRAD ? mul2(K, i2) : K;
+        }
+        accum_particle<GRAD>(a, K, h, rx, ry, rz, make_float2(q1.z, q1.w), make_float2(q2.x, q2.y),
+                             make_float2(q2.z, q2.w), make_float2(q3.x, q3.y), make_float2(q3.z, q3.w),
+                             make_float2(q4.x, q4.y));
+    }
+}
+
+// Inverse lengths of one segment pair for one lane, with the end-point and axis
+// guards: a target within 1e-10 |r0| (or 1e-15 m) of an end point, or with
+// D == 0, gets zero.
+__device__ __forceinline__ void seg_lane(float n1, float n2, float c2, float L2, float e, int vn, float& i1,
+                                         float& i2, float& invD)
+{
+    const float thr = fmaxf(1e-20f * L2, 1e-30f);  // (1e-10 |r0|)^2, (1e-15 m)^2
+    const bool ok = (n1 > thr) && (n2 > thr);
+    float D;
+    if (vn == 2) {
+        const float Dsq = fmaf(c2, c2, e);
+        invD = Dsq > 0.f ? rsqrt_approx(Dsq) : 0.f;
+        D = Dsq;
+    } else {
+        D = c2 + e;
+        invD = D > 0.f ? __frcp_rn(D) : 0.f;
+    }
+    i1 = ok ? rsqrt_approx(n1) : 0.f;
+    i2 = ok ? rsqrt_approx(n2) : 0.f;
+    if (!ok || !(D > 0.f)) invD = 0.f;
+}
+
+// Packed segment source (6 float4, both lanes equal):
+//   (-ax,-ax,-ay,-ay) (-az,-az,r0x,r0x) (r0y,r0y,r0z,r0z) (-r0x,-r0x,-r0y,-r0y) (-r0z,-r0z,-L2,-L2) (G,G,e,e)
+// with r0 = b - a, L2 = |r0|^2, e = (core |r0|)^(2n).  Velocity
+//   u = G/(4 pi) c d / D,  c = r0 x r1,  d = r0.(r1/|r1| - r2/|r2|),
+//   D = (|c|^(2n) + e)^(1/n);
+// gradient J = G/(4 pi D) ( d [r0 x] + c (x) w ),  w = grad d - d grad D / D,
+//   grad d = r0 (1/|r1| - 1/|r2|) - (r0.r1) r1/|r1|^3 + (r0.r2) r2/|r2|^3,
+//   grad D / D = 2 |c|^(2n-2) D^(-n) (c x r0).
+template <bool GRAD>
+__device__ __forceinline__ void segment_tile(Acc<GRAD>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y, f2 Z,
+                                             int vn)
+{
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+        const float4* e4 = s + j * S_F4;
+        const float4 s0 = e4[0], s1 = e4[1], s2 = e4[2], s3 = e4[3], s4 = e4[4], s5 = e4[5];
+        const f2 r0x = make_float2(s1.z, s1.w), r0y = make_float2(s2.x, s2.y), r0z = make_float2(s2.z, s2.w);
+        const f2 nr0x = make_float2(s3.x, s3.y), nr0y = make_float2(s3.z, s3.w), nr0z = make_float2(s4.x, s4.y);
+        const f2 nL2 = make_float2(s4.z, s4.w), gs = make_float2(s5.x, s5.y);
+        const f2 r1x = add2(X, make_float2(s0.x, s0.y));
+        const f2 r1y = add2(Y, make_float2(s0.z, s0.w));
+        const f2 r1z = add2(Z, make_float2(s1.x, s1.y));
+        const f2 r2x = add2(r1x, nr0x), r2y = add2(r1y, nr0y), r2z = add2(r1z, nr0z);
+        const f2 cx = fma2(r0y, r1z, mul2(nr0z, r1y));
+        const f2 cy = fma2(r0z, r1x, mul2(nr0x, r1z));
+        const f2 cz = fma2(r0x, r1y, mul2(nr0y, r1x));
+        const f2 n1 = fma2(r1z, r1z, fma2(r1y, r1y, mul2(r1x, r1x)));
+        const f2 n2 = fma2(r2z, r2z, fma2(r2y, r2y, mul2(r2x, r2x)));
+        const f2 p1 = fma2(r0z, r1z, fma2(r0y, r1y, mul2(r0x, r1x)));
+        const f2 c2 = fma2(cz, cz, fma2(cy, cy, mul2(cx, cx)));
+        f2 i1, i2, invD;
+        seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, invD.x);
+        seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, invD.y);
+        const f2 p2 = add2(p1, nL2);  // r0 . r2
+        const f2 ni2 = mul2(i2, splat(-1.f));
+        const f2 d = fma2(p1, i1, mul2(p2, ni2));
+        const f2 gi = mul2(gs, invD);
+        const f2 coef = mul2(gi, d);
+        a.u[0] = fma2(coef, cx, a.u[0]);
+        a.u[1] = fma2(coef, cy, a.u[1]);
+        a.u[2] = fma2(coef, cz, a.u[2]);
+        if (GRAD) {
+            a.S[0] = fma2(coef, r0x, a.S[0]);
+            a.S[1] = fma2(coef, r0y, a.S[1]);
+            a.S[2] = fma2(coef, r0z, a.S[2]);
+            const f2 t1 = add2(i1, ni2);
+            // -(r0.r1)/|r1|^3 and (r0.r2)/|r2|^3, ordered so that no power of 1/|r| overflows
+            const f2 k1n = mul2(mul2(p1, mul2(i1, splat(-1.f))), mul2(i1, i1));
+            const f2 k2 = mul2(mul2(p2, i2), mul2(i2, i2));
+            f2 k3;
+            if (vn == 2) {
+                const f2 tmp = mul2(mul2(d, c2), mul2(invD, invD));
+                k3 = add2(tmp, tmp);
+            } else {
+                const f2 tmp = mul2(d, invD);
+                k3 = add2(tmp, tmp);
+            }
+            // r0 x c = -(c x r0)
+            const f2 crx = fma2(r0y, cz, mul2(nr0z, cy));
+            const f2 cry = fma2(r0z, cx, mul2(nr0x, cz));
+            const f2 crz = fma2(r0x, cy, mul2(nr0y, cx));
+            const f2 wx = fma2(r0x, t1, fma2(r1x, k1n, fma2(r2x, k2, mul2(crx, k3))));
+            const f2 wy = fma2(r0y, t1, fma2(r1y, k1n, fma2(r2y, k2, mul2(cry, k3))));
+            const f2 wz = fma2(r0z, t1, fma2(r1z, k1n, fma2(r2z, k2, mul2(crz, k3))));
+            const f2 cg = mul2(gi, splat(-1.0f / 3.0f));  // stored as G' with J = -3 G'
+            const f2 gx = mul2(cg, cx), gy = mul2(cg, cy), gz = mul2(cg, cz);
+            a.G[0] = fma2(gx, wx, a.G[0]);
+            a.G[1] = fma2(gx, wy, a.G[1]);
+            a.G[2] = fma2(gx, wz, a.G[2]);
+            a.G[3] = fma2(gy, wx, a.G[3]);
+            a.G[4] = fma2(gy, wy, a.G[4]);
+            a.G[5] = fma2(gy, wz, a.G[5]);
+            a.G[6] = fma2(gz, wx, a.G[6]);
+            a.G[7] = fma2(gz, wy, a.G[7]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packing kernels (one thread per source slot, 128 per block = one tile).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SRC_TILE) pack_particles_kernel(const float4* __restrict__ pos,
+                                                                  const float4* __restrict__ str, int n,
+                                                                  float4* __restrict__ out, float4* __restrict__ box)
+{
+    const int j = blockIdx.x * SRC_TILE + threadIdx.x;
+    const bool valid = j < n;
+    float x = 0.f, y = 0.f, z = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    if (valid) {
+        const float4 p = pos[j], g = str[j];
+        x = p.x, y = p.y, z = p.z;
+        gx = g.x, gy = g.y, gz = g.z;
+    }
+    float4* o = out + (size_t)j * P_F4;
+    o[0] = make_float4(-x, -x, -y, -y);
+    o[1] = make_float4(-z, -z, gx, gx);
+    o[2] = make_float4(gy, gy, gz, gz);
+    o[3] = make_float4(-gx, -gx, -gy, -gy);
+    o[4] = make_float4(-gz, -gz, 0.f, 0.f);
+    float lo[3] = {valid ? x : INFINITY, valid ? y : INFINITY, valid ? z : INFINITY};
+    float hi[3] = {valid ? x : -INFINITY, valid ? y : -INFINITY, valid ? z : -INFINITY};
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o2));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o2));
+        }
+    __shared__ float sb[SRC_TILE / 32][6];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 3; ++c) sb[w][c] = lo[c], sb[w][3 + c] = hi[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int ww = 1; ww < SRC_TILE / 32; ++ww)
+            for (int c = 0; c < 3; ++c) lo[c] = fminf(lo[c], sb[ww][c]), hi[c] = fmaxf(hi[c], sb[ww][3 + c]);
+        box[2 * blockIdx.x] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        box[2 * blockIdx.x + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* __restrict__ sa,
+                                                                 const float4* __restrict__ sb, int m, float core,
+                                                                 int vn, float4* __restrict__ out)
+{
+    const int j = blockIdx.x * SRC_TILE + threadIdx.x;
+    float ax = 0.f, ay = 0.f, az = 0.f, rx = 1.f, ry = 0.f, rz = 0.f, g = 0.f;
+    if (j < m) {
+        const float4 a = sa[j], b = sb[j];
+        ax = a.x, ay = a.y, az = a.z;
+        rx = b.x - a.x, ry = b.y - a.y, rz = b.z - a.z;
+        g = a.w;
+    }
+    const float L2 = rx * rx + ry * ry + rz * rz;
+    const float cl2 = core * core * L2;
+    const float e = vn == 2 ? cl2 * cl2 : cl2;
+    float4* o = out + (size_t)j * S_F4;
+    o[0] = make_float4(-ax, -ax, -ay, -ay);
+    o[1] = make_float4(-az, -az, rx, rx);
+    o[2] = make_float4(ry, ry, rz, rz);
+    o[3] = make_float4(-rx, -rx, -ry, -ry);
+    o[4] = make_float4(-rz, -rz, -L2, -L2);
+    o[5] = make_float4(g, g, e, e);
+}
+
+// ---------------------------------------------------------------------------
+// The stream-K sweep.
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    const float4* tgt;
+    int n_tgt;
+    const float4* psrc;
+    const float4* pbox;
+    int n_src;
+    const float4* ssrc;
+    int m_seg;
+    int vn;
+    StreamK sk;
+    NearConst nc;
+    float* part;
+    int* dev_err;
+};
+
+constexpr int BUF_F4 = SRC_TILE * S_F4;  // the larger of the two tile formats
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+template <bool GRAD, bool COMP>
+__global__ void __launch_bounds__(TPB, 1) sweep_kernel(const SweepArgs A)
+{
+    __shared__ __align__(128) float4 sbuf[2][BUF_F4];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ float wbox[TPB / 32][6];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const StreamK& sk = A.sk;
+    const int b = blockIdx.x;
+    const long long lo_b = sk.lo(b), hi_b = sk.lo(b + 1);
+    int t, k;
+    sk.first_at_or_after(lo_b, t, k);
+    if (t >= sk.TT || sk.unit_start(t, k) >= hi_b) return;  // block owns no unit (uniform)
+    const int nunits = sk.np + sk.ns;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int kk, int slot) {
+        const float4* src;
+        uint32_t bytes;
+        if (kk < sk.np) {
+            src = A.psrc + (size_t)kk * SRC_TILE * P_F4;
+            bytes = SRC_TILE * P_F4 * 16;
+        } else {
+            src = A.ssrc + (size_t)(kk - sk.np) * SRC_TILE * S_F4;
+            bytes = SRC_TILE * S_F4 * 16;
+        }
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bars[slot], bytes);
+        bulk_g2s(&sbuf[slot][0], src, bytes, &bars[slot]);
+    };
+
+    if (tid == 0) issue(k, 0);
+
+    Acc<GRAD> acc, hi, lo;
+    acc.zero();
+    if (COMP) {
+        hi.zero();
+        lo.zero();
+    }
+    f2 X = zero2(), Y = zero2(), Z = zero2();
+    int cur_t = -1;
+    uint32_t phase0 = 0, phase1 = 0;
+    bool outstanding_next = false;
+
+    for (int it = 0;; ++it) {
+        const int slot = it & 1;
+        int nt = t, nk = k + 1;
+        if (nk == nunits) {
+            nk = 0;
+            ++nt;
+        }
+        const bool has_next = nt < sk.TT && sk.unit_start(nt, nk) < hi_b;
+        if (has_next && tid == 0) issue(nk, slot ^ 1);
+        outstanding_next = has_next;
+
+        if (t != cur_t) {  // new target tile: load two targets per thread and the warp's box
+            cur_t = t;
+            const int i0 = t * TGT_TILE + warp * 64 + lane, i1 = i0 + 32;
+            float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+            const bool v0 = i0 < A.n_tgt, v1 = i1 < A.n_tgt;
+            if (v0) p0 = A.tgt[i0];
+            if (v1) p1 = A.tgt[i1];
+            X = make_float2(p0.x, p1.x);
+            Y = make_float2(p0.y, p1.y);
+            Z = make_float2(p0.z, p1.z);
+            float blo[3] = {v0 ? p0.x : INFINITY, v0 ? p0.y : INFINITY, v0 ? p0.z : INFINITY};
+            float bhi[3] = {v0 ? p0.x : -INFINITY, v0 ? p0.y : -INFINITY, v0 ? p0.z : -INFINITY};
+            if (v1) {
+                blo[0] = fminf(blo[0], p1.x), blo[1] = fminf(blo[1], p1.y), blo[2] = fminf(blo[2], p1.z);
+                bhi[0] = fmaxf(bhi[0], p1.x), bhi[1] = fmaxf(bhi[1], p1.y), bhi[2] = fmaxf(bhi[2], p1.z);
+            }
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
+                    bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
+                }
+            if (lane == 0)
+                for (int c = 0; c < 3; ++c) wbox[warp][c] = blo[c], wbox[warp][3 + c] = bhi[c];
+            __syncwarp();
+        }
+
+        const bool ok = mbar_wait_bounded(&bars[slot], slot ? phase1 : phase0, A.dev_err, WAIT_LIMIT);
+        if (slot)
+            phase1 ^= 1;
+        else
+            phase0 ^= 1;
+        if (!__syncthreads_and(ok)) break;
+
+        const float4* s = &sbuf[slot][0];
+        if (k < sk.np) {
+            const int cnt = min(SRC_TILE, A.n_src - k * SRC_TILE);
+            const float4 tlo = A.pbox[2 * k], thi = A.pbox[2 * k + 1];
+            const float dx = fmaxf(0.f, fmaxf(tlo.x - wbox[warp][3], wbox[warp][0] - thi.x));
+            const float dy = fmaxf(0.f, fmaxf(tlo.y - wbox[warp][4], wbox[warp][1] - thi.y));
+            const float dz = fmaxf(0.f, fmaxf(tlo.z - wbox[warp][5], wbox[warp][2] - thi.z));
+            const bool near = dx * dx + dy * dy + dz * dz < A.nc.far2;
+            if (near)
+                particle_tile<GRAD, true>(acc, s, cnt, X, Y, Z, A.nc);
+            else
+                particle_tile<GRAD, false>(acc, s, cnt, X, Y, Z, A.nc);
+        } else {
+            const int cnt = min(SRC_TILE, A.m_seg - (k - sk.np) * SRC_TILE);
+            segment_tile<GRAD>(acc, s, cnt, X, Y, Z, A.vn);
+        }
+        if (COMP) {
+#pragma unroll
+            for (int i = 0; i < (GRAD ? 14 : 3); ++i) fold2(hi.at(i), lo.at(i), acc.at(i));
+            acc.zero();
+        }
+        __syncthreads();  // buffer `slot` is free for the copy issued next iteration
+
+        const bool tile_end = !has_next || nt != t;
+        if (tile_end) {
+            const int nc = GRAD ? 14 : 3;
+            float* P = A.part + ((size_t)(b + t) * (COMP ? 2 * nc : nc)) * TGT_TILE + warp * 64 + lane;
+#pragma unroll
+            for (int i = 0; i < (GRAD ? 14 : 3); ++i) {
+                const f2 v = COMP ? hi.at(i) : acc.at(i);
+                P[(size_t)i * TGT_TILE] = v.x;
+                P[(size_t)i * TGT_TILE + 32] = v.y;
+                if (COMP) {
+                    const f2 w = lo.at(i);
+                    P[(size_t)(nc + i) * TGT_TILE] = w.x;
+                    P[(size_t)(nc + i) * TGT_TILE + 32] = w.y;
+                }
+            }
+            acc.zero();
+            if (COMP) {
+                hi.zero();
+                lo.zero();
+            }
+        }
+        if (!has_next) {
+            outstanding_next = false;
+            break;
+        }
+        t = nt;
+        k = nk;
+    }
+    // On a timed-out wait: give copies still in flight a bounded chance to land
+    // before the block's shared memory is released.
+    if (outstanding_next && tid == 0) {
+        mbar_wait_bounded(&bars[0], phase0, A.dev_err, WAIT_LIMIT);
+        mbar_wait_bounded(&bars[1], phase1, A.dev_err, WAIT_LIMIT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reduction of the stream-K partial sums (fixed order, FP64) and epilogue.
+// ---------------------------------------------------------------------------
+struct EpiArgs {
+    StreamK sk;
+    const float* part;
+    int n, ncomp, comp;
+    EpilogueOut o;
+    int* dev_err;
+};
+
+__device__ __forceinline__ void check_finite(int* dev_err, double v)
+{
+    if (!isfinite(v)) atomicOr(dev_err, DEV_ERR_NONFINITE);
+}
+
+__global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= E.n) return;
+    const StreamK& sk = E.sk;
+    const int t = i / TGT_TILE, l = i % TGT_TILE;
+    const int nunits = sk.np + sk.ns;
+    double acc[14];
+#pragma unroll
+    for (int c = 0; c < 14; ++c) acc[c] = 0.0;
+    if (nunits > 0) {
+        const int b0 = sk.block_of(sk.unit_start(t, 0));
+        const int b1 = sk.block_of(sk.unit_start(t, nunits - 1));
+        const int rows = E.comp ? 2 * E.ncomp : E.ncomp;
+        for (int b = b0; b <= b1; ++b) {
+            const long long lo_b = sk.lo(b), hi_b = sk.lo(b + 1);
+            long long c0 = lo_b > (long long)t * sk.C ? lo_b : (long long)t * sk.C;
+            int tt, kk;
+            sk.first_at_or_after(c0, tt, kk);
+            if (tt != t || sk.unit_start(tt, kk) >= hi_b) continue;  // block b ran no unit of tile t
+            const float* P = E.part + (size_t)(b + t) * rows * TGT_TILE + l;
+            for (int c = 0; c < E.ncomp; ++c) {
+                double v = (double)P[(size_t)c * TGT_TILE];
+                if (E.comp) v += (double)P[(size_t)(E.ncomp + c) * TGT_TILE];
+                acc[c] += v;
+            }
+        }
+    }
+    const double f4pi = 0.079577471545947667884;  // 1/(4 pi)
+    const EpilogueOut& o = E.o;
+    const double u0 = acc[0] * f4pi, u1 = acc[1] * f4pi, u2 = acc[2] * f4pi;
+    double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (E.ncomp == 14) {
+        const double Sx = acc[3], Sy = acc[4], Sz = acc[5];
+        const double Gzz = -(acc[6] + acc[10]);
+        // J = ([S x] - 3 G') / (4 pi)
+        J[0] = (-3.0 * acc[6]) * f4pi;
+        J[1] = (-Sz - 3.0 * acc[7]) * f4pi;
+        J[2] = (Sy - 3.0 * acc[8]) * f4pi;
+        J[3] = (Sz - 3.0 * acc[9]) * f4pi;
+        J[4] = (-3.0 * acc[10]) * f4pi;
+        J[5] = (-Sx - 3.0 * acc[11]) * f4pi;
+        J[6] = (-Sy - 3.0 * acc[12]) * f4pi;
+        J[7] = (Sx - 3.0 * acc[13]) * f4pi;
+        J[8] = (-3.0 * Gzz) * f4pi;
+    }
+    if (o.mode == 0) {
+        o.u[i] = (float)u0;
+        o.u[E.n + i] = (float)u1;
+        o.u[2 * E.n + i] = (float)u2;
+        if (o.grad_u)
+            for (int c = 0; c < 9; ++c) o.grad_u[(size_t)c * E.n + i] = (float)J[c];
+        if (o.check_finite) {
+            check_finite(E.dev_err, u0 + u1 + u2);
+            if (o.grad_u) check_finite(E.dev_err, J[0] + J[1] + J[2] + J[3] + J[4] + J[5] + J[6] + J[7] + J[8]);
+        }
+        return;
+    }
+    // Right-hand side of Eq. 4-5 for particle i.
+    const float4 G4 = reinterpret_cast<const float4*>(o.str)[i];
+    const double Gm[3] = {G4.x, G4.y, G4.z};
+    // Vreman: alpha = J^T, beta = Delta^2 J J^T, Delta = sigma
+    double bt[3][3];
+    double aa = 0.0;
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            double s = 0.0;
+            for (int m = 0; m < 3; ++m) s += J[3 * p + m] * J[3 * q + m];
+            bt[p][q] = s * (double)o.sigma * (double)o.sigma;
+        }
+    for (int c = 0; c < 9; ++c) aa += J[c] * J[c];
+    const double B = bt[0][0] * bt[1][1] - bt[0][1] * bt[0][1] + bt[0][0] * bt[2][2] - bt[0][2] * bt[0][2] +
+                     bt[1][1] * bt[2][2] - bt[1][2] * bt[1][2];
+    const double nut = (aa > 0.0 && B > 0.0) ? (double)o.c_v * sqrt(B / aa) : 0.0;
+    double s[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        for (int c = 0; c < 3; ++c) v += o.classic ? J[3 * a + c] * Gm[c] : J[3 * c + a] * Gm[c];
+        s[a] = v;
+    }
+    o.dxdt[i] = (float)(u0 + o.uinf[0]);
+    o.dxdt[E.n + i] = (float)(u1 + o.uinf[1]);
+    o.dxdt[2 * E.n + i] = (float)(u2 + o.uinf[2]);
+    o.dGdt[i] = (float)s[0];
+    o.dGdt[E.n + i] = (float)s[1];
+    o.dGdt[2 * E.n + i] = (float)s[2];
+    o.nu_t[i] = (float)nut;
+    if (o.check_finite) check_finite(E.dev_err, u0 + u1 + u2 + s[0] + s[1] + s[2] + nut);
+}
+
+// ---------------------------------------------------------------------------
+// Particle strength exchange (Eq. 5's diffusion term):
+//   p_i = (2/sigma^2) sum_j nu_ij (v_i Gamma_j - v_j Gamma_i) zeta_sigma(r_ij),
+//   nu_ij = nu + (nu_t,i + nu_t,j)/2, zeta of Eq. 3.
+// A warp owns 32 consecutive particles; each lane tests one source tile's box
+// against the warp's box and the warp walks the tiles within 7 sigma, reading
+// each source once for all 32 lanes.  v_i Gamma_j - v_j Gamma_i is formed from two
+// rounded products so that the i == j term is exactly zero.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) pse_kernel(const float4* __restrict__ pos, const float4* __restrict__ str,
+                                                  const float* __restrict__ nu_t, int n,
+                                                  const float4* __restrict__ box, int ntiles, float inv2s2,
+                                                  float cut2, float nu, float pref, float* __restrict__ dGdt)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x);
+    const bool valid = i < n;
+    if ((blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >= n) return;  // whole warp past the end
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), gi = pi;
+    float nti = 0.f;
+    if (valid) {
+        pi = pos[i];
+        gi = str[i];
+        nti = nu_t ? nu_t[i] : 0.f;
+    }
+    float blo[3] = {valid ? pi.x : INFINITY, valid ? pi.y : INFINITY, valid ? pi.z : INFINITY};
+    float bhi[3] = {valid ? pi.x : -INFINITY, valid ? pi.y : -INFINITY, valid ? pi.z : -INFINITY};
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
+            bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
+        }
+    const float base = nu + 0.5f * nti;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    for (int tb = 0; tb < ntiles; tb += 32) {
+        const int tt = tb + lane;
+        bool near = false;
+        if (tt < ntiles) {
+            const float4 tlo = box[2 * tt], thi = box[2 * tt + 1];
+            const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
+            const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
+            const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
+            near = dx * dx + dy * dy + dz * dz < cut2;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, near);
+        while (mask) {
+            const int tile = tb + __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int j0 = tile * SRC_TILE, j1 = min(n, j0 + SRC_TILE);
+            for (int j = j0; j < j1; ++j) {
+                const float4 pj = __ldg(&pos[j]);
+                const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 < cut2) {
+                    const float4 gj = __ldg(&str[j]);
+                    const float ntj = nu_t ? __ldg(&nu_t[j]) : 0.f;
+                    const float w = fmaf(0.5f, ntj, base) * expf(-r2 * inv2s2);
+                    const float vi = pi.w, vj = pj.w;
+                    ax = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x)), ax);
+                    ay = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y)), ay);
+                    az = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.z), __fmul_rn(vj, gi.z)), az);
+                }
+            }
+        }
+    }
+    if (valid) {
+        dGdt[i] += pref * ax;
+        dGdt[n + i] += pref * ay;
+        dGdt[2 * n + i] += pref * az;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+__device__ int g_dev_err;  // device error word (one instance per device)
+
+namespace {
+std::mutex g_mu;
+int g_sm[64];
+int* g_err[64];
+int g_blocks[64][4];
+}  // namespace
+
+static int cur_dev()
+{
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+int sm_count()
+{
+    const int d = cur_dev();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (d < 0 || d >= 64) return 0;
+    if (!g_sm[d]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) v = 0;
+        g_sm[d] = v;
+    }
+    return g_sm[d];
+}
+
+int* dev_err_ptr()
+{
+    const int d = cur_dev();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (d < 0 || d >= 64) return nullptr;
+    if (!g_err[d]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dev_err) != cudaSuccess) return nullptr;
+        g_err[d] = static_cast<int*>(p);
+    }
+    return g_err[d];
+}
+
+template <bool G, bool C>
+static int occ_blocks()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, C>, TPB, 0) != cudaSuccess) nb = 1;
+    return nb < 1 ? 1 : nb;
+}
+
+int sweep_blocks(bool grad, bool comp)
+{
+    const int d = cur_dev();
+    const int sms = sm_count();
+    const int idx = (grad ? 2 : 0) + (comp ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (d >= 0 && d < 64 && g_blocks[d][idx]) return g_blocks[d][idx];
+    }
+    int per = grad ? (comp ? occ_blocks<true, true>() : occ_blocks<true, false>())
+                   : (comp ? occ_blocks<false, true>() : occ_blocks<false, false>());
+    const int v = per * (sms > 0 ? sms : 1);
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (d >= 0 && d < 64) g_blocks[d][idx] = v;
+    return v;
+}
+
+SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv)
+{
+    SweepPlan p;
+    p.n_tgt = (int)n_tgt;
+    p.n_src = (int)n_src;
+    p.m_seg = (int)m_seg;
+    p.grad = grad;
+    p.comp = comp;
+    p.ncomp = grad ? 14 : 3;
+    p.TT = (int)((n_tgt + TGT_TILE - 1) / TGT_TILE);
+    p.SP = (int)((n_src + SRC_TILE - 1) / SRC_TILE);
+    p.SS = (int)((m_seg + SRC_TILE - 1) / SRC_TILE);
+    StreamK& sk = p.sk;
+    sk.TT = p.TT;
+    sk.np = p.SP;
+    sk.ns = p.SS;
+    sk.wp = UNIT_W_P;
+    sk.ws = grad ? UNIT_W_S_GRAD : UNIT_W_S_VEL;
+    sk.C = (long long)sk.np * sk.wp + (long long)sk.ns * sk.ws;
+    sk.tot = (long long)sk.TT * sk.C;
+    const long long units = (long long)sk.TT * (sk.np + sk.ns);
+    long long B = sweep_blocks(grad, comp);
+    if (B > units) B = units;
+    if (B < 1) B = 1;
+    sk.B = (int)B;
+    p.off_psrc = cv.take((size_t)p.SP * SRC_TILE * P_F4 * 16);
+    p.off_pbox = cv.take((size_t)p.SP * 2 * 16);
+    p.off_ssrc = cv.take((size_t)p.SS * SRC_TILE * S_F4 * 16);
+    const size_t rows = (size_t)(comp ? 2 : 1) * p.ncomp;
+    p.off_part = cv.take((size_t)(sk.TT + sk.B) * rows * TGT_TILE * sizeof(float));
+    p.bytes = cv.off;
+    return p;
+}
+
+cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const float* src_pos, const float* src_str,
+                      const float* seg_a, const float* seg_b, float sigma, float seg_core, int vatistas_n,
+                      const EpilogueOut& out, cudaStream_t st)
+{
+    if (p.n_tgt == 0) return cudaSuccess;
+    float4* psrc = reinterpret_cast<float4*>(ws + p.off_psrc);
+    float4* pbox = reinterpret_cast<float4*>(ws + p.off_pbox);
+    float4* ssrc = reinterpret_cast<float4*>(ws + p.off_ssrc);
+    float* part = reinterpret_cast<float*>(ws + p.off_part);
+    if (p.SP > 0) trace_launch();
+    if (p.SP > 0)
+        pack_particles_kernel<<<p.SP, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(src_pos),
+                                                         reinterpret_cast<const float4*>(src_str), p.n_src, psrc,
+                                                         pbox);
+    if (p.SS > 0) trace_launch();
+    if (p.SS > 0)
+        pack_segments_kernel<<<p.SS, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(seg_a),
+                                                        reinterpret_cast<const float4*>(seg_b), p.m_seg, seg_core,
+                                                        vatistas_n, ssrc);
+    int* err = dev_err_ptr();
+    if (p.SP + p.SS > 0) {
+        SweepArgs A;
+        A.tgt = reinterpret_cast<const float4*>(tgt);
+        A.n_tgt = p.n_tgt;
+        A.psrc = psrc;
+        A.pbox = pbox;
+        A.n_src = p.n_src;
+        A.ssrc = ssrc;
+        A.m_seg = p.m_seg;
+        A.vn = vatistas_n;
+        A.sk = p.sk;
+        const double s = sigma;
+        A.nc.inv_s2 = (float)(1.0 / (s * s));
+        A.nc.inv_s3 = (float)(1.0 / (s * s * s));
+        A.nc.inv_s5 = (float)(1.0 / (s * s * s * s * s));
+        A.nc.far2 = (float)((double)RHO_FAR * RHO_FAR * s * s);
+        A.part = part;
+        A.dev_err = err;
+        const int B = p.sk.B;
+        TraceScope ts(p.grad ? VPM_TRACE_SWEEP : VPM_TRACE_SWEEP_VEL, st);
+        if (p.grad) {
+            if (p.comp)
+                sweep_kernel<true, true><<<B, TPB, 0, st>>>(A);
+            else
+                sweep_kernel<true, false><<<B, TPB, 0, st>>>(A);
+        } else {
+            if (p.comp)
+                sweep_kernel<false, true><<<B, TPB, 0, st>>>(A);
+            else
+                sweep_kernel<false, false><<<B, TPB, 0, st>>>(A);
+        }
+    }
+    EpiArgs E;
+    E.sk = p.sk;
+    E.part = part;
+    E.n = p.n_tgt;
+    E.ncomp = p.ncomp;
+    E.comp = p.comp ? 1 : 0;
+    E.o = out;
+    E.dev_err = err;
+    trace_launch();
+    epilogue_kernel<<<(p.n_tgt + 255) / 256, 256, 0, st>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t run_pse(const SweepPlan& p, char* ws, const float* pos, const float* str, const float* nu_t, int n,
+                    float sigma, float nu, float* dGdt, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const float4* pbox = reinterpret_cast<const float4*>(ws + p.off_pbox);
+    const double s = sigma;
+    const float inv2s2 = (float)(0.5 / (s * s));
+    const float cut2 = (float)((double)RHO_FAR * RHO_FAR * s * s);
+    // (2/sigma^2) (2 pi sigma^2)^(-3/2)
+    const float pref = (float)(2.0 / (s * s) * pow(2.0 * 3.14159265358979323846 * s * s, -1.5));
+    TraceScope ts(VPM_TRACE_PSE, st);
+    pse_kernel<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float4*>(pos),
+                                                reinterpret_cast<const float4*>(str), nu_t, n, pbox, p.SP, inv2s2,
+                                                cut2, nu, pref, dGdt);
+    return cudaGetLastError();
+}
+
+}  // namespace vpm

@@ -1,0 +1,201 @@
+"""GPU parity: every entry point of libvpm against the FP64 oracle on identical
+seeded FP32 inputs.  Relative L2 per output: compensated FP32 <= 2e-6, plain FP32
+<= 1e-4 (the stated error budget); integer-valued properties bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_11430_gb300 import synth
+from tests._util import TOL_COMP, TOL_PLAIN, grad_rows, planar_to_rows, rel_l2, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_11430_gb300 import api as a
+    from paper_2511_11430_gb300 import build
+
+    build.build()
+    return a
+
+
+def _check(api_u, api_g, ref_u, ref_J, tol, tag=""):
+    eu = rel_l2(planar_to_rows(api_u, 3), ref_u)
+    assert eu <= tol, f"{tag} u rel-L2 {eu:.3e} > {tol}"
+    if api_g is not None:
+        eg = rel_l2(grad_rows(api_g), ref_J)
+        assert eg <= tol, f"{tag} grad rel-L2 {eg:.3e} > {tol}"
+        return eu, eg
+    return eu, None
+
+
+@pytest.mark.parametrize("compensated", [True, False])
+@pytest.mark.parametrize("n", [1, 37, 2000, 3001])
+def test_induce_self_config1(api, n, compensated):
+    """Targets = sources (self-exclusion), 2-blade hover wake; sizes span several tiles and a ragged tail."""
+    w = synth.make(1, n=max(n, 2))
+    pos, G = w.pos[:n], w.strength[:n]
+    ru, rJ = oracle.p2p(pos, G, pos, w.sigma)
+    u, g = api.induce(to_dev(pos), to_dev(G), to_dev(pos), w.sigma, compensated=compensated)
+    torch.cuda.synchronize()
+    if n == 1:
+        assert np.all(u.cpu().numpy() == 0) and np.all(g.cpu().numpy() == 0)
+        return
+    _check(u, g, ru, rJ, TOL_COMP if compensated else TOL_PLAIN, f"n={n}")
+
+
+@pytest.mark.parametrize("compensated", [True, False])
+def test_induce_random_cloud_other_targets_velocity_only(api, compensated):
+    pos, G = synth.random_cloud(5, 4099, sigma=0.05)
+    tgt, _ = synth.random_cloud(6, 777, sigma=0.05)
+    ru = oracle.p2p(pos, G, tgt, 0.05, grad=False)
+    u = api.induce(to_dev(pos), to_dev(G), to_dev(tgt), 0.05, compensated=compensated, grad=False)
+    torch.cuda.synchronize()
+    _check(u, None, ru, None, TOL_COMP if compensated else TOL_PLAIN)
+
+
+def test_induce_coincident_and_empty(api):
+    pos = np.array([[0.1, 0.2, 0.3, 1e-3], [0.1, 0.2, 0.3, 1e-3], [0.4, 0.2, 0.3, 1e-3]], dtype=np.float32)
+    G = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], dtype=np.float32)
+    ru, rJ = oracle.p2p(pos, G, pos, 0.1)
+    u, g = api.induce(to_dev(pos), to_dev(G), to_dev(pos), 0.1)
+    torch.cuda.synchronize()
+    _check(u, g, ru, rJ, TOL_COMP)
+    u0, g0 = api.induce(to_dev(pos[:0]), to_dev(G[:0]), to_dev(pos), 0.1)
+    torch.cuda.synchronize()
+    assert np.all(u0.cpu().numpy() == 0) and np.all(g0.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("vn", [1, 2])
+@pytest.mark.parametrize("compensated", [True, False])
+def test_segments_config1(api, vn, compensated):
+    w = synth.make(1)
+    ru, rJ = oracle.segments(w.seg_a, w.seg_b, w.pos, w.seg_core, vn)
+    u, g = api.segments_induce(to_dev(w.seg_a), to_dev(w.seg_b), to_dev(w.pos), w.seg_core, vn,
+                               compensated=compensated)
+    torch.cuda.synchronize()
+    _check(u, g, ru, rJ, TOL_COMP if compensated else TOL_PLAIN, f"vn={vn}")
+
+
+def test_segments_random_ragged_and_near(api):
+    sa, sb = synth.random_segments(3, 301, length=0.2)
+    tgt, _ = synth.random_cloud(4, 1029, sigma=0.05)
+    # a few targets right next to segments (inside the core)
+    tgt[:50, :3] = (0.5 * (sa[:50, :3] + sb[:50, :3]) + 1e-3).astype(np.float32)
+    ru, rJ = oracle.segments(sa, sb, tgt, 0.02, 2)
+    u, g = api.segments_induce(to_dev(sa), to_dev(sb), to_dev(tgt), 0.02, 2)
+    torch.cuda.synchronize()
+    _check(u, g, ru, rJ, TOL_COMP)
+
+
+@pytest.mark.parametrize("classic", [False, True])
+@pytest.mark.parametrize("compensated", [True, False])
+def test_rhs_config1(api, classic, compensated):
+    w = synth.make(1)
+    rdx, rdG, rnut = oracle.rhs(w.pos, w.strength, w.seg_a, w.seg_b, w.sigma, nu=w.nu, c_v=w.c_v,
+                                seg_core=w.seg_core, u_inf=w.u_inf, classic=classic)
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=compensated,
+                     classic=classic)
+    dx, dG, nut = api.rhs(to_dev(w.pos), to_dev(w.strength), to_dev(w.seg_a), to_dev(w.seg_b), prm)
+    torch.cuda.synchronize()
+    tol = TOL_COMP if compensated else TOL_PLAIN
+    assert rel_l2(planar_to_rows(dx, 3), rdx) <= tol
+    assert rel_l2(planar_to_rows(dG, 3), rdG) <= tol
+    assert rel_l2(nut.cpu().numpy(), rnut) <= (1e-5 if compensated else 1e-3)
+
+
+def test_rhs_conserves_total_vorticity_without_segments(api):
+    """Transposed stretching + PSE cancel pairwise: sum_i dGamma_i/dt ~ 0 (up to FP32 rounding)."""
+    w = synth.make(1)
+    prm = api.Params(sigma=w.sigma, nu=1e-3, c_v=w.c_v)
+    dx, dG, nut = api.rhs(to_dev(w.pos), to_dev(w.strength), None, None, prm)
+    torch.cuda.synchronize()
+    d = dG.double().cpu().numpy()
+    assert np.abs(d.sum(axis=1)).max() <= 1e-5 * np.abs(d).sum(axis=1).max()
+
+
+def test_step_config1(api):
+    w = synth.make(1)
+    x0 = w.pos[:, :3].astype(np.float64)
+    G0 = w.strength[:, :3].astype(np.float64)
+    vol = w.pos[:, 3].copy()
+    dt = w.dt * 20  # a larger step makes the increment well above rounding
+    rx, rG = oracle.step(x0, G0, vol, w.seg_a, w.seg_b, w.sigma, dt, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core,
+                         u_inf=w.u_inf, cast_f32=True)
+    X = to_dev(np.ascontiguousarray(x0.T))
+    Gd = to_dev(np.ascontiguousarray(G0.T))
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=True)
+    api.step(X, Gd, to_dev(vol), to_dev(w.seg_a), to_dev(w.seg_b), prm, dt)
+    torch.cuda.synchronize()
+    gx = X.cpu().numpy().T
+    gG = Gd.cpu().numpy().T
+    # compare the increments (the state itself is dominated by its unchanged part)
+    assert rel_l2(gx - x0, rx - x0) <= 1e-5
+    assert rel_l2(gG - G0, rG - G0) <= 1e-5
+
+
+def test_aic_build_and_solve(api):
+    w = synth.make(1)
+    A_ref = oracle.aic_build(w.rings, w.colloc, w.normal, w.seg_core)
+    u_ind = oracle.p2p(w.pos, w.strength, w.colloc, w.sigma, grad=False)
+    b_ref = oracle.aic_rhs(w.v_rel, u_ind, w.normal)
+    A, b = api.aic_build(to_dev(w.rings), to_dev(w.colloc), to_dev(w.normal), w.seg_core, 2, v_rel=to_dev(w.v_rel),
+                         w_ind=to_dev(np.ascontiguousarray(u_ind.T.astype(np.float32))))
+    torch.cuda.synchronize()
+    assert rel_l2(A.cpu().numpy(), A_ref) <= 1e-5
+    np.testing.assert_allclose(b.cpu().numpy(), b_ref, rtol=1e-6, atol=1e-6 * np.abs(b_ref).max())
+    x, it, be = api.aic_solve(A, b, tol=1e-12, max_iter=30)
+    assert be <= 1e-12
+    # the FP64 solution of the FP32-stored system
+    xr = oracle.lu_solve(A.cpu().numpy().astype(np.float64), b.cpu().numpy())
+    assert rel_l2(x.cpu().numpy(), xr) <= 1e-9
+
+
+def test_aic_solve_large_random_and_not_converged(api):
+    rng = np.random.default_rng(1)
+    n = 1283  # ragged with respect to the 32-column panels
+    A = (rng.normal(size=(n, n)) + n ** 0.5 * np.eye(n)).astype(np.float32)
+    b = rng.normal(size=n)
+    x, it, be = api.aic_solve(to_dev(A), to_dev(b), tol=1e-13, max_iter=30)
+    assert be <= 1e-13
+    xr = np.linalg.solve(A.astype(np.float64), b)
+    assert rel_l2(x.cpu().numpy(), xr) <= 1e-10
+    with pytest.raises(Exception):
+        api.aic_solve(to_dev(A), to_dev(b), tol=0.0, max_iter=1)
+    Z = np.zeros((4, 4), dtype=np.float32)
+    with pytest.raises(Exception):
+        api.aic_solve(to_dev(Z), to_dev(np.ones(4)), tol=1e-12)
+
+
+@pytest.mark.parametrize("compensated", [True, False])
+def test_backward_vs_oracle_adjoint(api, compensated):
+    w = synth.make(4, n=5000)
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=(w.n_ctrl, 3)).astype(np.float32)
+    rx, rG = oracle.p2p_adjoint(w.pos, w.strength, w.colloc, w.sigma, g.astype(np.float64))
+    dx, dG = api.induce_backward(to_dev(w.pos), to_dev(w.strength), to_dev(w.colloc), w.sigma,
+                                 to_dev(np.ascontiguousarray(g.T)), compensated=compensated)
+    torch.cuda.synchronize()
+    tol = 1e-5 if compensated else 1e-3
+    assert rel_l2(planar_to_rows(dx, 3), rx) <= tol
+    assert rel_l2(planar_to_rows(dG, 3), rG) <= tol
+
+
+def test_backward_near_field_targets(api):
+    pos, G = synth.random_cloud(8, 1500, sigma=0.05, box=0.5)
+    tgt = pos[:300].copy()
+    tgt[:, :3] += np.float32(0.01)  # evaluation points inside the cores
+    g = np.random.default_rng(2).normal(size=(300, 3)).astype(np.float32)
+    rx, rG = oracle.p2p_adjoint(pos, G, tgt, 0.05, g.astype(np.float64))
+    dx, dG = api.induce_backward(to_dev(pos), to_dev(G), to_dev(tgt), 0.05, to_dev(np.ascontiguousarray(g.T)))
+    torch.cuda.synchronize()
+    assert rel_l2(planar_to_rows(dx, 3), rx) <= 1e-5
+    assert rel_l2(planar_to_rows(dG, 3), rG) <= 1e-5
+
+
+def test_device_error_word_clean(api):
+    assert api.device_error() == 0
