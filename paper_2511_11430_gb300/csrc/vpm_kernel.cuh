@@ -14,14 +14,15 @@ namespace vpm {
 // has only positive terms.  Hence, with K = q(rho)/(4 pi sigma^3) and
 // H = f(rho)/(4 pi sigma^5),
 //   q = g / rho^3      =  2^(-3/2) e^(-x) sum_k x^k / Gamma(k + 5/2)
-//   f = q'(rho) / rho  = dq/dx = -2^(-3/2) e^(-x) sum_k (k + 3/2) x^k / Gamma(k + 7/2)
-// (the second by differentiating the first term by term), both free of
+//   f = q'(rho) / rho  = dq/dx = -(3/2) 2^(-3/2) e^(-x) sum_k x^k / Gamma(k + 7/2)
+// (the second by differentiating the first term by term: the x^k coefficient of
+// T' - T, T the sum in q, is ((k + 1) - (k + 5/2)) / Gamma(k + 7/2)), both free of
 // cancellation.  For x >= 2 the closed form g = erf(sqrt x) - sqrt(2/pi) rho e^(-x)
 // loses at most a factor 1.3 and is used instead.
 // ---------------------------------------------------------------------------
 struct SeriesCoef {
     float c[16];  // 1 / Gamma(k + 5/2)
-    float d[16];  // (k + 3/2) / Gamma(k + 7/2)
+    float d[16];  // (3/2) / Gamma(k + 7/2)
 };
 
 constexpr SeriesCoef make_series()
@@ -31,7 +32,7 @@ constexpr SeriesCoef make_series()
     for (int k = 0; k < 16; ++k) {
         s.c[k] = (float)ck;
         const double cn = ck / (k + 2.5);  // 1/Gamma(k + 7/2)
-        s.d[k] = (float)((k + 1.5) * cn);
+        s.d[k] = (float)(1.5 * cn);
         ck = cn;
     }
     return s;
