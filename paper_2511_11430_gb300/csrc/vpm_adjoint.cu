@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(TPB, 1) adjoint_kernel(const AdjArgs A)
         outstanding = has_next;
         if (t != cur_t) {
             cur_t = t;
-            const int i0 = t * TGT_TILE + warp * 64 + lane, i1 = i0 + 32;
+            const int i0 = t * ADJ_TILE + warp * 64 + lane, i1 = i0 + 32;
             const bool v0 = i0 < A.n_src, v1 = i1 < A.n_src;
             float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0, g0 = p0, g1 = p0;
             if (v0) p0 = A.pos[i0], g0 = A.str[i0];
@@ -235,15 +235,15 @@ __global__ void __launch_bounds__(TPB, 1) adjoint_kernel(const AdjArgs A)
         }
         __syncthreads();
         if (!has_next || nt != t) {
-            float* P = A.part + ((size_t)(b + t) * (COMP ? 2 * A_NC : A_NC)) * TGT_TILE + warp * 64 + lane;
+            float* P = A.part + ((size_t)(b + t) * (COMP ? 2 * A_NC : A_NC)) * ADJ_TILE + warp * 64 + lane;
 #pragma unroll
             for (int i = 0; i < A_NC; ++i) {
                 const f2 v = COMP ? hi.v[i] : acc.v[i];
-                P[(size_t)i * TGT_TILE] = v.x;
-                P[(size_t)i * TGT_TILE + 32] = v.y;
+                P[(size_t)i * ADJ_TILE] = v.x;
+                P[(size_t)i * ADJ_TILE + 32] = v.y;
                 if (COMP) {
-                    P[(size_t)(A_NC + i) * TGT_TILE] = lo.v[i].x;
-                    P[(size_t)(A_NC + i) * TGT_TILE + 32] = lo.v[i].y;
+                    P[(size_t)(A_NC + i) * ADJ_TILE] = lo.v[i].x;
+                    P[(size_t)(A_NC + i) * ADJ_TILE + 32] = lo.v[i].y;
                 }
             }
             acc.zero();
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) adjoint_epilogue_kernel(const AdjEpiArgs 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= E.n) return;
     const StreamK& sk = E.sk;
-    const int t = i / TGT_TILE, l = i % TGT_TILE;
+    const int t = i / ADJ_TILE, l = i % ADJ_TILE;
     double acc[A_NC];
 #pragma unroll
     for (int c = 0; c < A_NC; ++c) acc[c] = 0.0;
@@ -293,11 +293,11 @@ __global__ void __launch_bounds__(256) adjoint_epilogue_kernel(const AdjEpiArgs 
             int tt, kk;
             sk.first_at_or_after(c0, tt, kk);
             if (tt != t || sk.unit_start(tt, kk) >= hi_b) continue;
-            const float* P = E.part + (size_t)(b + t) * rows * TGT_TILE + l;
+            const float* P = E.part + (size_t)(b + t) * rows * ADJ_TILE + l;
 #pragma unroll
             for (int c = 0; c < A_NC; ++c) {
-                double v = (double)P[(size_t)c * TGT_TILE];
-                if (E.comp) v += (double)P[(size_t)(A_NC + c) * TGT_TILE];
+                double v = (double)P[(size_t)c * ADJ_TILE];
+                if (E.comp) v += (double)P[(size_t)(A_NC + c) * ADJ_TILE];
                 acc[c] += v;
             }
         }
@@ -332,7 +332,7 @@ AdjPlan plan_adjoint(int64_t n_src, int64_t n_tgt, bool comp)
 {
     AdjPlan p;
     StreamK& sk = p.sk;
-    sk.TT = (int)((n_src + TGT_TILE - 1) / TGT_TILE);
+    sk.TT = (int)((n_src + ADJ_TILE - 1) / ADJ_TILE);
     sk.np = (int)((n_tgt + SRC_TILE - 1) / SRC_TILE);
     sk.ns = 0;
     sk.wp = 1;
@@ -346,7 +346,7 @@ AdjPlan plan_adjoint(int64_t n_src, int64_t n_tgt, bool comp)
     Carve cv;
     p.off_pts = cv.take((size_t)sk.np * SRC_TILE * A_F4 * 16);
     p.off_box = cv.take((size_t)sk.np * 2 * 16);
-    p.off_part = cv.take((size_t)(sk.TT + sk.B) * (comp ? 2 : 1) * A_NC * TGT_TILE * sizeof(float));
+    p.off_part = cv.take((size_t)(sk.TT + sk.B) * (comp ? 2 : 1) * A_NC * ADJ_TILE * sizeof(float));
     p.bytes = cv.off;
     return p;
 }

@@ -60,11 +60,11 @@ struct StepWs {
     size_t nut, pos, str, dxdt, dGdt, qx, qG, bytes;
 };
 
-StepWs step_layout(int64_t n, int64_t m, bool comp)
+StepWs step_layout(int64_t n, int64_t m, bool comp, bool classic)
 {
     StepWs s;
     Carve cv;
-    s.p = plan_sweep(n, n, m, true, comp, cv);
+    s.p = plan_sweep(n, n, m, true, comp, cv, !classic);
     s.nut = cv.take((size_t)n * sizeof(float));
     s.pos = cv.take((size_t)n * 16);
     s.str = cv.take((size_t)n * 16);
@@ -144,10 +144,11 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
         break;
     }
     case VPM_OP_RHS:
-        *bytes = plan_sweep(n_src, n_src, m_seg, true, comp, cv).bytes + rhs_extra(n_src);
+        *bytes = plan_sweep(n_src, n_src, m_seg, true, comp, cv, !(flags & VPM_STRETCH_CLASSIC)).bytes +
+                 rhs_extra(n_src);
         break;
     case VPM_OP_STEP:
-        *bytes = step_layout(n_src, m_seg, comp).bytes;
+        *bytes = step_layout(n_src, m_seg, comp, flags & VPM_STRETCH_CLASSIC).bytes;
         break;
     case VPM_OP_AIC_SOLVE:
         REQUIRE(n_tgt <= VPM_MAX_AIC, "AIC order %lld above %d", (long long)n_tgt, VPM_MAX_AIC);
@@ -272,7 +273,7 @@ vpm_status vpm_rhs(const float* pos_d, const float* str_d, int64_t n, const floa
             "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
     const bool comp = prm->flags & VPM_COMPENSATED;
     Carve cv;
-    const SweepPlan p = plan_sweep(n, n, m, true, comp, cv);
+    const SweepPlan p = plan_sweep(n, n, m, true, comp, cv, !(prm->flags & VPM_STRETCH_CLASSIC));
     const size_t off_nut = cv.take((size_t)n * sizeof(float));
     if (!overflow_guard(p)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
     if (!ws_d || ws_bytes < cv.off || !aligned16(ws_d))
@@ -312,7 +313,7 @@ vpm_status vpm_step(double* x_d, double* G_d, const float* vol_d, int64_t n, con
     REQUIRE(m == 0 || (seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d)),
             "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
     const bool comp = prm->flags & VPM_COMPENSATED;
-    const StepWs L = step_layout(n, m, comp);
+    const StepWs L = step_layout(n, m, comp, prm->flags & VPM_STRETCH_CLASSIC);
     if (!overflow_guard(L.p)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
     if (!ws_d || ws_bytes < L.bytes || !aligned16(ws_d))
         return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", L.bytes, ws_bytes);

@@ -10,15 +10,19 @@
 
 namespace vpm {
 
-constexpr int TPB = 256;          // threads per sweep block (8 warps)
-constexpr int TGT_TILE = 512;     // targets per target tile: two per thread
+constexpr int SWEEP_CW = 16;                 // consumer warps per sweep block
+constexpr int SWEEP_TPB = (SWEEP_CW + 1) * 32;  // + one producer warp
+constexpr int TGT_TILE = SWEEP_CW * 64;      // targets per sweep target tile: two per thread
+constexpr int SWEEP_STAGES = 4;              // shared-memory source tiles in flight
+constexpr int TPB = 256;          // threads per adjoint block (8 warps)
+constexpr int ADJ_TILE = 512;     // particles per adjoint tile: two per thread
 constexpr int SRC_TILE = 128;     // sources per particle or segment tile
 constexpr int P_F4 = 5;           // float4 per packed particle source
 constexpr int S_F4 = 6;           // float4 per packed segment source
 constexpr int T_F4 = 4;           // float4 per packed adjoint target (control point)
 constexpr float RHO_FAR = 7.0f;   // beyond 7 sigma the blob is a point vortex in FP32
 constexpr int UNIT_W_P = 10;      // stream-K cost of a particle tile
-constexpr int UNIT_W_S_GRAD = 28; // ... of a segment tile with gradient
+constexpr int UNIT_W_S_GRAD = 26; // ... of a segment tile with gradient
 constexpr int UNIT_W_S_VEL = 20;  // ... of a segment tile, velocity only
 
 // Workspace carving: 256-byte aligned sub-buffers.
@@ -34,21 +38,23 @@ struct Carve {
 
 int sm_count();
 int* dev_err_ptr();          // device error word of the current device
-int sweep_blocks(bool grad, bool comp);  // resident sweep blocks on the current device
+int sweep_blocks(bool grad, bool comp, bool stretch);  // resident sweep blocks on the current device
 int adjoint_blocks(bool comp);
 
 struct SweepPlan {
     int n_tgt = 0, n_src = 0, m_seg = 0;
     int TT = 0, SP = 0, SS = 0;
     bool grad = false, comp = false;
-    int ncomp = 0;  // logical accumulator rows (3 or 14)
+    bool stretch = false;  // accumulate the transposed stretching J^T Gamma_i per target
+    int ncomp = 0;         // logical accumulator rows (3, 14 or 17)
     StreamK sk{};
     size_t off_psrc = 0, off_pbox = 0, off_ssrc = 0, off_part = 0, bytes = 0;
 };
 
 // Plans a particle + segment sweep onto `n_tgt` targets starting at offset `base`
 // of a workspace carve; fills sk and the sub-buffer offsets.
-SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv);
+SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv,
+                     bool stretch = false);
 
 // Launches packing, the sweep and the reduction/epilogue.
 struct EpilogueOut {

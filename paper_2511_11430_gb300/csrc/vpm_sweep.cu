@@ -3,23 +3,28 @@
 //  * Gaussian-particle velocity and gradient (Eq. 2-4): u = sum_j K (Gamma_j x r),
 //    J = [S x]/(4 pi) + sum_j H (Gamma_j x r) (x) r with S = sum_j K Gamma_j.
 //  * Vatistas-cored straight segments (Sec. II.A), their velocity and exact gradient.
-//  * The stream-K reduction of per-block partial sums and the per-target epilogue:
+//  * Optionally the transposed stretching J^T Gamma_i of Eq. 5 per target.
+//  * The stream-K reduction of per-warp partial sums and the per-target epilogue:
 //    the velocity/gradient outputs, or the right-hand side of Eq. 4-5 (Vreman eddy
-//    viscosity, stretching) computed in FP64 from the reduced sums.
+//    viscosity, stretching) formed in FP64 from the reduced sums.
 //  * Particle strength exchange (the nu lap(Gamma) term of Eq. 5).
 //
 // Kernel organisation.  A thread owns two targets, kept in the two lanes of packed
 // float2 registers so that each FFMA2/FADD2/FMUL2 advances two pair interactions.
 // Sources are packed once per call into 128-source tiles (duplicated into both
-// lanes, negated copies included so that every subtraction is an add) and staged
-// into shared memory by one thread with the 1-D bulk-copy engine
-// (cp.async.bulk + mbarrier, double-buffered); every lane of every warp reads the
-// same source (broadcast).  Work is split stream-K over (target tile, source
-// tile) pairs so that every SM gets the same cost however few targets there are.
-// Far from the targets of a warp (tile bounding boxes more than 7 sigma apart) the
-// blob kernel equals the point-vortex kernel to FP32 precision, so far tiles run
-// the 1/r^3 form with a single rsqrt; near tiles evaluate the regularised kernel
-// exactly per pair.
+// lanes, negated copies included so that every subtraction is an add).  In the
+// sweep block a producer warp streams the tiles into a ring of shared-memory stages
+// with the bulk-copy engine (cp.async.bulk completing on a "full" mbarrier); each of
+// the 16 consumer warps waits on "full", reads every source by broadcast, and
+// releases the stage through an "empty" mbarrier, so warps drift freely within the
+// ring and no block-wide barrier sits in the loop.  Work is split stream-K over
+// (target tile, source tile) cost units so every SM gets the same cost however few
+// targets there are.  Far from a warp's 64 targets (bounding boxes more than 7 sigma
+// apart) the blob kernel equals the point-vortex kernel to FP32 precision, so far
+// tiles run the 1/r^3 form with one rsqrt; near tiles evaluate the regularised
+// kernel exactly per pair.  Each tile's sums start from zero and are folded into a
+// per-thread running sum kept in shared memory: a compensated (hi, lo) pair with
+// Knuth's two-sum, or a plain sum, so long source lists keep a tile-sized error.
 #include <math.h>
 
 #include <mutex>
@@ -31,60 +36,78 @@
 namespace vpm {
 
 // ---------------------------------------------------------------------------
-// Accumulators of one thread (two targets per f2): u, S and the 8 independent
+// Accumulators of one thread (two targets per f2): u, S, the 8 independent
 // entries of G' = sum h (Gamma x r) (x) r (its trace vanishes pair by pair, so
-// G'_zz = -G'_xx - G'_yy).  J = ([S x] - 3 G') / (4 pi), u = u / (4 pi).
+// G'_zz = -G'_xx - G'_yy) and, with STRETCH, s = 4 pi J^T Gamma_i.
+// J = ([S x] - 3 G') / (4 pi), u = u / (4 pi).
 // ---------------------------------------------------------------------------
-template <bool GRAD>
+template <bool GRAD, bool STRETCH>
 struct Acc {
-    f2 u[3];
-    f2 S[3];
-    f2 G[8];
+    static constexpr int N = GRAD ? (STRETCH ? 17 : 14) : 3;
+    f2 v[N];
     __device__ __forceinline__ void zero()
     {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) u[i] = zero2();
-        if (GRAD) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) S[i] = zero2();
-#pragma unroll
-            for (int i = 0; i < 8; ++i) G[i] = zero2();
-        }
+        for (int i = 0; i < N; ++i) v[i] = zero2();
     }
-    __device__ __forceinline__ f2& at(int i) { return i < 3 ? u[i] : (i < 6 ? S[i - 3] : G[i - 6]); }
 };
 
-template <bool GRAD>
-__device__ __forceinline__ void accum_particle(Acc<GRAD>& a, f2 K, f2 h, f2 rx, f2 ry, f2 rz, f2 gx, f2 gy, f2 gz,
-                                               f2 ngx, f2 ngy, f2 ngz)
+// The target's own strength, for the stretching terms.
+struct Own {
+    f2 gx, gy, gz, ngx, ngy, ngz;
+};
+
+template <bool GRAD, bool STRETCH, bool NEAR>
+__device__ __forceinline__ void accum_particle(Acc<GRAD, STRETCH>& a, f2 K, f2 h, f2 rx, f2 ry, f2 rz, f2 gx, f2 gy,
+                                               f2 gz, f2 ngx, f2 ngy, f2 ngz, const Own& o)
 {
     const f2 cx = fma2(gy, rz, mul2(ngz, ry));
     const f2 cy = fma2(gz, rx, mul2(ngx, rz));
     const f2 cz = fma2(gx, ry, mul2(ngy, rx));
-    a.u[0] = fma2(K, cx, a.u[0]);
-    a.u[1] = fma2(K, cy, a.u[1]);
-    a.u[2] = fma2(K, cz, a.u[2]);
+    a.v[0] = fma2(K, cx, a.v[0]);
+    a.v[1] = fma2(K, cy, a.v[1]);
+    a.v[2] = fma2(K, cz, a.v[2]);
     if (GRAD) {
-        a.S[0] = fma2(K, gx, a.S[0]);
-        a.S[1] = fma2(K, gy, a.S[1]);
-        a.S[2] = fma2(K, gz, a.S[2]);
+        a.v[3] = fma2(K, gx, a.v[3]);
+        a.v[4] = fma2(K, gy, a.v[4]);
+        a.v[5] = fma2(K, gz, a.v[5]);
         const f2 hx = mul2(h, cx), hy = mul2(h, cy), hz = mul2(h, cz);
-        a.G[0] = fma2(hx, rx, a.G[0]);
-        a.G[1] = fma2(hx, ry, a.G[1]);
-        a.G[2] = fma2(hx, rz, a.G[2]);
-        a.G[3] = fma2(hy, rx, a.G[3]);
-        a.G[4] = fma2(hy, ry, a.G[4]);
-        a.G[5] = fma2(hy, rz, a.G[5]);
-        a.G[6] = fma2(hz, rx, a.G[6]);
-        a.G[7] = fma2(hz, ry, a.G[7]);
+        a.v[6] = fma2(hx, rx, a.v[6]);
+        a.v[7] = fma2(hx, ry, a.v[7]);
+        a.v[8] = fma2(hx, rz, a.v[8]);
+        a.v[9] = fma2(hy, rx, a.v[9]);
+        a.v[10] = fma2(hy, ry, a.v[10]);
+        a.v[11] = fma2(hy, rz, a.v[11]);
+        a.v[12] = fma2(hz, rx, a.v[12]);
+        a.v[13] = fma2(hz, ry, a.v[13]);
+    }
+    if (STRETCH && NEAR) {
+        // Transposed stretching per pair, written with d = Gamma_j - Gamma_i (exact
+        // when the strengths are close) so that nothing cancels:
+        //   K (Gamma_i x Gamma_j) = K (Gamma_i x d),
+        //   -3 h ((Gamma_j x r) . Gamma_i) r = 3 h (d . (Gamma_i x r)) r.
+        const f2 dx = add2(gx, o.ngx), dy = add2(gy, o.ngy), dz = add2(gz, o.ngz);
+        const f2 tx = fma2(o.gy, dz, mul2(o.ngz, dy));
+        const f2 ty = fma2(o.gz, dx, mul2(o.ngx, dz));
+        const f2 tz = fma2(o.gx, dy, mul2(o.ngy, dx));
+        a.v[14] = fma2(K, tx, a.v[14]);
+        a.v[15] = fma2(K, ty, a.v[15]);
+        a.v[16] = fma2(K, tz, a.v[16]);
+        const f2 ex = fma2(o.gy, rz, mul2(o.ngz, ry));
+        const f2 ey = fma2(o.gz, rx, mul2(o.ngx, rz));
+        const f2 ez = fma2(o.gx, ry, mul2(o.ngy, rx));
+        const f2 w = mul2(mul2(h, splat(3.f)), fma2(dz, ez, fma2(dy, ey, mul2(dx, ex))));
+        a.v[14] = fma2(w, rx, a.v[14]);
+        a.v[15] = fma2(w, ry, a.v[15]);
+        a.v[16] = fma2(w, rz, a.v[16]);
     }
 }
 
 // Packed particle source (5 float4, both lanes equal):
 //   (-x,-x,-y,-y) (-z,-z,gx,gx) (gy,gy,gz,gz) (-gx,-gx,-gy,-gy) (-gz,-gz,0,0)
-template <bool GRAD, bool NEAR>
-__device__ __forceinline__ void particle_tile(Acc<GRAD>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y, f2 Z,
-                                              const NearConst& nc)
+template <bool GRAD, bool STRETCH, bool NEAR>
+__device__ __forceinline__ void particle_tile(Acc<GRAD, STRETCH>& a, const float4* __restrict__ s, int cnt, f2 X,
+                                              f2 Y, f2 Z, const NearConst& nc, const Own& o)
 {
 #pragma unroll 2
     for (int j = 0; j < cnt; ++j) {
@@ -104,45 +127,59 @@ __device__ __forceinline__ void particle_tile(Acc<GRAD>& a, const float4* __rest
             K = mul2(i2, rs);
             h = GRAD ? mul2(K, i2) : K;
         }
-        accum_particle<GRAD>(a, K, h, rx, ry, rz, make_float2(q1.z, q1.w), make_float2(q2.x, q2.y),
-                             make_float2(q2.z, q2.w), make_float2(q3.x, q3.y), make_float2(q3.z, q3.w),
-                             make_float2(q4.x, q4.y));
+        accum_particle<GRAD, STRETCH, NEAR>(a, K, h, rx, ry, rz, make_float2(q1.z, q1.w), make_float2(q2.x, q2.y),
+                                            make_float2(q2.z, q2.w), make_float2(q3.x, q3.y),
+                                            make_float2(q3.z, q3.w), make_float2(q4.x, q4.y), o);
     }
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Inverse lengths of one segment pair for one lane, with the end-point and axis
 // guards: a target within 1e-10 |r0| (or 1e-15 m) of an end point, or with
-// D == 0, gets zero.
+// D == 0, gets zero (all outputs zero so every later product stays finite).
 __device__ __forceinline__ void seg_lane(float n1, float n2, float c2, float L2, float e, int vn, float& i1,
-                                         float& i2, float& invD)
+                                         float& i2, float& irs, float& invD)
 {
     const float thr = fmaxf(1e-20f * L2, 1e-30f);  // (1e-10 |r0|)^2, (1e-15 m)^2
     const bool ok = (n1 > thr) && (n2 > thr);
     float D;
     if (vn == 2) {
-        const float Dsq = fmaf(c2, c2, e);
-        invD = Dsq > 0.f ? rsqrt_approx(Dsq) : 0.f;
-        D = Dsq;
+        D = fmaf(c2, c2, e);
+        invD = D > 0.f ? rsqrt_approx(D) : 0.f;
     } else {
         D = c2 + e;
         invD = D > 0.f ? __frcp_rn(D) : 0.f;
     }
-    i1 = ok ? rsqrt_approx(n1) : 0.f;
-    i2 = ok ? rsqrt_approx(n2) : 0.f;
-    if (!ok || !(D > 0.f)) invD = 0.f;
+    if (!ok || !(D > 0.f)) {
+        i1 = i2 = irs = invD = 0.f;
+        return;
+    }
+    i1 = rsqrt_approx(n1);
+    i2 = rsqrt_approx(n2);
+    irs = rcp_approx(fmaf(n1, i1, n2 * i2));  // 1 / (|r1| + |r2|)
 }
 
 // Packed segment source (6 float4, both lanes equal):
 //   (-ax,-ax,-ay,-ay) (-az,-az,r0x,r0x) (r0y,r0y,r0z,r0z) (-r0x,-r0x,-r0y,-r0y) (-r0z,-r0z,-L2,-L2) (G,G,e,e)
-// with r0 = b - a, L2 = |r0|^2, e = (core |r0|)^(2n).  Velocity
-//   u = G/(4 pi) c d / D,  c = r0 x r1,  d = r0.(r1/|r1| - r2/|r2|),
-//   D = (|c|^(2n) + e)^(1/n);
-// gradient J = G/(4 pi D) ( d [r0 x] + c (x) w ),  w = grad d - d grad D / D,
-//   grad d = r0 (1/|r1| - 1/|r2|) - (r0.r1) r1/|r1|^3 + (r0.r2) r2/|r2|^3,
-//   grad D / D = 2 |c|^(2n-2) D^(-n) (c x r0).
-template <bool GRAD>
-__device__ __forceinline__ void segment_tile(Acc<GRAD>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y, f2 Z,
-                                             int vn)
+// with r0 = b - a, L2 = |r0|^2, e = (core |r0|)^(2n).  With r1 = x - a, r2 = x - b,
+// c = r0 x r1 (= r1 x r2), D = (|c|^(2n) + e)^(1/n):
+//   u = G/(4 pi) c d / D,   d = r0 . (r1/|r1| - r2/|r2|),
+//   J = G/(4 pi D) ( d [r0 x] + c (x) w ),   w = grad d - d grad D / D.
+// Both are written to avoid cancellation in FP32:
+//   d = (r0 . r1) (1/|r1| - 1/|r2|) + L2/|r2|,
+//     1/|r1| - 1/|r2| = (L2 - 2 r0.r1) / (|r1| |r2| (|r1| + |r2|))   (|r2|^2 - |r1|^2 = L2 - 2 r0.r1),
+//   grad d = (r1/|r1|^3 - r2/|r2|^3) x c   (the projections of r0 normal to r1, r2),
+//   grad D / D = 2 |c|^(2n-2) D^(-n) (c x r0),   so  w = (r1/|r1|^3 - r2/|r2|^3 + k3 r0) x c
+//   with k3 = 2 d |c|^(2n-2) D^(-n).
+template <bool GRAD, bool STRETCH>
+__device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y,
+                                             f2 Z, int vn)
 {
 #pragma unroll 1
     for (int j = 0; j < cnt; ++j) {
@@ -162,25 +199,21 @@ __device__ __forceinline__ void segment_tile(Acc<GRAD>& a, const float4* __restr
         const f2 n2 = fma2(r2z, r2z, fma2(r2y, r2y, mul2(r2x, r2x)));
         const f2 p1 = fma2(r0z, r1z, fma2(r0y, r1y, mul2(r0x, r1x)));
         const f2 c2 = fma2(cz, cz, fma2(cy, cy, mul2(cx, cx)));
-        f2 i1, i2, invD;
-        seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, invD.x);
-        seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, invD.y);
-        const f2 p2 = add2(p1, nL2);  // r0 . r2
-        const f2 ni2 = mul2(i2, splat(-1.f));
-        const f2 d = fma2(p1, i1, mul2(p2, ni2));
+        f2 i1, i2, irs, invD;
+        seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, irs.x, invD.x);
+        seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, irs.y, invD.y);
+        const f2 L2 = mul2(nL2, splat(-1.f));
+        const f2 di = mul2(mul2(fma2(splat(-2.f), p1, L2), mul2(i1, i2)), irs);  // 1/|r1| - 1/|r2|
+        const f2 d = fma2(p1, di, mul2(L2, i2));
         const f2 gi = mul2(gs, invD);
         const f2 coef = mul2(gi, d);
-        a.u[0] = fma2(coef, cx, a.u[0]);
-        a.u[1] = fma2(coef, cy, a.u[1]);
-        a.u[2] = fma2(coef, cz, a.u[2]);
+        a.v[0] = fma2(coef, cx, a.v[0]);
+        a.v[1] = fma2(coef, cy, a.v[1]);
+        a.v[2] = fma2(coef, cz, a.v[2]);
         if (GRAD) {
-            a.S[0] = fma2(coef, r0x, a.S[0]);
-            a.S[1] = fma2(coef, r0y, a.S[1]);
-            a.S[2] = fma2(coef, r0z, a.S[2]);
-            const f2 t1 = add2(i1, ni2);
-            // -(r0.r1)/|r1|^3 and (r0.r2)/|r2|^3, ordered so that no power of 1/|r| overflows
-            const f2 k1n = mul2(mul2(p1, mul2(i1, splat(-1.f))), mul2(i1, i1));
-            const f2 k2 = mul2(mul2(p2, i2), mul2(i2, i2));
+            a.v[3] = fma2(coef, r0x, a.v[3]);
+            a.v[4] = fma2(coef, r0y, a.v[4]);
+            a.v[5] = fma2(coef, r0z, a.v[5]);
             f2 k3;
             if (vn == 2) {
                 const f2 tmp = mul2(mul2(d, c2), mul2(invD, invD));
@@ -189,25 +222,50 @@ __device__ __forceinline__ void segment_tile(Acc<GRAD>& a, const float4* __restr
                 const f2 tmp = mul2(d, invD);
                 k3 = add2(tmp, tmp);
             }
-            // r0 x c = -(c x r0)
-            const f2 crx = fma2(r0y, cz, mul2(nr0z, cy));
-            const f2 cry = fma2(r0z, cx, mul2(nr0x, cz));
-            const f2 crz = fma2(r0x, cy, mul2(nr0y, cx));
-            const f2 wx = fma2(r0x, t1, fma2(r1x, k1n, fma2(r2x, k2, mul2(crx, k3))));
-            const f2 wy = fma2(r0y, t1, fma2(r1y, k1n, fma2(r2y, k2, mul2(cry, k3))));
-            const f2 wz = fma2(r0z, t1, fma2(r1z, k1n, fma2(r2z, k2, mul2(crz, k3))));
+            const f2 i1c = mul2(mul2(i1, i1), i1);
+            const f2 ni2c = mul2(mul2(i2, i2), mul2(i2, splat(-1.f)));
+            const f2 vx = fma2(k3, r0x, fma2(r1x, i1c, mul2(r2x, ni2c)));
+            const f2 vy = fma2(k3, r0y, fma2(r1y, i1c, mul2(r2y, ni2c)));
+            const f2 vz = fma2(k3, r0z, fma2(r1z, i1c, mul2(r2z, ni2c)));
+            const f2 nvx = mul2(vx, splat(-1.f)), nvy = mul2(vy, splat(-1.f)), nvz = mul2(vz, splat(-1.f));
+            const f2 wx = fma2(vy, cz, mul2(nvz, cy));  // w = v x c
+            const f2 wy = fma2(vz, cx, mul2(nvx, cz));
+            const f2 wz = fma2(vx, cy, mul2(nvy, cx));
             const f2 cg = mul2(gi, splat(-1.0f / 3.0f));  // stored as G' with J = -3 G'
             const f2 gx = mul2(cg, cx), gy = mul2(cg, cy), gz = mul2(cg, cz);
-            a.G[0] = fma2(gx, wx, a.G[0]);
-            a.G[1] = fma2(gx, wy, a.G[1]);
-            a.G[2] = fma2(gx, wz, a.G[2]);
-            a.G[3] = fma2(gy, wx, a.G[3]);
-            a.G[4] = fma2(gy, wy, a.G[4]);
-            a.G[5] = fma2(gy, wz, a.G[5]);
-            a.G[6] = fma2(gz, wx, a.G[6]);
-            a.G[7] = fma2(gz, wy, a.G[7]);
+            a.v[6] = fma2(gx, wx, a.v[6]);
+            a.v[7] = fma2(gx, wy, a.v[7]);
+            a.v[8] = fma2(gx, wz, a.v[8]);
+            a.v[9] = fma2(gy, wx, a.v[9]);
+            a.v[10] = fma2(gy, wy, a.v[10]);
+            a.v[11] = fma2(gy, wz, a.v[11]);
+            a.v[12] = fma2(gz, wx, a.v[12]);
+            a.v[13] = fma2(gz, wy, a.v[13]);
         }
     }
+}
+
+// s += J_tile^T Gamma_i (times 4 pi) from a tile's partial S and G': the far
+// tiles and segment tiles, whose stretching does not cancel.
+template <bool GRAD, bool STRETCH>
+__device__ __forceinline__ void stretch_from_tile(Acc<GRAD, STRETCH>& a, const Own& o)
+{
+    if (!STRETCH) return;
+    const f2 Sx = a.v[3], Sy = a.v[4], Sz = a.v[5];
+    const f2 Gxx = a.v[6], Gxy = a.v[7], Gxz = a.v[8], Gyx = a.v[9], Gyy = a.v[10], Gyz = a.v[11], Gzx = a.v[12],
+             Gzy = a.v[13];
+    const f2 Gzz = mul2(add2(Gxx, Gyy), splat(-1.f));
+    const f2 m3 = splat(-3.f);
+    // Gamma_i x S - 3 G'^T Gamma_i
+    const f2 tx = fma2(o.gy, Sz, mul2(o.ngz, Sy));
+    const f2 ty = fma2(o.gz, Sx, mul2(o.ngx, Sz));
+    const f2 tz = fma2(o.gx, Sy, mul2(o.ngy, Sx));
+    const f2 gx = fma2(Gzx, o.gz, fma2(Gyx, o.gy, mul2(Gxx, o.gx)));
+    const f2 gy = fma2(Gzy, o.gz, fma2(Gyy, o.gy, mul2(Gxy, o.gx)));
+    const f2 gz = fma2(Gzz, o.gz, fma2(Gyz, o.gy, mul2(Gxz, o.gx)));
+    a.v[14] = add2(a.v[14], fma2(m3, gx, tx));
+    a.v[15] = add2(a.v[15], fma2(m3, gy, ty));
+    a.v[16] = add2(a.v[16], fma2(m3, gz, tz));
 }
 
 // ---------------------------------------------------------------------------
@@ -278,10 +336,11 @@ __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* _
 }
 
 // ---------------------------------------------------------------------------
-// The stream-K sweep.
+// The stream-K sweep: one producer warp + SWEEP_CW consumer warps per block.
 // ---------------------------------------------------------------------------
 struct SweepArgs {
     const float4* tgt;
+    const float4* tstr;  // target strengths (stretching), may be null
     int n_tgt;
     const float4* psrc;
     const float4* pbox;
@@ -298,69 +357,113 @@ struct SweepArgs {
 constexpr int BUF_F4 = SRC_TILE * S_F4;  // the larger of the two tile formats
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
-template <bool GRAD, bool COMP>
-__global__ void __launch_bounds__(TPB, 1) sweep_kernel(const SweepArgs A)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
-    __shared__ __align__(128) float4 sbuf[2][BUF_F4];
-    __shared__ __align__(8) uint64_t bars[2];
-    __shared__ float wbox[TPB / 32][6];
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <bool GRAD, bool STRETCH>
+__host__ __device__ constexpr int n_rows()
+{
+    return Acc<GRAD, STRETCH>::N;
+}
+
+// Dynamic shared memory: SWEEP_STAGES source tiles, then the running sums of the
+// consumer threads, [row][hi|lo][thread] as float2 (the two targets).
+template <bool GRAD, bool COMP, bool STRETCH>
+__host__ __device__ constexpr size_t sweep_smem_bytes()
+{
+    return (size_t)SWEEP_STAGES * BUF_F4 * 16 + (size_t)n_rows<GRAD, STRETCH>() * (COMP ? 2 : 1) * SWEEP_CW * 32 * 8;
+}
+
+template <bool GRAD, bool COMP, bool STRETCH>
+__global__ void __maxnreg__(120) sweep_kernel(const SweepArgs A)
+{
+    extern __shared__ __align__(128) float4 dsm[];
+    __shared__ __align__(8) uint64_t full[SWEEP_STAGES], empty[SWEEP_STAGES];
+    constexpr int NR = n_rows<GRAD, STRETCH>();
+    constexpr int NT = SWEEP_CW * 32;
+    float4* stage = dsm;
+    f2* run = reinterpret_cast<f2*>(dsm + SWEEP_STAGES * BUF_F4);  // [NR][COMP?2:1][NT]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const StreamK& sk = A.sk;
     const int b = blockIdx.x;
     const long long lo_b = sk.lo(b), hi_b = sk.lo(b + 1);
-    int t, k;
-    sk.first_at_or_after(lo_b, t, k);
-    if (t >= sk.TT || sk.unit_start(t, k) >= hi_b) return;  // block owns no unit (uniform)
+    int t0, k0;
+    sk.first_at_or_after(lo_b, t0, k0);
+    if (t0 >= sk.TT || sk.unit_start(t0, k0) >= hi_b) return;  // block owns no unit (uniform)
     const int nunits = sk.np + sk.ns;
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int s = 0; s < SWEEP_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], SWEEP_CW);
+        }
         mbar_fence_init();
     }
     __syncthreads();
 
-    auto issue = [&](int kk, int slot) {
-        const float4* src;
-        uint32_t bytes;
-        if (kk < sk.np) {
-            src = A.psrc + (size_t)kk * SRC_TILE * P_F4;
-            bytes = SRC_TILE * P_F4 * 16;
-        } else {
-            src = A.ssrc + (size_t)(kk - sk.np) * SRC_TILE * S_F4;
-            bytes = SRC_TILE * S_F4 * 16;
+    if (warp == SWEEP_CW) {
+        // ---------------- producer ----------------
+        if (lane != 0) return;
+        int t = t0, k = k0;
+        bool ok = true;
+        int issued = 0;
+        for (int i = 0;; ++i) {
+            const int s = i % SWEEP_STAGES, r = i / SWEEP_STAGES;
+            if (r > 0 && !mbar_wait_bounded(&empty[s], (r - 1) & 1, A.dev_err, WAIT_LIMIT)) {
+                ok = false;
+                break;
+            }
+            const float4* src;
+            uint32_t bytes;
+            if (k < sk.np) {
+                src = A.psrc + (size_t)k * SRC_TILE * P_F4;
+                bytes = SRC_TILE * P_F4 * 16;
+            } else {
+                src = A.ssrc + (size_t)(k - sk.np) * SRC_TILE * S_F4;
+                bytes = SRC_TILE * S_F4 * 16;
+            }
+            fence_proxy_async_smem();
+            mbar_expect_tx(&full[s], bytes);
+            bulk_g2s(stage + (size_t)s * BUF_F4, src, bytes, &full[s]);
+            issued = i + 1;
+            if (++k == nunits) {
+                k = 0;
+                ++t;
+            }
+            if (t >= sk.TT || sk.unit_start(t, k) >= hi_b) break;
         }
-        fence_proxy_async_smem();
-        mbar_expect_tx(&bars[slot], bytes);
-        bulk_g2s(&sbuf[slot][0], src, bytes, &bars[slot]);
-    };
-
-    if (tid == 0) issue(k, 0);
-
-    Acc<GRAD> acc, hi, lo;
-    acc.zero();
-    if (COMP) {
-        hi.zero();
-        lo.zero();
+        if (!ok) {
+            // let the copies already issued land before the block's shared memory is released
+            for (int i = (issued > SWEEP_STAGES ? issued - SWEEP_STAGES : 0); i < issued; ++i)
+                mbar_wait_bounded(&full[i % SWEEP_STAGES], (i / SWEEP_STAGES) & 1, A.dev_err, WAIT_LIMIT);
+        }
+        return;
     }
-    f2 X = zero2(), Y = zero2(), Z = zero2();
-    int cur_t = -1;
-    uint32_t phase0 = 0, phase1 = 0;
-    bool outstanding_next = false;
 
-    for (int it = 0;; ++it) {
-        const int slot = it & 1;
+    // ---------------- consumers ----------------
+    const int ct = warp * 32 + lane;  // consumer thread index
+    Acc<GRAD, STRETCH> acc;
+    Own own{zero2(), zero2(), zero2(), zero2(), zero2(), zero2()};
+    f2 X = zero2(), Y = zero2(), Z = zero2();
+    float blo[3], bhi[3];
+    int t = t0, k = k0, cur_t = -1;
+    auto zero_run = [&]() {
+#pragma unroll
+        for (int q = 0; q < NR * (COMP ? 2 : 1); ++q) run[q * NT + ct] = zero2();
+    };
+    zero_run();
+    for (int i = 0;; ++i) {
+        const int s = i % SWEEP_STAGES, r = i / SWEEP_STAGES;
         int nt = t, nk = k + 1;
         if (nk == nunits) {
             nk = 0;
             ++nt;
         }
         const bool has_next = nt < sk.TT && sk.unit_start(nt, nk) < hi_b;
-        if (has_next && tid == 0) issue(nk, slot ^ 1);
-        outstanding_next = has_next;
-
-        if (t != cur_t) {  // new target tile: load two targets per thread and the warp's box
+        if (t != cur_t) {  // new target tile: this warp's 64 targets, their box and strengths
             cur_t = t;
             const int i0 = t * TGT_TILE + warp * 64 + lane, i1 = i0 + 32;
             float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
@@ -370,8 +473,19 @@ __global__ void __launch_bounds__(TPB, 1) sweep_kernel(const SweepArgs A)
             X = make_float2(p0.x, p1.x);
             Y = make_float2(p0.y, p1.y);
             Z = make_float2(p0.z, p1.z);
-            float blo[3] = {v0 ? p0.x : INFINITY, v0 ? p0.y : INFINITY, v0 ? p0.z : INFINITY};
-            float bhi[3] = {v0 ? p0.x : -INFINITY, v0 ? p0.y : -INFINITY, v0 ? p0.z : -INFINITY};
+            if (STRETCH) {
+                float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+                if (v0) g0 = A.tstr[i0];
+                if (v1) g1 = A.tstr[i1];
+                own.gx = make_float2(g0.x, g1.x);
+                own.gy = make_float2(g0.y, g1.y);
+                own.gz = make_float2(g0.z, g1.z);
+                own.ngx = mul2(own.gx, splat(-1.f));
+                own.ngy = mul2(own.gy, splat(-1.f));
+                own.ngz = mul2(own.gz, splat(-1.f));
+            }
+            blo[0] = v0 ? p0.x : INFINITY, blo[1] = v0 ? p0.y : INFINITY, blo[2] = v0 ? p0.z : INFINITY;
+            bhi[0] = v0 ? p0.x : -INFINITY, bhi[1] = v0 ? p0.y : -INFINITY, bhi[2] = v0 ? p0.z : -INFINITY;
             if (v1) {
                 blo[0] = fminf(blo[0], p1.x), blo[1] = fminf(blo[1], p1.y), blo[2] = fminf(blo[2], p1.z);
                 bhi[0] = fmaxf(bhi[0], p1.x), bhi[1] = fmaxf(bhi[1], p1.y), bhi[2] = fmaxf(bhi[2], p1.z);
@@ -383,74 +497,57 @@ __global__ void __launch_bounds__(TPB, 1) sweep_kernel(const SweepArgs A)
                     blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
                     bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
                 }
-            if (lane == 0)
-                for (int c = 0; c < 3; ++c) wbox[warp][c] = blo[c], wbox[warp][3 + c] = bhi[c];
-            __syncwarp();
         }
+        if (!mbar_wait_bounded(&full[s], r & 1, A.dev_err, WAIT_LIMIT)) break;  // latched; results invalid
 
-        const bool ok = mbar_wait_bounded(&bars[slot], slot ? phase1 : phase0, A.dev_err, WAIT_LIMIT);
-        if (slot)
-            phase1 ^= 1;
-        else
-            phase0 ^= 1;
-        if (!__syncthreads_and(ok)) break;
-
-        const float4* s = &sbuf[slot][0];
+        const float4* src = stage + (size_t)s * BUF_F4;
+        acc.zero();
+        bool near_tile = false;
         if (k < sk.np) {
             const int cnt = min(SRC_TILE, A.n_src - k * SRC_TILE);
             const float4 tlo = A.pbox[2 * k], thi = A.pbox[2 * k + 1];
-            const float dx = fmaxf(0.f, fmaxf(tlo.x - wbox[warp][3], wbox[warp][0] - thi.x));
-            const float dy = fmaxf(0.f, fmaxf(tlo.y - wbox[warp][4], wbox[warp][1] - thi.y));
-            const float dz = fmaxf(0.f, fmaxf(tlo.z - wbox[warp][5], wbox[warp][2] - thi.z));
-            const bool near = dx * dx + dy * dy + dz * dz < A.nc.far2;
-            if (near)
-                particle_tile<GRAD, true>(acc, s, cnt, X, Y, Z, A.nc);
+            const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
+            const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
+            const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
+            near_tile = dx * dx + dy * dy + dz * dz < A.nc.far2;
+            if (near_tile)
+                particle_tile<GRAD, STRETCH, true>(acc, src, cnt, X, Y, Z, A.nc, own);
             else
-                particle_tile<GRAD, false>(acc, s, cnt, X, Y, Z, A.nc);
+                particle_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.nc, own);
         } else {
             const int cnt = min(SRC_TILE, A.m_seg - (k - sk.np) * SRC_TILE);
-            segment_tile<GRAD>(acc, s, cnt, X, Y, Z, A.vn);
+            segment_tile<GRAD, STRETCH>(acc, src, cnt, X, Y, Z, A.vn);
         }
-        if (COMP) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // stage s may be refilled
+        if (!near_tile) stretch_from_tile<GRAD, STRETCH>(acc, own);
+        // fold this tile's sums into the running sums
 #pragma unroll
-            for (int i = 0; i < (GRAD ? 14 : 3); ++i) fold2(hi.at(i), lo.at(i), acc.at(i));
-            acc.zero();
-        }
-        __syncthreads();  // buffer `slot` is free for the copy issued next iteration
-
-        const bool tile_end = !has_next || nt != t;
-        if (tile_end) {
-            const int nc = GRAD ? 14 : 3;
-            float* P = A.part + ((size_t)(b + t) * (COMP ? 2 * nc : nc)) * TGT_TILE + warp * 64 + lane;
-#pragma unroll
-            for (int i = 0; i < (GRAD ? 14 : 3); ++i) {
-                const f2 v = COMP ? hi.at(i) : acc.at(i);
-                P[(size_t)i * TGT_TILE] = v.x;
-                P[(size_t)i * TGT_TILE + 32] = v.y;
-                if (COMP) {
-                    const f2 w = lo.at(i);
-                    P[(size_t)(nc + i) * TGT_TILE] = w.x;
-                    P[(size_t)(nc + i) * TGT_TILE + 32] = w.y;
-                }
-            }
-            acc.zero();
+        for (int q = 0; q < NR; ++q) {
             if (COMP) {
-                hi.zero();
-                lo.zero();
+                f2 hi = run[(2 * q) * NT + ct], lo = run[(2 * q + 1) * NT + ct];
+                fold2(hi, lo, acc.v[q]);
+                run[(2 * q) * NT + ct] = hi;
+                run[(2 * q + 1) * NT + ct] = lo;
+            } else {
+                run[q * NT + ct] = add2(run[q * NT + ct], acc.v[q]);
             }
         }
-        if (!has_next) {
-            outstanding_next = false;
-            break;
+        if (!has_next || nt != t) {  // this warp's partial of target tile t
+            float* P = A.part + ((size_t)(b + t) * (COMP ? 2 * NR : NR)) * TGT_TILE + warp * 64 + lane;
+#pragma unroll
+            for (int q = 0; q < NR * (COMP ? 2 : 1); ++q) {
+                const f2 v = run[q * NT + ct];
+                // rows: hi of every accumulator first, then lo
+                const int row = COMP ? ((q & 1) ? NR + (q >> 1) : (q >> 1)) : q;
+                P[(size_t)row * TGT_TILE] = v.x;
+                P[(size_t)row * TGT_TILE + 32] = v.y;
+            }
+            zero_run();
         }
+        if (!has_next) break;
         t = nt;
         k = nk;
-    }
-    // On a timed-out wait: give copies still in flight a bounded chance to land
-    // before the block's shared memory is released.
-    if (outstanding_next && tid == 0) {
-        mbar_wait_bounded(&bars[0], phase0, A.dev_err, WAIT_LIMIT);
-        mbar_wait_bounded(&bars[1], phase1, A.dev_err, WAIT_LIMIT);
     }
 }
 
@@ -477,9 +574,9 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
     const StreamK& sk = E.sk;
     const int t = i / TGT_TILE, l = i % TGT_TILE;
     const int nunits = sk.np + sk.ns;
-    double acc[14];
+    double acc[17];
 #pragma unroll
-    for (int c = 0; c < 14; ++c) acc[c] = 0.0;
+    for (int c = 0; c < 17; ++c) acc[c] = 0.0;
     if (nunits > 0) {
         const int b0 = sk.block_of(sk.unit_start(t, 0));
         const int b1 = sk.block_of(sk.unit_start(t, nunits - 1));
@@ -502,7 +599,7 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
     const EpilogueOut& o = E.o;
     const double u0 = acc[0] * f4pi, u1 = acc[1] * f4pi, u2 = acc[2] * f4pi;
     double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (E.ncomp == 14) {
+    if (E.ncomp >= 14) {
         const double Sx = acc[3], Sy = acc[4], Sz = acc[5];
         const double Gzz = -(acc[6] + acc[10]);
         // J = ([S x] - 3 G') / (4 pi)
@@ -545,10 +642,16 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
                      bt[1][1] * bt[2][2] - bt[1][2] * bt[1][2];
     const double nut = (aa > 0.0 && B > 0.0) ? (double)o.c_v * sqrt(B / aa) : 0.0;
     double s[3];
-    for (int a = 0; a < 3; ++a) {
-        double v = 0.0;
-        for (int c = 0; c < 3; ++c) v += o.classic ? J[3 * a + c] * Gm[c] : J[3 * c + a] * Gm[c];
-        s[a] = v;
+    if (E.ncomp == 17) {  // transposed stretching accumulated per target
+        s[0] = acc[14] * f4pi;
+        s[1] = acc[15] * f4pi;
+        s[2] = acc[16] * f4pi;
+    } else {
+        for (int a = 0; a < 3; ++a) {
+            double v = 0.0;
+            for (int c = 0; c < 3; ++c) v += o.classic ? J[3 * a + c] * Gm[c] : J[3 * c + a] * Gm[c];
+            s[a] = v;
+        }
     }
     o.dxdt[i] = (float)(u0 + o.uinf[0]);
     o.dxdt[E.n + i] = (float)(u1 + o.uinf[1]);
@@ -564,20 +667,30 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
 // Particle strength exchange (Eq. 5's diffusion term):
 //   p_i = (2/sigma^2) sum_j nu_ij (v_i Gamma_j - v_j Gamma_i) zeta_sigma(r_ij),
 //   nu_ij = nu + (nu_t,i + nu_t,j)/2, zeta of Eq. 3.
-// A warp owns 32 consecutive particles; each lane tests one source tile's box
-// against the warp's box and the warp walks the tiles within 7 sigma, reading
-// each source once for all 32 lanes.  v_i Gamma_j - v_j Gamma_i is formed from two
-// rounded products so that the i == j term is exactly zero.
+// A block owns 256 consecutive particles.  It lists, in increasing order, the
+// source tiles whose bounding boxes come within 7 sigma of the block's box (a
+// block-wide ballot scan, so the summation order is fixed), then stages each
+// listed tile (positions, strengths, nu_t) in shared memory and every thread sums
+// over it.  v_i Gamma_j - v_j Gamma_i is formed from two rounded products so that
+// the i == j term is exactly zero; pairs beyond 7 sigma get exp(-r^2/2s^2) < 3e-11
+// and are skipped.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) pse_kernel(const float4* __restrict__ pos, const float4* __restrict__ str,
-                                                  const float* __restrict__ nu_t, int n,
-                                                  const float4* __restrict__ box, int ntiles, float inv2s2,
-                                                  float cut2, float nu, float pref, float* __restrict__ dGdt)
+constexpr int PSE_T = 256;
+
+__global__ void __launch_bounds__(PSE_T) pse_kernel(const float4* __restrict__ pos, const float4* __restrict__ str,
+                                                    const float* __restrict__ nu_t, int n,
+                                                    const float4* __restrict__ box, int ntiles, float inv2s2,
+                                                    float cut2, float nu, float pref, float* __restrict__ dGdt)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x);
+    __shared__ float4 sp[SRC_TILE], sg[SRC_TILE];
+    __shared__ float snt[SRC_TILE];
+    __shared__ int list[PSE_T];
+    __shared__ int wcount[PSE_T / 32];
+    __shared__ float bb[PSE_T / 32][6];
+    __shared__ int nlist;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i = blockIdx.x * PSE_T + tid;
     const bool valid = i < n;
-    if ((blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >= n) return;  // whole warp past the end
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), gi = pi;
     float nti = 0.f;
     if (valid) {
@@ -585,6 +698,7 @@ __global__ void __launch_bounds__(256) pse_kernel(const float4* __restrict__ pos
         gi = str[i];
         nti = nu_t ? nu_t[i] : 0.f;
     }
+    // block bounding box
     float blo[3] = {valid ? pi.x : INFINITY, valid ? pi.y : INFINITY, valid ? pi.z : INFINITY};
     float bhi[3] = {valid ? pi.x : -INFINITY, valid ? pi.y : -INFINITY, valid ? pi.z : -INFINITY};
 #pragma unroll
@@ -594,10 +708,17 @@ __global__ void __launch_bounds__(256) pse_kernel(const float4* __restrict__ pos
             blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
             bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
         }
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) bb[warp][c] = blo[c], bb[warp][3 + c] = bhi[c];
+    __syncthreads();
+    for (int w = 0; w < PSE_T / 32; ++w)
+        for (int c = 0; c < 3; ++c) blo[c] = fminf(blo[c], bb[w][c]), bhi[c] = fmaxf(bhi[c], bb[w][3 + c]);
+
     const float base = nu + 0.5f * nti;
     float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int tb = 0; tb < ntiles; tb += 32) {
-        const int tt = tb + lane;
+    for (int t0 = 0; t0 < ntiles; t0 += PSE_T) {
+        // ordered list of the near tiles among t0 .. t0 + 255
+        const int tt = t0 + tid;
         bool near = false;
         if (tt < ntiles) {
             const float4 tlo = box[2 * tt], thi = box[2 * tt + 1];
@@ -606,25 +727,48 @@ __global__ void __launch_bounds__(256) pse_kernel(const float4* __restrict__ pos
             const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
             near = dx * dx + dy * dy + dz * dz < cut2;
         }
-        unsigned mask = __ballot_sync(0xffffffffu, near);
-        while (mask) {
-            const int tile = tb + __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int j0 = tile * SRC_TILE, j1 = min(n, j0 + SRC_TILE);
-            for (int j = j0; j < j1; ++j) {
-                const float4 pj = __ldg(&pos[j]);
+        const unsigned m = __ballot_sync(0xffffffffu, near);
+        if (lane == 0) wcount[warp] = __popc(m);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int w = 0; w < PSE_T / 32; ++w) {
+                const int c = wcount[w];
+                wcount[w] = acc;
+                acc += c;
+            }
+            nlist = acc;
+        }
+        __syncthreads();
+        if (near) list[wcount[warp] + __popc(m & ((1u << lane) - 1u))] = tt;
+        __syncthreads();
+        const int nl = nlist;
+        for (int q = 0; q < nl; ++q) {
+            const int tile = list[q];
+            const int j0 = tile * SRC_TILE;
+            const int cnt = min(SRC_TILE, n - j0);
+            if (tid < cnt) {
+                sp[tid] = pos[j0 + tid];
+                snt[tid] = nu_t ? nu_t[j0 + tid] : 0.f;
+            } else if (tid >= SRC_TILE && tid - SRC_TILE < cnt) {
+                sg[tid - SRC_TILE] = str[j0 + tid - SRC_TILE];
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 pj = sp[j];
                 const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
-                const float r2 = rx * rx + ry * ry + rz * rz;
+                const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                 if (r2 < cut2) {
-                    const float4 gj = __ldg(&str[j]);
-                    const float ntj = nu_t ? __ldg(&nu_t[j]) : 0.f;
-                    const float w = fmaf(0.5f, ntj, base) * expf(-r2 * inv2s2);
+                    const float4 gj = sg[j];
+                    const float w = fmaf(0.5f, snt[j], base) * expf(-r2 * inv2s2);
                     const float vi = pi.w, vj = pj.w;
                     ax = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x)), ax);
                     ay = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y)), ay);
                     az = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.z), __fmul_rn(vj, gi.z)), az);
                 }
             }
+            __syncthreads();
         }
     }
     if (valid) {
@@ -643,7 +787,8 @@ namespace {
 std::mutex g_mu;
 int g_sm[64];
 int* g_err[64];
-int g_blocks[64][4];
+int g_blocks[64][8];
+bool g_attr[64][8];
 }  // namespace
 
 static int cur_dev()
@@ -679,32 +824,46 @@ int* dev_err_ptr()
     return g_err[d];
 }
 
-template <bool G, bool C>
-static int occ_blocks()
-{
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, C>, TPB, 0) != cudaSuccess) nb = 1;
-    return nb < 1 ? 1 : nb;
-}
+static int variant(bool G, bool C, bool S) { return (G ? 4 : 0) + (C ? 2 : 0) + (S ? 1 : 0); }
 
-int sweep_blocks(bool grad, bool comp)
+// Opts the kernel into its dynamic shared memory (once per device) and returns the resident blocks per SM.
+template <bool G, bool C, bool S>
+static int prepare_kernel(int d)
 {
-    const int d = cur_dev();
-    const int sms = sm_count();
-    const int idx = (grad ? 2 : 0) + (comp ? 1 : 0);
+    const int v = variant(G, C, S);
+    const size_t smem = sweep_smem_bytes<G, C, S>();
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (d >= 0 && d < 64 && g_blocks[d][idx]) return g_blocks[d][idx];
+        if (d >= 0 && d < 64 && g_attr[d][v]) return g_blocks[d][v];
     }
-    int per = grad ? (comp ? occ_blocks<true, true>() : occ_blocks<true, false>())
-                   : (comp ? occ_blocks<false, true>() : occ_blocks<false, false>());
-    const int v = per * (sms > 0 ? sms : 1);
+    cudaFuncSetAttribute(sweep_kernel<G, C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, C, S>, SWEEP_TPB, smem) != cudaSuccess)
+        nb = 1;
+    if (nb < 1) nb = 1;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (d >= 0 && d < 64) g_blocks[d][idx] = v;
-    return v;
+    if (d >= 0 && d < 64) {
+        g_blocks[d][v] = nb;
+        g_attr[d][v] = true;
+    }
+    return nb;
 }
 
-SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv)
+static int blocks_per_sm(bool g, bool c, bool s)
+{
+    const int d = cur_dev();
+    if (g && s) return c ? prepare_kernel<true, true, true>(d) : prepare_kernel<true, false, true>(d);
+    if (g) return c ? prepare_kernel<true, true, false>(d) : prepare_kernel<true, false, false>(d);
+    return c ? prepare_kernel<false, true, false>(d) : prepare_kernel<false, false, false>(d);
+}
+
+int sweep_blocks(bool grad, bool comp, bool stretch)
+{
+    const int sms = sm_count();
+    return blocks_per_sm(grad, comp, stretch && grad) * (sms > 0 ? sms : 1);
+}
+
+SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv, bool stretch)
 {
     SweepPlan p;
     p.n_tgt = (int)n_tgt;
@@ -712,7 +871,8 @@ SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, boo
     p.m_seg = (int)m_seg;
     p.grad = grad;
     p.comp = comp;
-    p.ncomp = grad ? 14 : 3;
+    p.stretch = stretch && grad;
+    p.ncomp = grad ? (p.stretch ? 17 : 14) : 3;
     p.TT = (int)((n_tgt + TGT_TILE - 1) / TGT_TILE);
     p.SP = (int)((n_src + SRC_TILE - 1) / SRC_TILE);
     p.SS = (int)((m_seg + SRC_TILE - 1) / SRC_TILE);
@@ -725,7 +885,7 @@ SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, boo
     sk.C = (long long)sk.np * sk.wp + (long long)sk.ns * sk.ws;
     sk.tot = (long long)sk.TT * sk.C;
     const long long units = (long long)sk.TT * (sk.np + sk.ns);
-    long long B = sweep_blocks(grad, comp);
+    long long B = sweep_blocks(grad, comp, p.stretch);
     if (B > units) B = units;
     if (B < 1) B = 1;
     sk.B = (int)B;
@@ -738,6 +898,12 @@ SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, boo
     return p;
 }
 
+template <bool G, bool C, bool S>
+static void launch_sweep(const SweepArgs& A, int B, cudaStream_t st)
+{
+    sweep_kernel<G, C, S><<<B, SWEEP_TPB, sweep_smem_bytes<G, C, S>(), st>>>(A);
+}
+
 cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const float* src_pos, const float* src_str,
                       const float* seg_a, const float* seg_b, float sigma, float seg_core, int vatistas_n,
                       const EpilogueOut& out, cudaStream_t st)
@@ -747,20 +913,24 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
     float4* pbox = reinterpret_cast<float4*>(ws + p.off_pbox);
     float4* ssrc = reinterpret_cast<float4*>(ws + p.off_ssrc);
     float* part = reinterpret_cast<float*>(ws + p.off_part);
-    if (p.SP > 0) trace_launch();
-    if (p.SP > 0)
+    if (p.SP > 0) {
+        trace_launch();
         pack_particles_kernel<<<p.SP, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(src_pos),
                                                          reinterpret_cast<const float4*>(src_str), p.n_src, psrc,
                                                          pbox);
-    if (p.SS > 0) trace_launch();
-    if (p.SS > 0)
+    }
+    if (p.SS > 0) {
+        trace_launch();
         pack_segments_kernel<<<p.SS, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(seg_a),
                                                         reinterpret_cast<const float4*>(seg_b), p.m_seg, seg_core,
                                                         vatistas_n, ssrc);
+    }
     int* err = dev_err_ptr();
     if (p.SP + p.SS > 0) {
+        blocks_per_sm(p.grad, p.comp, p.stretch);  // ensures the shared-memory opt-in
         SweepArgs A;
         A.tgt = reinterpret_cast<const float4*>(tgt);
+        A.tstr = p.stretch ? reinterpret_cast<const float4*>(out.str) : nullptr;
         A.n_tgt = p.n_tgt;
         A.psrc = psrc;
         A.pbox = pbox;
@@ -778,16 +948,21 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
         A.dev_err = err;
         const int B = p.sk.B;
         TraceScope ts(p.grad ? VPM_TRACE_SWEEP : VPM_TRACE_SWEEP_VEL, st);
-        if (p.grad) {
+        if (p.grad && p.stretch) {
             if (p.comp)
-                sweep_kernel<true, true><<<B, TPB, 0, st>>>(A);
+                launch_sweep<true, true, true>(A, B, st);
             else
-                sweep_kernel<true, false><<<B, TPB, 0, st>>>(A);
+                launch_sweep<true, false, true>(A, B, st);
+        } else if (p.grad) {
+            if (p.comp)
+                launch_sweep<true, true, false>(A, B, st);
+            else
+                launch_sweep<true, false, false>(A, B, st);
         } else {
             if (p.comp)
-                sweep_kernel<false, true><<<B, TPB, 0, st>>>(A);
+                launch_sweep<false, true, false>(A, B, st);
             else
-                sweep_kernel<false, false><<<B, TPB, 0, st>>>(A);
+                launch_sweep<false, false, false>(A, B, st);
         }
     }
     EpiArgs E;
@@ -814,9 +989,9 @@ cudaError_t run_pse(const SweepPlan& p, char* ws, const float* pos, const float*
     // (2/sigma^2) (2 pi sigma^2)^(-3/2)
     const float pref = (float)(2.0 / (s * s) * pow(2.0 * 3.14159265358979323846 * s * s, -1.5));
     TraceScope ts(VPM_TRACE_PSE, st);
-    pse_kernel<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float4*>(pos),
-                                                reinterpret_cast<const float4*>(str), nu_t, n, pbox, p.SP, inv2s2,
-                                                cut2, nu, pref, dGdt);
+    pse_kernel<<<(n + PSE_T - 1) / PSE_T, PSE_T, 0, st>>>(reinterpret_cast<const float4*>(pos),
+                                                          reinterpret_cast<const float4*>(str), nu_t, n, pbox, p.SP,
+                                                          inv2s2, cut2, nu, pref, dGdt);
     return cudaGetLastError();
 }
 
