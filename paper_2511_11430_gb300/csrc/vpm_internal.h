@@ -10,7 +10,7 @@
 
 namespace vpm {
 
-constexpr int SWEEP_CW = 16;                 // consumer warps per sweep block
+constexpr int SWEEP_CW = 15;                 // consumer warps per sweep block (16 warps in all)
 constexpr int SWEEP_TPB = (SWEEP_CW + 1) * 32;  // + one producer warp
 constexpr int TGT_TILE = SWEEP_CW * 64;      // targets per sweep target tile: two per thread
 constexpr int SWEEP_STAGES = 4;              // shared-memory source tiles in flight

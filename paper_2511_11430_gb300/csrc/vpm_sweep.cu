@@ -15,7 +15,7 @@
 // lanes, negated copies included so that every subtraction is an add).  In the
 // sweep block a producer warp streams the tiles into a ring of shared-memory stages
 // with the bulk-copy engine (cp.async.bulk completing on a "full" mbarrier); each of
-// the 16 consumer warps waits on "full", reads every source by broadcast, and
+// the 15 consumer warps waits on "full", reads every source by broadcast, and
 // releases the stage through an "empty" mbarrier, so warps drift freely within the
 // ring and no block-wide barrier sits in the loop.  Work is split stream-K over
 // (target tile, source tile) cost units so every SM gets the same cost however few
@@ -377,7 +377,7 @@ __host__ __device__ constexpr size_t sweep_smem_bytes()
 }
 
 template <bool GRAD, bool COMP, bool STRETCH>
-__global__ void __maxnreg__(120) sweep_kernel(const SweepArgs A)
+__global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
 {
     extern __shared__ __align__(128) float4 dsm[];
     __shared__ __align__(8) uint64_t full[SWEEP_STAGES], empty[SWEEP_STAGES];
