@@ -23,7 +23,7 @@ namespace vpm {
 
 constexpr int A_F4 = 5;  // float4 per packed evaluation point
 constexpr int A_NC = 9;  // accumulators: dG (3), W (3), X3 (3)
-constexpr uint32_t A_WAIT_LIMIT = 1u << 22;
+constexpr uint64_t A_WAIT_LIMIT = 2000000000ull;  // 2 s of wall time
 
 // Packed point (both lanes equal): (yx,yx,yy,yy) (yz,yz,gx,gx) (gy,gy,gz,gz) (-gx,-gx,-gy,-gy) (-gz,-gz,0,0)
 __global__ void __launch_bounds__(SRC_TILE) pack_points_kernel(const float4* __restrict__ tgt,
@@ -94,7 +94,7 @@ __device__ __forceinline__ void adjoint_tile(AdjAcc& a, const float4* __restrict
             near_kh(r2.x, nc, K.x, h.x);
             near_kh(r2.y, nc, K.y, h.y);
         } else {
-            const f2 rs = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const f2 rs = rsqrt2_approx(r2);
             const f2 i2 = mul2(rs, rs);
             K = mul2(i2, rs);
             h = mul2(K, i2);

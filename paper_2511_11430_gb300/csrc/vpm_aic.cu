@@ -122,50 +122,83 @@ __device__ __forceinline__ void argmax_abs_block(float v, int idx, float* sv, in
     __syncthreads();
 }
 
-// Factors columns [k0, k0 + nb) of rows [k0, n) in place (one block); swaps whole rows.
+// Factors columns [k0, k0 + nb) of rows [k0, n) in place with partial pivoting (one
+// block).  The panel is held in shared memory (rows padded to nb + 1 floats) when it
+// fits, else worked on in global memory; only the panel's own columns are swapped
+// here, the other columns by lu_laswp_kernel.
+template <bool SMEM>
 __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(float* __restrict__ A, int n, int k0, int nb,
                                                               int* __restrict__ piv, int* __restrict__ info)
 {
+    extern __shared__ float P[];
     __shared__ float sv[32];
     __shared__ int si[32];
-    for (int j = k0; j < k0 + nb; ++j) {
+    const int rows = n - k0, ld = SMEM ? nb + 1 : n;
+    float* base = SMEM ? P : A + (size_t)k0 * n + k0;
+    if (SMEM) {
+        for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+            const int r = e / nb, c = e % nb;
+            P[r * ld + c] = A[(size_t)(k0 + r) * n + k0 + c];
+        }
+        __syncthreads();
+    }
+    for (int j = 0; j < nb; ++j) {
         float v = -1.f;
         int idx = 0x7fffffff;
-        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-            const float a = fabsf(A[(size_t)i * n + j]);
-            if (a > v || (a == v && i < idx)) v = a, idx = i;
+        for (int r = j + threadIdx.x; r < rows; r += blockDim.x) {
+            const float a = fabsf(base[(size_t)r * ld + j]);
+            if (a > v || (a == v && r < idx)) v = a, idx = r;
         }
         float best;
         int p;
         argmax_abs_block(v, idx, sv, si, best, p);
         if (!(best > 0.f)) {  // exactly singular column (or NaN): keep going, report
             if (threadIdx.x == 0) {
-                piv[j] = j;
-                if (*info == 0) *info = j + 1;
+                piv[k0 + j] = k0 + j;
+                if (*info == 0) *info = k0 + j + 1;
             }
             __syncthreads();
             continue;
         }
-        if (threadIdx.x == 0) piv[j] = p;
-        if (p != j)
-            for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                const float t = A[(size_t)j * n + c];
-                A[(size_t)j * n + c] = A[(size_t)p * n + c];
-                A[(size_t)p * n + c] = t;
-            }
-        __syncthreads();
-        const float inv = 1.0f / A[(size_t)j * n + j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + j] *= inv;
-        __syncthreads();
-        const int ncol = k0 + nb - (j + 1);
-        if (ncol > 0) {
-            const int rows = n - (j + 1);
-            for (int e = threadIdx.x; e < rows * ncol; e += blockDim.x) {
-                const int i = j + 1 + e / ncol, c = j + 1 + e % ncol;
-                A[(size_t)i * n + c] -= A[(size_t)i * n + j] * A[(size_t)j * n + c];
-            }
+        if (threadIdx.x == 0) piv[k0 + j] = k0 + p;
+        if (p != j && threadIdx.x < nb) {
+            const int c = threadIdx.x;
+            const float t = base[(size_t)j * ld + c];
+            base[(size_t)j * ld + c] = base[(size_t)p * ld + c];
+            base[(size_t)p * ld + c] = t;
         }
         __syncthreads();
+        const float inv = 1.0f / base[(size_t)j * ld + j];
+        for (int r = j + 1 + threadIdx.x; r < rows; r += blockDim.x) {
+            float* row = base + (size_t)r * ld;
+            const float l = row[j] * inv;
+            row[j] = l;
+            for (int c = j + 1; c < nb; ++c) row[c] = fmaf(-l, base[(size_t)j * ld + c], row[c]);
+        }
+        __syncthreads();
+    }
+    if (SMEM) {
+        for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+            const int r = e / nb, c = e % nb;
+            A[(size_t)(k0 + r) * n + k0 + c] = P[r * ld + c];
+        }
+    }
+}
+
+// Applies the row exchanges of panel [k0, k0 + nb) to every column outside it.
+__global__ void __launch_bounds__(256) lu_laswp_kernel(float* __restrict__ A, int n, int k0, int nb,
+                                                       const int* __restrict__ piv)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n - nb) return;
+    if (c >= k0) c += nb;
+    for (int j = k0; j < k0 + nb; ++j) {
+        const int p = piv[j];
+        if (p != j) {
+            const float t = A[(size_t)j * n + c];
+            A[(size_t)j * n + c] = A[(size_t)p * n + c];
+            A[(size_t)p * n + c] = t;
+        }
     }
 }
 
@@ -234,13 +267,15 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
     }
 }
 
-// Solves (LU) z = P r in FP32 for a FP64 right-hand side, one block; z returned in FP64.
+// Solves (LU) z = P r in FP32 for a FP64 right-hand side, one block, the vector in
+// shared memory; z returned in FP64.  Each 32-row diagonal block is solved by one
+// warp, then every thread updates one remaining row with a 32-long dot product.
 __global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __restrict__ LU,
                                                               const int* __restrict__ piv, int n,
-                                                              const double* __restrict__ rhs, float* __restrict__ y,
-                                                              double* __restrict__ z)
+                                                              const double* __restrict__ rhs, double* __restrict__ z)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    extern __shared__ float y[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < n; i += blockDim.x) y[i] = (float)rhs[i];
     __syncthreads();
     if (tid == 0)
@@ -258,17 +293,30 @@ __global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __res
         const int bn = min(32, n - b0);
         if (warp == 0) {
             float v = lane < bn ? y[b0 + lane] : 0.f;
-            for (int p = 0; p < bn; ++p) {
+            const float* row = LU + (size_t)(b0 + (lane < bn ? lane : 0)) * n + b0;
+            float lr[32];
+#pragma unroll
+            for (int p = 0; p < 32; ++p) lr[p] = p < bn ? row[p] : 0.f;  // all loads in flight at once
+#pragma unroll
+            for (int p = 0; p < 32; ++p) {
                 const float yp = __shfl_sync(0xffffffffu, v, p);
-                if (lane > p && lane < bn) v -= LU[(size_t)(b0 + lane) * n + b0 + p] * yp;
+                if (lane > p && lane < bn) v = fmaf(-lr[p], yp, v);
             }
             if (lane < bn) y[b0 + lane] = v;
         }
         __syncthreads();
-        for (int i = b0 + bn + warp; i < n; i += nw) {
-            float s = lane < bn ? LU[(size_t)i * n + b0 + lane] * y[b0 + lane] : 0.f;
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[i] -= s;
+        for (int i = b0 + bn + tid; i < n; i += blockDim.x) {
+            const float* row = LU + (size_t)i * n + b0;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int p = 0;
+            for (; p + 4 <= bn; p += 4) {
+                s0 = fmaf(row[p], y[b0 + p], s0);
+                s1 = fmaf(row[p + 1], y[b0 + p + 1], s1);
+                s2 = fmaf(row[p + 2], y[b0 + p + 2], s2);
+                s3 = fmaf(row[p + 3], y[b0 + p + 3], s3);
+            }
+            for (; p < bn; ++p) s0 = fmaf(row[p], y[b0 + p], s0);
+            y[i] -= (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
     }
@@ -277,18 +325,33 @@ __global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __res
         const int b0 = max(0, b1 - 32), bn = b1 - b0;
         if (warp == 0) {
             float v = lane < bn ? y[b0 + lane] : 0.f;
-            for (int p = bn - 1; p >= 0; --p) {
-                if (lane == p) v /= LU[(size_t)(b0 + p) * n + b0 + p];
-                const float yp = __shfl_sync(0xffffffffu, v, p);
-                if (lane < p) v -= LU[(size_t)(b0 + lane) * n + b0 + p] * yp;
+            const float* row = LU + (size_t)(b0 + (lane < bn ? lane : 0)) * n + b0;
+            float lr[32];
+#pragma unroll
+            for (int p = 0; p < 32; ++p) lr[p] = p < bn ? row[p] : 1.f;
+#pragma unroll
+            for (int p = 31; p >= 0; --p) {
+                if (p < bn) {
+                    if (lane == p) v /= lr[p];
+                    const float yp = __shfl_sync(0xffffffffu, v, p);
+                    if (lane < p) v = fmaf(-lr[p], yp, v);
+                }
             }
             if (lane < bn) y[b0 + lane] = v;
         }
         __syncthreads();
-        for (int i = warp; i < b0; i += nw) {
-            float s = lane < bn ? LU[(size_t)i * n + b0 + lane] * y[b0 + lane] : 0.f;
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[i] -= s;
+        for (int i = tid; i < b0; i += blockDim.x) {
+            const float* row = LU + (size_t)i * n + b0;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int p = 0;
+            for (; p + 4 <= bn; p += 4) {
+                s0 = fmaf(row[p], y[b0 + p], s0);
+                s1 = fmaf(row[p + 1], y[b0 + p + 1], s1);
+                s2 = fmaf(row[p + 2], y[b0 + p + 2], s2);
+                s3 = fmaf(row[p + 3], y[b0 + p + 3], s3);
+            }
+            for (; p < bn; ++p) s0 = fmaf(row[p], y[b0 + p], s0);
+            y[i] -= (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
     }
@@ -357,7 +420,7 @@ __global__ void add_kernel(double* __restrict__ x, const double* __restrict__ d,
 
 namespace {
 struct AicWs {
-    size_t lu, piv, info, r, d, rowabs, norms, y, bytes;
+    size_t lu, piv, info, r, d, rowabs, norms, bytes;
 };
 AicWs aic_layout(int n)
 {
@@ -370,7 +433,6 @@ AicWs aic_layout(int n)
     w.d = cv.take((size_t)n * sizeof(double));
     w.rowabs = cv.take((size_t)n * sizeof(double));
     w.norms = cv.take(4 * sizeof(double));
-    w.y = cv.take((size_t)n * sizeof(float));
     w.bytes = cv.off;
     return w;
 }
@@ -392,7 +454,6 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     double* d = reinterpret_cast<double*>(ws + L.d);
     double* rowabs = reinterpret_cast<double*>(ws + L.rowabs);
     double* norms = reinterpret_cast<double*>(ws + L.norms);
-    float* y = reinterpret_cast<float*>(ws + L.y);
 #define VPM_CU(call)                                 \
     do {                                             \
         if ((call) != cudaSuccess) {                 \
@@ -402,10 +463,27 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     } while (0)
     VPM_CU(cudaMemcpyAsync(LU, A, (size_t)n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
     VPM_CU(cudaMemsetAsync(info, 0, sizeof(int), st));
-    for (int k0 = 0; k0 < n; k0 += NB) {
-        const int nb = n - k0 < NB ? n - k0 : NB;
+    // panel width 32 when the panel fits in shared memory, else 16, else a global-memory panel
+    const int maxsm = 200 * 1024;
+    const int pnb = ((size_t)n * 33 * sizeof(float) <= (size_t)maxsm) ? 32 : 16;
+    const bool psmem = (size_t)n * (pnb + 1) * sizeof(float) <= (size_t)maxsm;
+    if (psmem) {
+        VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    }
+    VPM_CU(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(n * sizeof(float))));
+    for (int k0 = 0; k0 < n; k0 += pnb) {
+        const int nb = n - k0 < pnb ? n - k0 : pnb;
         trace_launch();
-        lu_panel_kernel<<<1, LU_THREADS, 0, st>>>(LU, n, k0, nb, piv, info);
+        if (psmem)
+            lu_panel_kernel<true><<<1, LU_THREADS, (size_t)(n - k0) * (nb + 1) * sizeof(float), st>>>(LU, n, k0, nb,
+                                                                                                     piv, info);
+        else
+            lu_panel_kernel<false><<<1, LU_THREADS, 0, st>>>(LU, n, k0, nb, piv, info);
+        if (n - nb > 0) {
+            trace_launch();
+            lu_laswp_kernel<<<(n - nb + 255) / 256, 256, 0, st>>>(LU, n, k0, nb, piv);
+        }
         const int rest = n - k0 - nb;
         if (rest > 0) {
             trace_launch();
@@ -424,7 +502,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         return VPM_ERR_NOT_CONVERGED;
     }
     trace_launch();
-    lu_solve_kernel<<<1, LU_THREADS, 0, st>>>(LU, piv, n, b, y, x);
+    lu_solve_kernel<<<1, LU_THREADS, n * sizeof(float), st>>>(LU, piv, n, b, x);
     double h[4];
     double best = INFINITY;
     for (int it = 0;; ++it) {
@@ -446,7 +524,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
             return VPM_ERR_NOT_CONVERGED;
         }
         trace_launch();
-        lu_solve_kernel<<<1, LU_THREADS, 0, st>>>(LU, piv, n, r, y, d);
+        lu_solve_kernel<<<1, LU_THREADS, n * sizeof(float), st>>>(LU, piv, n, r, d);
         trace_launch();
         add_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, d, n);
     }

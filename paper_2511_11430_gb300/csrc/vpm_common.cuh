@@ -100,25 +100,38 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+// One potentially blocking probe of a barrier phase: the hardware may suspend the
+// thread for up to `hint_ns` until the phase completes, so waiting warps do not
+// spin on the issue slots.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, uint32_t hint_ns)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait for a phase of `bar`.  Returns false (and latches the device
-// error word) if the phase has not completed after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* dev_err, uint32_t limit)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (uint32_t it = 0; it < limit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for a phase of `bar`: gives up (latching the device error word)
+// once `limit_ns` of wall time has passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* dev_err, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity, 100000u)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity, 100000u)) return true;
+        if (global_ns() - t0 > limit_ns) break;
     }
     atomicOr(dev_err, DEV_ERR_TIMEOUT);
     return false;

@@ -48,7 +48,7 @@ struct SweepPlan {
     bool stretch = false;  // accumulate the transposed stretching J^T Gamma_i per target
     int ncomp = 0;         // logical accumulator rows (3, 14 or 17)
     StreamK sk{};
-    size_t off_psrc = 0, off_pbox = 0, off_ssrc = 0, off_part = 0, bytes = 0;
+    size_t off_psrc = 0, off_pbox = 0, off_ssrc = 0, off_sbox = 0, off_part = 0, bytes = 0;
 };
 
 // Plans a particle + segment sweep onto `n_tgt` targets starting at offset `base`

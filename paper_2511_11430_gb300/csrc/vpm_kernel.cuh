@@ -51,6 +51,34 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 
+// 1/x of both lanes of a packed pair.
+__device__ __forceinline__ float2 rcp2_approx(float2 x)
+{
+    unsigned long long in = *reinterpret_cast<unsigned long long*>(&x), out;
+    asm("{\n\t.reg .f32 a, b;\n\t"
+        "mov.b64 {a, b}, %1;\n\t"
+        "rcp.approx.ftz.f32 a, a;\n\t"
+        "rcp.approx.ftz.f32 b, b;\n\t"
+        "mov.b64 %0, {a, b};\n\t}"
+        : "=l"(out)
+        : "l"(in));
+    return *reinterpret_cast<float2*>(&out);
+}
+
+// rsqrt of both lanes of a packed pair, produced directly into a register pair.
+__device__ __forceinline__ float2 rsqrt2_approx(float2 x)
+{
+    unsigned long long in = *reinterpret_cast<unsigned long long*>(&x), out;
+    asm("{\n\t.reg .f32 a, b;\n\t"
+        "mov.b64 {a, b}, %1;\n\t"
+        "rsqrt.approx.ftz.f32 a, a;\n\t"
+        "rsqrt.approx.ftz.f32 b, b;\n\t"
+        "mov.b64 %0, {a, b};\n\t}"
+        : "=l"(out)
+        : "l"(in));
+    return *reinterpret_cast<float2*>(&out);
+}
+
 // K (without 1/(4 pi)) and h = H * (-1/3) (without 1/(4 pi)) of one pair; in the far
 // field K = r^-3 and h = r^-5.  A pair at zero distance contributes nothing.
 __device__ __forceinline__ void near_kh(float r2, const NearConst& nc, float& K, float& h)

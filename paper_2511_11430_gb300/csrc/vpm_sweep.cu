@@ -54,7 +54,7 @@ struct Acc {
 
 // The target's own strength, for the stretching terms.
 struct Own {
-    f2 gx, gy, gz, ngx, ngy, ngz;
+    f2 gx, gy, gz;
 };
 
 template <bool GRAD, bool STRETCH, bool NEAR>
@@ -86,16 +86,16 @@ __device__ __forceinline__ void accum_particle(Acc<GRAD, STRETCH>& a, f2 K, f2 h
         // when the strengths are close) so that nothing cancels:
         //   K (Gamma_i x Gamma_j) = K (Gamma_i x d),
         //   -3 h ((Gamma_j x r) . Gamma_i) r = 3 h (d . (Gamma_i x r)) r.
-        const f2 dx = add2(gx, o.ngx), dy = add2(gy, o.ngy), dz = add2(gz, o.ngz);
-        const f2 tx = fma2(o.gy, dz, mul2(o.ngz, dy));
-        const f2 ty = fma2(o.gz, dx, mul2(o.ngx, dz));
-        const f2 tz = fma2(o.gx, dy, mul2(o.ngy, dx));
+        const f2 dx = sub2(gx, o.gx), dy = sub2(gy, o.gy), dz = sub2(gz, o.gz);
+        const f2 tx = sub2(mul2(o.gy, dz), mul2(o.gz, dy));
+        const f2 ty = sub2(mul2(o.gz, dx), mul2(o.gx, dz));
+        const f2 tz = sub2(mul2(o.gx, dy), mul2(o.gy, dx));
         a.v[14] = fma2(K, tx, a.v[14]);
         a.v[15] = fma2(K, ty, a.v[15]);
         a.v[16] = fma2(K, tz, a.v[16]);
-        const f2 ex = fma2(o.gy, rz, mul2(o.ngz, ry));
-        const f2 ey = fma2(o.gz, rx, mul2(o.ngx, rz));
-        const f2 ez = fma2(o.gx, ry, mul2(o.ngy, rx));
+        const f2 ex = sub2(mul2(o.gy, rz), mul2(o.gz, ry));
+        const f2 ey = sub2(mul2(o.gz, rx), mul2(o.gx, rz));
+        const f2 ez = sub2(mul2(o.gx, ry), mul2(o.gy, rx));
         const f2 w = mul2(mul2(h, splat(3.f)), fma2(dz, ez, fma2(dy, ey, mul2(dx, ex))));
         a.v[14] = fma2(w, rx, a.v[14]);
         a.v[15] = fma2(w, ry, a.v[15]);
@@ -122,7 +122,7 @@ __device__ __forceinline__ void particle_tile(Acc<GRAD, STRETCH>& a, const float
             near_kh(r2.x, nc, K.x, h.x);
             near_kh(r2.y, nc, K.y, h.y);
         } else {
-            const f2 rs = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const f2 rs = rsqrt2_approx(r2);
             const f2 i2 = mul2(rs, rs);
             K = mul2(i2, rs);
             h = GRAD ? mul2(K, i2) : K;
@@ -177,11 +177,14 @@ __device__ __forceinline__ void seg_lane(float n1, float n2, float c2, float L2,
 //   grad d = (r1/|r1|^3 - r2/|r2|^3) x c   (the projections of r0 normal to r1, r2),
 //   grad D / D = 2 |c|^(2n-2) D^(-n) (c x r0),   so  w = (r1/|r1|^3 - r2/|r2|^3 + k3 r0) x c
 //   with k3 = 2 d |c|^(2n-2) D^(-n).
-template <bool GRAD, bool STRETCH>
+// SAFE: the warp's targets are at least 1e-3 of the longest segment away from the
+// tile's bounding box and the core is positive, so no guard can trigger and every
+// reciprocal is taken on both lanes at once.
+template <bool GRAD, bool STRETCH, bool SAFE>
 __device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y,
                                              f2 Z, int vn)
 {
-#pragma unroll 1
+#pragma unroll 2
     for (int j = 0; j < cnt; ++j) {
         const float4* e4 = s + j * S_F4;
         const float4 s0 = e4[0], s1 = e4[1], s2 = e4[2], s3 = e4[3], s4 = e4[4], s5 = e4[5];
@@ -200,8 +203,16 @@ __device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4
         const f2 p1 = fma2(r0z, r1z, fma2(r0y, r1y, mul2(r0x, r1x)));
         const f2 c2 = fma2(cz, cz, fma2(cy, cy, mul2(cx, cx)));
         f2 i1, i2, irs, invD;
-        seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, irs.x, invD.x);
-        seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, irs.y, invD.y);
+        if (SAFE) {
+            i1 = rsqrt2_approx(n1);
+            i2 = rsqrt2_approx(n2);
+            const f2 e = make_float2(s5.z, s5.w);
+            invD = vn == 2 ? rsqrt2_approx(fma2(c2, c2, e)) : rcp2_approx(add2(c2, e));
+            irs = rcp2_approx(fma2(n1, i1, mul2(n2, i2)));
+        } else {
+            seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, irs.x, invD.x);
+            seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, irs.y, invD.y);
+        }
         const f2 L2 = mul2(nL2, splat(-1.f));
         const f2 di = mul2(mul2(fma2(splat(-2.f), p1, L2), mul2(i1, i2)), irs);  // 1/|r1| - 1/|r2|
         const f2 d = fma2(p1, di, mul2(L2, i2));
@@ -257,9 +268,9 @@ __device__ __forceinline__ void stretch_from_tile(Acc<GRAD, STRETCH>& a, const O
     const f2 Gzz = mul2(add2(Gxx, Gyy), splat(-1.f));
     const f2 m3 = splat(-3.f);
     // Gamma_i x S - 3 G'^T Gamma_i
-    const f2 tx = fma2(o.gy, Sz, mul2(o.ngz, Sy));
-    const f2 ty = fma2(o.gz, Sx, mul2(o.ngx, Sz));
-    const f2 tz = fma2(o.gx, Sy, mul2(o.ngy, Sx));
+    const f2 tx = sub2(mul2(o.gy, Sz), mul2(o.gz, Sy));
+    const f2 ty = sub2(mul2(o.gz, Sx), mul2(o.gx, Sz));
+    const f2 tz = sub2(mul2(o.gx, Sy), mul2(o.gy, Sx));
     const f2 gx = fma2(Gzx, o.gz, fma2(Gyx, o.gy, mul2(Gxx, o.gx)));
     const f2 gy = fma2(Gzy, o.gz, fma2(Gyy, o.gy, mul2(Gxy, o.gx)));
     const f2 gz = fma2(Gzz, o.gz, fma2(Gyz, o.gy, mul2(Gxz, o.gx)));
@@ -313,11 +324,13 @@ __global__ void __launch_bounds__(SRC_TILE) pack_particles_kernel(const float4* 
 
 __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* __restrict__ sa,
                                                                  const float4* __restrict__ sb, int m, float core,
-                                                                 int vn, float4* __restrict__ out)
+                                                                 int vn, float4* __restrict__ out,
+                                                                 float4* __restrict__ box)
 {
     const int j = blockIdx.x * SRC_TILE + threadIdx.x;
+    const bool valid = j < m;
     float ax = 0.f, ay = 0.f, az = 0.f, rx = 1.f, ry = 0.f, rz = 0.f, g = 0.f;
-    if (j < m) {
+    if (valid) {
         const float4 a = sa[j], b = sb[j];
         ax = a.x, ay = a.y, az = a.z;
         rx = b.x - a.x, ry = b.y - a.y, rz = b.z - a.z;
@@ -333,6 +346,34 @@ __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* _
     o[3] = make_float4(-rx, -rx, -ry, -ry);
     o[4] = make_float4(-rz, -rz, -L2, -L2);
     o[5] = make_float4(g, g, e, e);
+    // tile box of both end points, and the longest segment (in lo.w)
+    const float bx = ax + rx, by = ay + ry, bz = az + rz;
+    float lo[4] = {valid ? fminf(ax, bx) : INFINITY, valid ? fminf(ay, by) : INFINITY,
+                   valid ? fminf(az, bz) : INFINITY, valid ? -sqrtf(L2) : 0.f};
+    float hi[3] = {valid ? fmaxf(ax, bx) : -INFINITY, valid ? fmaxf(ay, by) : -INFINITY,
+                   valid ? fmaxf(az, bz) : -INFINITY};
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o2));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o2));
+    }
+    __shared__ float sbx[SRC_TILE / 32][7];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        for (int c = 0; c < 4; ++c) sbx[w][c] = lo[c];
+        for (int c = 0; c < 3; ++c) sbx[w][4 + c] = hi[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int ww = 1; ww < SRC_TILE / 32; ++ww) {
+            for (int c = 0; c < 4; ++c) lo[c] = fminf(lo[c], sbx[ww][c]);
+            for (int c = 0; c < 3; ++c) hi[c] = fmaxf(hi[c], sbx[ww][4 + c]);
+        }
+        box[2 * blockIdx.x] = make_float4(lo[0], lo[1], lo[2], -lo[3]);
+        box[2 * blockIdx.x + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -346,16 +387,18 @@ struct SweepArgs {
     const float4* pbox;
     int n_src;
     const float4* ssrc;
+    const float4* sbox;
     int m_seg;
     int vn;
+    int core_pos;  // the segment core is > 0
     StreamK sk;
     NearConst nc;
     float* part;
     int* dev_err;
 };
 
-constexpr int BUF_F4 = SRC_TILE * S_F4;  // the larger of the two tile formats
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int BUF_F4 = SRC_TILE * S_F4 + 2;  // the larger tile format + the tile's bounding box
+constexpr uint64_t WAIT_LIMIT = 2000000000ull;  // 2 s of wall time
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -426,8 +469,15 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
                 bytes = SRC_TILE * S_F4 * 16;
             }
             fence_proxy_async_smem();
-            mbar_expect_tx(&full[s], bytes);
-            bulk_g2s(stage + (size_t)s * BUF_F4, src, bytes, &full[s]);
+            if (k < sk.np) {
+                mbar_expect_tx(&full[s], bytes + 32);
+                bulk_g2s(stage + (size_t)s * BUF_F4, src, bytes, &full[s]);
+                bulk_g2s(stage + (size_t)s * BUF_F4 + SRC_TILE * S_F4, A.pbox + 2 * k, 32, &full[s]);
+            } else {
+                mbar_expect_tx(&full[s], bytes + 32);
+                bulk_g2s(stage + (size_t)s * BUF_F4, src, bytes, &full[s]);
+                bulk_g2s(stage + (size_t)s * BUF_F4 + SRC_TILE * S_F4, A.sbox + 2 * (k - sk.np), 32, &full[s]);
+            }
             issued = i + 1;
             if (++k == nunits) {
                 k = 0;
@@ -446,7 +496,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
     // ---------------- consumers ----------------
     const int ct = warp * 32 + lane;  // consumer thread index
     Acc<GRAD, STRETCH> acc;
-    Own own{zero2(), zero2(), zero2(), zero2(), zero2(), zero2()};
+    Own own{zero2(), zero2(), zero2()};
     f2 X = zero2(), Y = zero2(), Z = zero2();
     float blo[3], bhi[3];
     int t = t0, k = k0, cur_t = -1;
@@ -480,9 +530,6 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
                 own.gx = make_float2(g0.x, g1.x);
                 own.gy = make_float2(g0.y, g1.y);
                 own.gz = make_float2(g0.z, g1.z);
-                own.ngx = mul2(own.gx, splat(-1.f));
-                own.ngy = mul2(own.gy, splat(-1.f));
-                own.ngz = mul2(own.gz, splat(-1.f));
             }
             blo[0] = v0 ? p0.x : INFINITY, blo[1] = v0 ? p0.y : INFINITY, blo[2] = v0 ? p0.z : INFINITY;
             bhi[0] = v0 ? p0.x : -INFINITY, bhi[1] = v0 ? p0.y : -INFINITY, bhi[2] = v0 ? p0.z : -INFINITY;
@@ -505,7 +552,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
         bool near_tile = false;
         if (k < sk.np) {
             const int cnt = min(SRC_TILE, A.n_src - k * SRC_TILE);
-            const float4 tlo = A.pbox[2 * k], thi = A.pbox[2 * k + 1];
+            const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
             const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
             const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
             const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
@@ -516,7 +563,15 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
                 particle_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.nc, own);
         } else {
             const int cnt = min(SRC_TILE, A.m_seg - (k - sk.np) * SRC_TILE);
-            segment_tile<GRAD, STRETCH>(acc, src, cnt, X, Y, Z, A.vn);
+            const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
+            const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
+            const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
+            const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
+            const float margin = 1e-3f * tlo.w;
+            if (A.core_pos && dx * dx + dy * dy + dz * dz > margin * margin)
+                segment_tile<GRAD, STRETCH, true>(acc, src, cnt, X, Y, Z, A.vn);
+            else
+                segment_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.vn);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);  // stage s may be refilled
@@ -892,6 +947,7 @@ SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, boo
     p.off_psrc = cv.take((size_t)p.SP * SRC_TILE * P_F4 * 16);
     p.off_pbox = cv.take((size_t)p.SP * 2 * 16);
     p.off_ssrc = cv.take((size_t)p.SS * SRC_TILE * S_F4 * 16);
+    p.off_sbox = cv.take((size_t)p.SS * 2 * 16);
     const size_t rows = (size_t)(comp ? 2 : 1) * p.ncomp;
     p.off_part = cv.take((size_t)(sk.TT + sk.B) * rows * TGT_TILE * sizeof(float));
     p.bytes = cv.off;
@@ -912,6 +968,7 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
     float4* psrc = reinterpret_cast<float4*>(ws + p.off_psrc);
     float4* pbox = reinterpret_cast<float4*>(ws + p.off_pbox);
     float4* ssrc = reinterpret_cast<float4*>(ws + p.off_ssrc);
+    float4* sbox = reinterpret_cast<float4*>(ws + p.off_sbox);
     float* part = reinterpret_cast<float*>(ws + p.off_part);
     if (p.SP > 0) {
         trace_launch();
@@ -923,7 +980,7 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
         trace_launch();
         pack_segments_kernel<<<p.SS, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(seg_a),
                                                         reinterpret_cast<const float4*>(seg_b), p.m_seg, seg_core,
-                                                        vatistas_n, ssrc);
+                                                        vatistas_n, ssrc, sbox);
     }
     int* err = dev_err_ptr();
     if (p.SP + p.SS > 0) {
@@ -936,6 +993,8 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
         A.pbox = pbox;
         A.n_src = p.n_src;
         A.ssrc = ssrc;
+        A.sbox = sbox;
+        A.core_pos = seg_core > 0.f ? 1 : 0;
         A.m_seg = p.m_seg;
         A.vn = vatistas_n;
         A.sk = p.sk;
