@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(TPB, 1) adjoint_kernel(const AdjArgs A)
     constexpr int BUF = SRC_TILE * A_F4;
     __shared__ __align__(128) float4 sbuf[2][BUF];
     __shared__ __align__(8) uint64_t bars[2];
-    __shared__ float wbox[TPB / 32][6];
+    __shared__ float wbox[TPB / 32][12];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const StreamK& sk = A.sk;
@@ -193,22 +193,7 @@ __global__ void __launch_bounds__(TPB, 1) adjoint_kernel(const AdjArgs A)
             GX = make_float2(g0.x, g1.x);
             GY = make_float2(g0.y, g1.y);
             GZ = make_float2(g0.z, g1.z);
-            float blo[3] = {v0 ? p0.x : INFINITY, v0 ? p0.y : INFINITY, v0 ? p0.z : INFINITY};
-            float bhi[3] = {v0 ? p0.x : -INFINITY, v0 ? p0.y : -INFINITY, v0 ? p0.z : -INFINITY};
-            if (v1) {
-                blo[0] = fminf(blo[0], p1.x), blo[1] = fminf(blo[1], p1.y), blo[2] = fminf(blo[2], p1.z);
-                bhi[0] = fmaxf(bhi[0], p1.x), bhi[1] = fmaxf(bhi[1], p1.y), bhi[2] = fmaxf(bhi[2], p1.z);
-            }
-#pragma unroll
-            for (int o2 = 16; o2 > 0; o2 >>= 1)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
-                    bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
-                }
-            if (lane == 0)
-                for (int c = 0; c < 3; ++c) wbox[warp][c] = blo[c], wbox[warp][3 + c] = bhi[c];
-            __syncwarp();
+            warp_two_boxes(make_float3(p0.x, p0.y, p0.z), v0, make_float3(p1.x, p1.y, p1.z), v1, wbox[warp]);
         }
         const bool ok = mbar_wait_bounded(&bars[slot], slot ? ph1 : ph0, A.dev_err, A_WAIT_LIMIT);
         if (slot)
@@ -220,11 +205,8 @@ __global__ void __launch_bounds__(TPB, 1) adjoint_kernel(const AdjArgs A)
         const float4* s = &sbuf[slot][0];
         const int cnt = min(SRC_TILE, A.n_pts - k * SRC_TILE);
         const float4 tlo = A.pbox[2 * k], thi = A.pbox[2 * k + 1];
-        const float dx = fmaxf(0.f, fmaxf(tlo.x - wbox[warp][3], wbox[warp][0] - thi.x));
-        const float dy = fmaxf(0.f, fmaxf(tlo.y - wbox[warp][4], wbox[warp][1] - thi.y));
-        const float dz = fmaxf(0.f, fmaxf(tlo.z - wbox[warp][5], wbox[warp][2] - thi.z));
         const f2 NGX = mul2(GX, splat(-1.f)), NGY = mul2(GY, splat(-1.f)), NGZ = mul2(GZ, splat(-1.f));
-        if (dx * dx + dy * dy + dz * dz < A.nc.far2)
+        if (boxes_near(wbox[warp], tlo, thi, A.nc.far2))
             adjoint_tile<true>(acc, s, cnt, NX, NY, NZ, GX, GY, GZ, NGX, NGY, NGZ, A.nc);
         else
             adjoint_tile<false>(acc, s, cnt, NX, NY, NZ, GX, GY, GZ, NGX, NGY, NGZ, A.nc);

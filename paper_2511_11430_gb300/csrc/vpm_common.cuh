@@ -138,6 +138,80 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------------------
+// Target boxes for the near/far test.  A warp's 64 targets (lane l holds index l
+// in p0 and 32 + l in p1) are split at the largest jump between index-consecutive
+// targets into two groups with one bounding box each, so that a warp straddling
+// two distant runs of particles (say the end of one tip-vortex spiral and the
+// start of the next) does not get one box spanning everything.  Boxes go to
+// out[12] = {loA, hiA, loB, hiB} (xyz each); an empty group has lo = +inf.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_two_boxes(float3 p0, bool v0, float3 p1, bool v1, float* out)
+{
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float3 n0, n1;
+    n0.x = __shfl_down_sync(F, p0.x, 1), n0.y = __shfl_down_sync(F, p0.y, 1), n0.z = __shfl_down_sync(F, p0.z, 1);
+    const float q0x = __shfl_sync(F, p1.x, 0), q0y = __shfl_sync(F, p1.y, 0), q0z = __shfl_sync(F, p1.z, 0);
+    const bool nv0d = __shfl_down_sync(F, (int)v0, 1) != 0, q0v = __shfl_sync(F, (int)v1, 0) != 0;
+    n1.x = __shfl_down_sync(F, p1.x, 1), n1.y = __shfl_down_sync(F, p1.y, 1), n1.z = __shfl_down_sync(F, p1.z, 1);
+    const bool nv1d = __shfl_down_sync(F, (int)v1, 1) != 0;
+    if (lane == 31) n0 = make_float3(q0x, q0y, q0z);
+    const bool nv0 = lane == 31 ? q0v : nv0d;
+    const bool nv1 = lane == 31 ? false : nv1d;
+    float g0 = -1.f, g1 = -1.f;
+    if (v0 && nv0) {
+        const float dx = p0.x - n0.x, dy = p0.y - n0.y, dz = p0.z - n0.z;
+        g0 = dx * dx + dy * dy + dz * dz;
+    }
+    if (v1 && nv1) {
+        const float dx = p1.x - n1.x, dy = p1.y - n1.y, dz = p1.z - n1.z;
+        g1 = dx * dx + dy * dy + dz * dz;
+    }
+    float g = g0;
+    int k = lane;
+    if (g1 > g) g = g1, k = 32 + lane;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float og = __shfl_xor_sync(F, g, o);
+        const int ok = __shfl_xor_sync(F, k, o);
+        if (og > g || (og == g && ok < k)) g = og, k = ok;
+    }
+    // target index t goes to group A when t <= k (k = -1 would put all in B)
+    const int ks = g >= 0.f ? k : -1;
+    const float I = INFINITY;
+    const bool a0 = v0 && lane <= ks, b0 = v0 && lane > ks;
+    const bool a1 = v1 && 32 + lane <= ks, b1 = v1 && 32 + lane > ks;
+    float lo[2][3], hi[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float x0 = c == 0 ? p0.x : (c == 1 ? p0.y : p0.z);
+        const float x1 = c == 0 ? p1.x : (c == 1 ? p1.y : p1.z);
+        lo[0][c] = fminf(a0 ? x0 : I, a1 ? x1 : I);
+        hi[0][c] = fmaxf(a0 ? x0 : -I, a1 ? x1 : -I);
+        lo[1][c] = fminf(b0 ? x0 : I, b1 ? x1 : I);
+        hi[1][c] = fmaxf(b0 ? x0 : -I, b1 ? x1 : -I);
+    }
+    if (lane == 0)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 3; ++c) out[6 * b + c] = lo[b][c], out[6 * b + 3 + c] = hi[b][c];
+    __syncwarp();
+}
+
+// Squared distance between box [lo, hi] and the tile box [tlo, thi] (0 when they overlap).
+__device__ __forceinline__ float box_dist2(const float* lo, const float* hi, float4 tlo, float4 thi)
+{
+    const float dx = fmaxf(0.f, fmaxf(tlo.x - hi[0], lo[0] - thi.x));
+    const float dy = fmaxf(0.f, fmaxf(tlo.y - hi[1], lo[1] - thi.y));
+    const float dz = fmaxf(0.f, fmaxf(tlo.z - hi[2], lo[2] - thi.z));
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Whether a tile box comes within sqrt(r2) of either of a warp's two boxes.
+__device__ __forceinline__ bool boxes_near(const float* b12, float4 tlo, float4 thi, float r2)
+{
+    return box_dist2(b12, b12 + 3, tlo, thi) < r2 || box_dist2(b12 + 6, b12 + 9, tlo, thi) < r2;
+}
+
+// ---------------------------------------------------------------------------
 // Stream-K work split.  A sweep is a grid of (target tile t, source unit k)
 // pairs; unit k < np is a particle tile of cost wp, else a segment tile of cost
 // ws.  The cost line [0, TT*C) is cut into B equal ranges, block b owning the

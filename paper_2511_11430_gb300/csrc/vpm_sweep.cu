@@ -19,10 +19,10 @@
 // releases the stage through an "empty" mbarrier, so warps drift freely within the
 // ring and no block-wide barrier sits in the loop.  Work is split stream-K over
 // (target tile, source tile) cost units so every SM gets the same cost however few
-// targets there are.  Far from a warp's 64 targets (bounding boxes more than 7 sigma
-// apart) the blob kernel equals the point-vortex kernel to FP32 precision, so far
-// tiles run the 1/r^3 form with one rsqrt; near tiles evaluate the regularised
-// kernel exactly per pair.  Each tile's sums start from zero and are folded into a
+// targets there are.  Far from a warp's 64 targets (the tile's bounding box more
+// than 7 sigma from both of the warp's two target boxes) the blob kernel equals
+// the point-vortex kernel to FP32 precision, so far tiles run the 1/r^3 form with
+// one rsqrt; near tiles evaluate the regularised kernel exactly per pair.  Each tile's sums start from zero and are folded into a
 // per-thread running sum kept in shared memory: a compensated (hi, lo) pair with
 // Knuth's two-sum, or a plain sum, so long source lists keep a tile-sized error.
 #include <math.h>
@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
 {
     extern __shared__ __align__(128) float4 dsm[];
     __shared__ __align__(8) uint64_t full[SWEEP_STAGES], empty[SWEEP_STAGES];
+    __shared__ float wbox[SWEEP_CW][12];
     constexpr int NR = n_rows<GRAD, STRETCH>();
     constexpr int NT = SWEEP_CW * 32;
     float4* stage = dsm;
@@ -498,7 +499,6 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
     Acc<GRAD, STRETCH> acc;
     Own own{zero2(), zero2(), zero2()};
     f2 X = zero2(), Y = zero2(), Z = zero2();
-    float blo[3], bhi[3];
     int t = t0, k = k0, cur_t = -1;
     auto zero_run = [&]() {
 #pragma unroll
@@ -531,19 +531,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
                 own.gy = make_float2(g0.y, g1.y);
                 own.gz = make_float2(g0.z, g1.z);
             }
-            blo[0] = v0 ? p0.x : INFINITY, blo[1] = v0 ? p0.y : INFINITY, blo[2] = v0 ? p0.z : INFINITY;
-            bhi[0] = v0 ? p0.x : -INFINITY, bhi[1] = v0 ? p0.y : -INFINITY, bhi[2] = v0 ? p0.z : -INFINITY;
-            if (v1) {
-                blo[0] = fminf(blo[0], p1.x), blo[1] = fminf(blo[1], p1.y), blo[2] = fminf(blo[2], p1.z);
-                bhi[0] = fmaxf(bhi[0], p1.x), bhi[1] = fmaxf(bhi[1], p1.y), bhi[2] = fmaxf(bhi[2], p1.z);
-            }
-#pragma unroll
-            for (int o2 = 16; o2 > 0; o2 >>= 1)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
-                    bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
-                }
+            warp_two_boxes(make_float3(p0.x, p0.y, p0.z), v0, make_float3(p1.x, p1.y, p1.z), v1, wbox[warp]);
         }
         if (!mbar_wait_bounded(&full[s], r & 1, A.dev_err, WAIT_LIMIT)) break;  // latched; results invalid
 
@@ -553,10 +541,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
         if (k < sk.np) {
             const int cnt = min(SRC_TILE, A.n_src - k * SRC_TILE);
             const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
-            const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
-            const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
-            const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
-            near_tile = dx * dx + dy * dy + dz * dz < A.nc.far2;
+            near_tile = boxes_near(wbox[warp], tlo, thi, A.nc.far2);
             if (near_tile)
                 particle_tile<GRAD, STRETCH, true>(acc, src, cnt, X, Y, Z, A.nc, own);
             else
@@ -564,11 +549,8 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
         } else {
             const int cnt = min(SRC_TILE, A.m_seg - (k - sk.np) * SRC_TILE);
             const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
-            const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
-            const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
-            const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
             const float margin = 1e-3f * tlo.w;
-            if (A.core_pos && dx * dx + dy * dy + dz * dz > margin * margin)
+            if (A.core_pos && !boxes_near(wbox[warp], tlo, thi, margin * margin))
                 segment_tile<GRAD, STRETCH, true>(acc, src, cnt, X, Y, Z, A.vn);
             else
                 segment_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.vn);
@@ -722,114 +704,84 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
 // Particle strength exchange (Eq. 5's diffusion term):
 //   p_i = (2/sigma^2) sum_j nu_ij (v_i Gamma_j - v_j Gamma_i) zeta_sigma(r_ij),
 //   nu_ij = nu + (nu_t,i + nu_t,j)/2, zeta of Eq. 3.
-// A block owns 256 consecutive particles.  It lists, in increasing order, the
-// source tiles whose bounding boxes come within 7 sigma of the block's box (a
-// block-wide ballot scan, so the summation order is fixed), then stages each
-// listed tile (positions, strengths, nu_t) in shared memory and every thread sums
-// over it.  v_i Gamma_j - v_j Gamma_i is formed from two rounded products so that
-// the i == j term is exactly zero; pairs beyond 7 sigma get exp(-r^2/2s^2) < 3e-11
-// and are skipped.
+// Each warp owns 64 consecutive particles (two per lane) with two bounding boxes
+// (split at the largest index-order jump).  It walks the source tiles 32 at a
+// time, one box test per lane, and for every tile within 7 sigma of either box
+// stages the tile (positions, strengths, nu_t) in its own slice of shared memory
+// with coalesced loads, then every lane sums over it.  No block-wide barrier:
+// warps proceed independently.  v_i Gamma_j - v_j Gamma_i is formed from two
+// rounded products so that the i == j term is exactly zero; pairs beyond 7 sigma
+// get exp(-r^2/2s^2) < 3e-11 and are skipped.
 // ---------------------------------------------------------------------------
 constexpr int PSE_T = 256;
+constexpr int PSE_W = PSE_T / 32;
+
+__device__ __forceinline__ void pse_pair(float4 pi, float4 gi, float base, float4 pj, float4 gj, float ntj,
+                                         float inv2s2, float cut2, float& ax, float& ay, float& az)
+{
+    const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    if (r2 < cut2) {
+        const float w = fmaf(0.5f, ntj, base) * expf(-r2 * inv2s2);
+        const float vi = pi.w, vj = pj.w;
+        ax = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x)), ax);
+        ay = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y)), ay);
+        az = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.z), __fmul_rn(vj, gi.z)), az);
+    }
+}
 
 __global__ void __launch_bounds__(PSE_T) pse_kernel(const float4* __restrict__ pos, const float4* __restrict__ str,
                                                     const float* __restrict__ nu_t, int n,
                                                     const float4* __restrict__ box, int ntiles, float inv2s2,
                                                     float cut2, float nu, float pref, float* __restrict__ dGdt)
 {
-    __shared__ float4 sp[SRC_TILE], sg[SRC_TILE];
-    __shared__ float snt[SRC_TILE];
-    __shared__ int list[PSE_T];
-    __shared__ int wcount[PSE_T / 32];
-    __shared__ float bb[PSE_T / 32][6];
-    __shared__ int nlist;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i = blockIdx.x * PSE_T + tid;
-    const bool valid = i < n;
-    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), gi = pi;
-    float nti = 0.f;
-    if (valid) {
-        pi = pos[i];
-        gi = str[i];
-        nti = nu_t ? nu_t[i] : 0.f;
-    }
-    // block bounding box
-    float blo[3] = {valid ? pi.x : INFINITY, valid ? pi.y : INFINITY, valid ? pi.z : INFINITY};
-    float bhi[3] = {valid ? pi.x : -INFINITY, valid ? pi.y : -INFINITY, valid ? pi.z : -INFINITY};
-#pragma unroll
-    for (int o2 = 16; o2 > 0; o2 >>= 1)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            blo[c] = fminf(blo[c], __shfl_xor_sync(0xffffffffu, blo[c], o2));
-            bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(0xffffffffu, bhi[c], o2));
-        }
-    if (lane == 0)
-        for (int c = 0; c < 3; ++c) bb[warp][c] = blo[c], bb[warp][3 + c] = bhi[c];
-    __syncthreads();
-    for (int w = 0; w < PSE_T / 32; ++w)
-        for (int c = 0; c < 3; ++c) blo[c] = fminf(blo[c], bb[w][c]), bhi[c] = fmaxf(bhi[c], bb[w][3 + c]);
-
-    const float base = nu + 0.5f * nti;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int t0 = 0; t0 < ntiles; t0 += PSE_T) {
-        // ordered list of the near tiles among t0 .. t0 + 255
-        const int tt = t0 + tid;
-        bool near = false;
-        if (tt < ntiles) {
-            const float4 tlo = box[2 * tt], thi = box[2 * tt + 1];
-            const float dx = fmaxf(0.f, fmaxf(tlo.x - bhi[0], blo[0] - thi.x));
-            const float dy = fmaxf(0.f, fmaxf(tlo.y - bhi[1], blo[1] - thi.y));
-            const float dz = fmaxf(0.f, fmaxf(tlo.z - bhi[2], blo[2] - thi.z));
-            near = dx * dx + dy * dy + dz * dz < cut2;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, near);
-        if (lane == 0) wcount[warp] = __popc(m);
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int w = 0; w < PSE_T / 32; ++w) {
-                const int c = wcount[w];
-                wcount[w] = acc;
-                acc += c;
+    __shared__ float4 sp[PSE_W][SRC_TILE], sg[PSE_W][SRC_TILE];
+    __shared__ float snt[PSE_W][SRC_TILE];
+    __shared__ float wbox[PSE_W][12];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base_i = (blockIdx.x * PSE_W + warp) * 64;
+    if (base_i >= n) return;  // whole warp past the end
+    const int i0 = base_i + lane, i1 = i0 + 32;
+    const bool v0 = i0 < n, v1 = i1 < n;
+    float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0, g0 = p0, g1 = p0;
+    float nt0 = 0.f, nt1 = 0.f;
+    if (v0) p0 = pos[i0], g0 = str[i0], nt0 = nu_t ? nu_t[i0] : 0.f;
+    if (v1) p1 = pos[i1], g1 = str[i1], nt1 = nu_t ? nu_t[i1] : 0.f;
+    warp_two_boxes(make_float3(p0.x, p0.y, p0.z), v0, make_float3(p1.x, p1.y, p1.z), v1, wbox[warp]);
+    const float base0 = nu + 0.5f * nt0, base1 = nu + 0.5f * nt1;
+    float a0x = 0.f, a0y = 0.f, a0z = 0.f, a1x = 0.f, a1y = 0.f, a1z = 0.f;
+    for (int tb = 0; tb < ntiles; tb += 32) {
+        const int tt = tb + lane;
+        const bool near = tt < ntiles && boxes_near(wbox[warp], box[2 * tt], box[2 * tt + 1], cut2);
+        unsigned mask = __ballot_sync(0xffffffffu, near);
+        while (mask) {
+            const int tile = tb + __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int j0 = tile * SRC_TILE, cnt = min(SRC_TILE, n - j0);
+            __syncwarp();
+            for (int q = lane; q < cnt; q += 32) {
+                sp[warp][q] = pos[j0 + q];
+                sg[warp][q] = str[j0 + q];
+                snt[warp][q] = nu_t ? nu_t[j0 + q] : 0.f;
             }
-            nlist = acc;
-        }
-        __syncthreads();
-        if (near) list[wcount[warp] + __popc(m & ((1u << lane) - 1u))] = tt;
-        __syncthreads();
-        const int nl = nlist;
-        for (int q = 0; q < nl; ++q) {
-            const int tile = list[q];
-            const int j0 = tile * SRC_TILE;
-            const int cnt = min(SRC_TILE, n - j0);
-            if (tid < cnt) {
-                sp[tid] = pos[j0 + tid];
-                snt[tid] = nu_t ? nu_t[j0 + tid] : 0.f;
-            } else if (tid >= SRC_TILE && tid - SRC_TILE < cnt) {
-                sg[tid - SRC_TILE] = str[j0 + tid - SRC_TILE];
-            }
-            __syncthreads();
-#pragma unroll 4
+            __syncwarp();
             for (int j = 0; j < cnt; ++j) {
-                const float4 pj = sp[j];
-                const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
-                const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                if (r2 < cut2) {
-                    const float4 gj = sg[j];
-                    const float w = fmaf(0.5f, snt[j], base) * expf(-r2 * inv2s2);
-                    const float vi = pi.w, vj = pj.w;
-                    ax = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x)), ax);
-                    ay = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y)), ay);
-                    az = fmaf(w, __fsub_rn(__fmul_rn(vi, gj.z), __fmul_rn(vj, gi.z)), az);
-                }
+                const float4 pj = sp[warp][j], gj = sg[warp][j];
+                const float ntj = snt[warp][j];
+                pse_pair(p0, g0, base0, pj, gj, ntj, inv2s2, cut2, a0x, a0y, a0z);
+                pse_pair(p1, g1, base1, pj, gj, ntj, inv2s2, cut2, a1x, a1y, a1z);
             }
-            __syncthreads();
         }
     }
-    if (valid) {
-        dGdt[i] += pref * ax;
-        dGdt[n + i] += pref * ay;
-        dGdt[2 * n + i] += pref * az;
+    if (v0) {
+        dGdt[i0] += pref * a0x;
+        dGdt[n + i0] += pref * a0y;
+        dGdt[2 * n + i0] += pref * a0z;
+    }
+    if (v1) {
+        dGdt[i1] += pref * a1x;
+        dGdt[n + i1] += pref * a1y;
+        dGdt[2 * n + i1] += pref * a1z;
     }
 }
 
@@ -1048,7 +1000,7 @@ cudaError_t run_pse(const SweepPlan& p, char* ws, const float* pos, const float*
     // (2/sigma^2) (2 pi sigma^2)^(-3/2)
     const float pref = (float)(2.0 / (s * s) * pow(2.0 * 3.14159265358979323846 * s * s, -1.5));
     TraceScope ts(VPM_TRACE_PSE, st);
-    pse_kernel<<<(n + PSE_T - 1) / PSE_T, PSE_T, 0, st>>>(reinterpret_cast<const float4*>(pos),
+    pse_kernel<<<(n + 64 * PSE_W - 1) / (64 * PSE_W), PSE_T, 0, st>>>(reinterpret_cast<const float4*>(pos),
                                                           reinterpret_cast<const float4*>(str), nu_t, n, pbox, p.SP,
                                                           inv2s2, cut2, nu, pref, dGdt);
     return cudaGetLastError();

@@ -199,3 +199,20 @@ def test_backward_near_field_targets(api):
 
 def test_device_error_word_clean(api):
     assert api.device_error() == 0
+
+
+@pytest.mark.parametrize("compensated", [True, False])
+def test_rhs_shuffled_particle_order(api, compensated):
+    """Results do not depend on the order of the particles (tile boxes, warp box
+    splits and the near/far choice only change cost, never values)."""
+    w = synth.make(1)
+    perm = np.random.default_rng(5).permutation(w.n)
+    pos, G = w.pos[perm], w.strength[perm]
+    rdx, rdG, rnut = oracle.rhs(pos, G, w.seg_a, w.seg_b, w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core,
+                                u_inf=w.u_inf)
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=compensated)
+    dx, dG, nut = api.rhs(to_dev(pos), to_dev(G), to_dev(w.seg_a), to_dev(w.seg_b), prm)
+    torch.cuda.synchronize()
+    tol = TOL_COMP if compensated else TOL_PLAIN
+    assert rel_l2(planar_to_rows(dx, 3), rdx) <= tol
+    assert rel_l2(planar_to_rows(dG, 3), rdG) <= tol
