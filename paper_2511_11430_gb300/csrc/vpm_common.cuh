@@ -190,6 +190,15 @@ __device__ __forceinline__ void warp_two_boxes(float3 p0, bool v0, float3 p1, bo
         lo[1][c] = fminf(b0 ? x0 : I, b1 ? x1 : I);
         hi[1][c] = fmaxf(b0 ? x0 : -I, b1 ? x1 : -I);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo[b][c] = fminf(lo[b][c], __shfl_xor_sync(F, lo[b][c], o));
+                hi[b][c] = fmaxf(hi[b][c], __shfl_xor_sync(F, hi[b][c], o));
+            }
     if (lane == 0)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 3; ++c) out[6 * b + c] = lo[b][c], out[6 * b + 3 + c] = hi[b][c];
