@@ -191,6 +191,26 @@ vpm_status vpm_induce_backward(const float* src_pos_d, const float* src_str_d, i
                                int64_t n_tgt, float sigma, int flags, const float* grad_out_d, float* dL_dx_d,
                                float* dL_dG_d, void* ws_d, size_t ws_bytes, void* stream);
 
+/* ---- velocity sweep without a caller workspace ------------------------------
+ * The paper has no counterpart: this is a library convenience.  vpm_induce for
+ * callers that cannot allocate device memory to pass as a workspace -- a solver in
+ * C or Fortran linked without any CUDA memory manager, or a time-critical loop
+ * that must not allocate.  Arguments and results are those of vpm_induce; the
+ * scratch is a fixed VPM_NOALLOC_SCRATCH_BYTES array in the library's own device
+ * memory, held by every GPU that loads the library until the process exits.
+ *  - The first call on a device (with that device current) looks the array's
+ *    device address up; make that first call before any stream capture.
+ *  - Problems whose scratch would exceed the array return VPM_ERR_LIMIT (message
+ *    in vpm_last_error) without launching anything; about 100,000 particles onto
+ *    themselves with the gradient fit on a 152-SM GB300.
+ *  - Every call uses the same array and nothing in it needs to start at zero;
+ *    calls whose GPU work overlaps (other streams, other host threads) race on it
+ *    and must be ordered by the caller.
+ *  - It allocates nothing and frees nothing. */
+#define VPM_NOALLOC_SCRATCH_BYTES (64 << 20)
+vpm_status vpm_induce_noalloc(const float* src_pos_d, const float* src_str_d, int64_t n_src, const float* tgt_d,
+                              int64_t n_tgt, float sigma, int flags, float* u_d, float* grad_u_d, void* stream);
+
 /* ---- launch tracing (not part of the method; for measurement) ------------
  * Every kernel the library launches increments a host-side counter.  With
  * vpm_trace_enable(1) the pair-sweep kernels are also bracketed by CUDA events

@@ -39,6 +39,7 @@ VPM_TRACE_SWEEP_VEL = 4
 
 VPM_MAX_ITEMS = 1 << 30
 VPM_MAX_AIC = 8192
+VPM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 STATUS_NAMES = {
     0: "VPM_OK", -1: "VPM_ERR_INVALID_ARG", -2: "VPM_ERR_CUDA", -3: "VPM_ERR_NONFINITE",
@@ -84,6 +85,7 @@ SIGNATURES = {
     "aic_build": (_INT, [_P, _P, _P, _INT, _F, _INT, _P, _P, _P, _P, _P]),
     "aic_solve": (_INT, [_P, _P, _P, _INT, _D, _INT, ctypes.POINTER(_INT), ctypes.POINTER(_D), _P, _SZ, _P]),
     "vpm_induce_backward": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P, _P, _SZ, _P]),
+    "vpm_induce_noalloc": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P]),
     "vpm_trace_enable": (_INT, [_INT]),
     "vpm_trace_reset": (_INT, []),
     "vpm_trace_read": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_D)]),

@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <mutex>
 #include <string>
 
 #include "vpm.h"
@@ -399,3 +400,83 @@ vpm_status vpm_induce_backward(const float* src_pos_d, const float* src_str_d, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// vpm_induce_noalloc: vpm_induce for callers that cannot give the library a
+// workspace because they have no way to allocate device memory themselves -- a
+// solver written in C or Fortran that links this library without any CUDA memory
+// manager, or a time-critical loop that is not allowed to allocate.  The scratch
+// is a fixed array in the library's own device memory, reserved on every GPU that
+// loads the library and kept until the process exits.  Its device address is
+// looked up once per device, on the first call made with that device current.
+// Nothing in it has to start at zero: each call writes every byte it later
+// reads.  All calls share the one array, so calls whose GPU work overlaps race
+// on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VPM_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_na_mu;
+void* g_na_ptr[64];
+
+cudaError_t noalloc_scratch_address(void** out)
+{
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[d]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[d] = p;
+    }
+    *out = g_na_ptr[d];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" vpm_status vpm_induce_noalloc(const float* src_pos_d, const float* src_str_d, int64_t n_src,
+                                         const float* tgt_d, int64_t n_tgt, float sigma, int flags, float* u_d,
+                                         float* grad_u_d, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(n_src, "n_src")) != VPM_OK) return s;
+    if ((s = check_count(n_tgt, "n_tgt")) != VPM_OK) return s;
+    REQUIRE(sigma > 0.f && isfinite(sigma), "sigma must be finite and > 0 (got %g)", (double)sigma);
+    if (n_tgt == 0) return ok();
+    REQUIRE(tgt_d && aligned16(tgt_d), "tgt must be a 16-byte aligned device pointer");
+    REQUIRE(u_d && aligned4(u_d), "u must be a 4-byte aligned device pointer");
+    REQUIRE(!grad_u_d || aligned4(grad_u_d), "grad_u misaligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_src == 0) {
+        cudaError_t e = cudaMemsetAsync(u_d, 0, sizeof(float) * 3 * (size_t)n_tgt, st);
+        if (e == cudaSuccess && grad_u_d) e = cudaMemsetAsync(grad_u_d, 0, sizeof(float) * 9 * (size_t)n_tgt, st);
+        return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_induce_noalloc");
+    }
+    REQUIRE(src_pos_d && src_str_d && aligned16(src_pos_d) && aligned16(src_str_d),
+            "src_pos/src_str must be 16-byte aligned device pointers");
+    const bool comp = flags & VPM_COMPENSATED;
+    Carve cv;
+    const SweepPlan p = plan_sweep(n_tgt, n_src, 0, grad_u_d != nullptr, comp, cv);
+    if (!overflow_guard(p)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
+    if (p.bytes > (size_t)VPM_NOALLOC_SCRATCH_BYTES)
+        return fail(VPM_ERR_LIMIT,
+                    "vpm_induce_noalloc: %lld sources onto %lld targets need %zu bytes of scratch, more than the "
+                    "%d bytes reserved; use vpm_induce with a workspace",
+                    (long long)n_src, (long long)n_tgt, p.bytes, VPM_NOALLOC_SCRATCH_BYTES);
+    if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
+    void* ws = nullptr;
+    cudaError_t e = noalloc_scratch_address(&ws);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_induce_noalloc: scratch address");
+    EpilogueOut o;
+    o.mode = 0;
+    o.u = u_d;
+    o.grad_u = grad_u_d;
+    o.check_finite = (flags & VPM_CHECK_FINITE) ? 1 : 0;
+    e = run_sweep(p, static_cast<char*>(ws), tgt_d, src_pos_d, src_str_d, nullptr, nullptr, sigma, 0.f, 2, o, st);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_induce_noalloc");
+}
