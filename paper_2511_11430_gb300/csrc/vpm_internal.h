@@ -10,10 +10,10 @@
 
 namespace vpm {
 
-constexpr int SWEEP_CW = 15;                 // consumer warps per sweep block (16 warps in all)
-constexpr int SWEEP_TPB = (SWEEP_CW + 1) * 32;  // + one producer warp
+constexpr int SWEEP_CW = 16;                 // warps per sweep block
+constexpr int SWEEP_TPB = SWEEP_CW * 32;
 constexpr int TGT_TILE = SWEEP_CW * 64;      // targets per sweep target tile: two per thread
-constexpr int SWEEP_STAGES = 4;              // shared-memory source tiles in flight
+constexpr int SWEEP_STAGES = 6;              // shared-memory source tiles in flight
 constexpr int TPB = 256;          // threads per adjoint block (8 warps)
 constexpr int ADJ_TILE = 512;     // particles per adjoint tile: two per thread
 constexpr int SRC_TILE = 128;     // sources per particle or segment tile

@@ -12,12 +12,13 @@
 // Kernel organisation.  A thread owns two targets, kept in the two lanes of packed
 // float2 registers so that each FFMA2/FADD2/FMUL2 advances two pair interactions.
 // Sources are packed once per call into 128-source tiles (duplicated into both
-// lanes, negated copies included so that every subtraction is an add).  In the
-// sweep block a producer warp streams the tiles into a ring of shared-memory stages
-// with the bulk-copy engine (cp.async.bulk completing on a "full" mbarrier); each of
-// the 15 consumer warps waits on "full", reads every source by broadcast, and
-// releases the stage through an "empty" mbarrier, so warps drift freely within the
-// ring and no block-wide barrier sits in the loop.  Work is split stream-K over
+// lanes, negated copies included so that every subtraction is an add).  The sweep
+// block streams the tiles through a ring of shared-memory stages with the bulk-copy
+// engine (cp.async.bulk completing on a per-stage "full" mbarrier); each of its 16
+// warps waits on "full", reads every source by broadcast and counts itself out of
+// the stage, and the last warp to leave a stage refills it with the tile six units
+// ahead.  Warps drift freely within the ring and no block-wide barrier sits in the
+// loop.  Work is split stream-K over
 // (target tile, source tile) cost units so every SM gets the same cost however few
 // targets there are.  Far from a warp's 64 targets (the tile's bounding box more
 // than 7 sigma from both of the warp's two target boxes) the blob kernel equals
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* _
 }
 
 // ---------------------------------------------------------------------------
-// The stream-K sweep: one producer warp + SWEEP_CW consumer warps per block.
+// The stream-K sweep: SWEEP_CW warps per block sharing a ring of source stages.
 // ---------------------------------------------------------------------------
 struct SweepArgs {
     const float4* tgt;
@@ -400,11 +401,6 @@ struct SweepArgs {
 constexpr int BUF_F4 = SRC_TILE * S_F4 + 2;  // the larger tile format + the tile's bounding box
 constexpr uint64_t WAIT_LIMIT = 2000000000ull;  // 2 s of wall time
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 template <bool GRAD, bool STRETCH>
 __host__ __device__ constexpr int n_rows()
 {
@@ -423,7 +419,9 @@ template <bool GRAD, bool COMP, bool STRETCH>
 __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
 {
     extern __shared__ __align__(128) float4 dsm[];
-    __shared__ __align__(8) uint64_t full[SWEEP_STAGES], empty[SWEEP_STAGES];
+    __shared__ __align__(8) uint64_t full[SWEEP_STAGES];
+    __shared__ int released[SWEEP_STAGES];
+    __shared__ int issued_round[SWEEP_STAGES];  // round of the latest copy into each stage
     __shared__ float wbox[SWEEP_CW][12];
     constexpr int NR = n_rows<GRAD, STRETCH>();
     constexpr int NT = SWEEP_CW * 32;
@@ -439,60 +437,43 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
     if (t0 >= sk.TT || sk.unit_start(t0, k0) >= hi_b) return;  // block owns no unit (uniform)
     const int nunits = sk.np + sk.ns;
 
+    // Copies source unit kk (and its bounding box) into stage s, completing on full[s].
+    auto issue = [&](int kk, int s, int round) {
+        issued_round[s] = round;
+        fence_proxy_async_smem();
+        if (kk < sk.np) {
+            const uint32_t bytes = SRC_TILE * P_F4 * 16;
+            mbar_expect_tx(&full[s], bytes + 32);
+            bulk_g2s(stage + (size_t)s * BUF_F4, A.psrc + (size_t)kk * SRC_TILE * P_F4, bytes, &full[s]);
+            bulk_g2s(stage + (size_t)s * BUF_F4 + SRC_TILE * S_F4, A.pbox + 2 * kk, 32, &full[s]);
+        } else {
+            const uint32_t bytes = SRC_TILE * S_F4 * 16;
+            mbar_expect_tx(&full[s], bytes + 32);
+            bulk_g2s(stage + (size_t)s * BUF_F4, A.ssrc + (size_t)(kk - sk.np) * SRC_TILE * S_F4, bytes, &full[s]);
+            bulk_g2s(stage + (size_t)s * BUF_F4 + SRC_TILE * S_F4, A.sbox + 2 * (kk - sk.np), 32, &full[s]);
+        }
+    };
+    // The unit `ahead` places after (t, k) in this block's run, if the block owns it.
+    auto unit_ahead = [&](int t, int k, int ahead, int& kk) {
+        for (int q = 0; q < ahead; ++q)
+            if (++k == nunits) k = 0, ++t;
+        kk = k;
+        return t < sk.TT && sk.unit_start(t, k) < hi_b;
+    };
+
     if (tid == 0) {
         for (int s = 0; s < SWEEP_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], SWEEP_CW);
+            released[s] = 0;
         }
         mbar_fence_init();
+        for (int s = 0; s < SWEEP_STAGES; ++s) {  // first fill of the ring
+            int kk;
+            if (!unit_ahead(t0, k0, s, kk)) break;
+            issue(kk, s, 0);
+        }
     }
     __syncthreads();
-
-    if (warp == SWEEP_CW) {
-        // ---------------- producer ----------------
-        if (lane != 0) return;
-        int t = t0, k = k0;
-        bool ok = true;
-        int issued = 0;
-        for (int i = 0;; ++i) {
-            const int s = i % SWEEP_STAGES, r = i / SWEEP_STAGES;
-            if (r > 0 && !mbar_wait_bounded(&empty[s], (r - 1) & 1, A.dev_err, WAIT_LIMIT)) {
-                ok = false;
-                break;
-            }
-            const float4* src;
-            uint32_t bytes;
-            if (k < sk.np) {
-                src = A.psrc + (size_t)k * SRC_TILE * P_F4;
-                bytes = SRC_TILE * P_F4 * 16;
-            } else {
-                src = A.ssrc + (size_t)(k - sk.np) * SRC_TILE * S_F4;
-                bytes = SRC_TILE * S_F4 * 16;
-            }
-            fence_proxy_async_smem();
-            if (k < sk.np) {
-                mbar_expect_tx(&full[s], bytes + 32);
-                bulk_g2s(stage + (size_t)s * BUF_F4, src, bytes, &full[s]);
-                bulk_g2s(stage + (size_t)s * BUF_F4 + SRC_TILE * S_F4, A.pbox + 2 * k, 32, &full[s]);
-            } else {
-                mbar_expect_tx(&full[s], bytes + 32);
-                bulk_g2s(stage + (size_t)s * BUF_F4, src, bytes, &full[s]);
-                bulk_g2s(stage + (size_t)s * BUF_F4 + SRC_TILE * S_F4, A.sbox + 2 * (k - sk.np), 32, &full[s]);
-            }
-            issued = i + 1;
-            if (++k == nunits) {
-                k = 0;
-                ++t;
-            }
-            if (t >= sk.TT || sk.unit_start(t, k) >= hi_b) break;
-        }
-        if (!ok) {
-            // let the copies already issued land before the block's shared memory is released
-            for (int i = (issued > SWEEP_STAGES ? issued - SWEEP_STAGES : 0); i < issued; ++i)
-                mbar_wait_bounded(&full[i % SWEEP_STAGES], (i / SWEEP_STAGES) & 1, A.dev_err, WAIT_LIMIT);
-        }
-        return;
-    }
 
     // ---------------- consumers ----------------
     const int ct = warp * 32 + lane;  // consumer thread index
@@ -533,7 +514,14 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
             }
             warp_two_boxes(make_float3(p0.x, p0.y, p0.z), v0, make_float3(p1.x, p1.y, p1.z), v1, wbox[warp]);
         }
-        if (!mbar_wait_bounded(&full[s], r & 1, A.dev_err, WAIT_LIMIT)) break;  // latched; results invalid
+        if (!mbar_wait_bounded(&full[s], r & 1, A.dev_err, WAIT_LIMIT)) {
+            // latched; the results are invalid.  Let this block's copies in flight land
+            // (bounded) before its shared memory is released, then leave.
+            if (lane == 0)
+                for (int q = 0; q < SWEEP_STAGES; ++q)
+                    mbar_wait_bounded(&full[q], issued_round[q] & 1, A.dev_err, WAIT_LIMIT);
+            break;
+        }
 
         const float4* src = stage + (size_t)s * BUF_F4;
         acc.zero();
@@ -556,7 +544,15 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
                 segment_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.vn);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);  // stage s may be refilled
+        if (lane == 0) {  // the last warp to finish with stage s refills it with unit i + SWEEP_STAGES
+            __threadfence_block();
+            if (atomicAdd(&released[s], 1) == SWEEP_CW - 1) {
+                released[s] = 0;
+                __threadfence_block();
+                int kk;
+                if (unit_ahead(t, k, SWEEP_STAGES, kk)) issue(kk, s, r + 1);
+            }
+        }
         if (!near_tile) stretch_from_tile<GRAD, STRETCH>(acc, own);
         // fold this tile's sums into the running sums
 #pragma unroll
