@@ -95,33 +95,6 @@ cudaError_t run_aic_build(const float* rings, const float* colloc, const float* 
 constexpr int NB = 32;
 constexpr int LU_THREADS = 1024;
 
-__device__ __forceinline__ void argmax_abs_block(float v, int idx, float* sv, int* si, float& best, int& bidx)
-{
-    // warp reduce then block reduce (max |v|, smallest index on ties)
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) v = ov, idx = oi;
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sv[w] = v, si[w] = idx;
-    __syncthreads();
-    if (w == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sv[lane] : -1.f;
-        idx = lane < (int)(blockDim.x >> 5) ? si[lane] : 0x7fffffff;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ov > v || (ov == v && oi < idx)) v = ov, idx = oi;
-        }
-        if (lane == 0) sv[0] = v, si[0] = idx;
-    }
-    __syncthreads();
-    best = sv[0];
-    bidx = si[0];
-    __syncthreads();
-}
-
 // Factors columns [k0, k0 + nb) of rows [k0, n) in place with partial pivoting (one
 // block).  The panel is held in shared memory (rows padded to nb + 1 floats) when it
 // fits, else worked on in global memory; only the panel's own columns are swapped
@@ -142,16 +115,31 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(float* __restrict_
         }
         __syncthreads();
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < nb; ++j) {
+        // pivot: per-warp candidates, one barrier, then every warp reduces the candidates itself
         float v = -1.f;
         int idx = 0x7fffffff;
         for (int r = j + threadIdx.x; r < rows; r += blockDim.x) {
             const float a = fabsf(base[(size_t)r * ld + j]);
             if (a > v || (a == v && r < idx)) v = a, idx = r;
         }
-        float best;
-        int p;
-        argmax_abs_block(v, idx, sv, si, best, p);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov > v || (ov == v && oi < idx)) v = ov, idx = oi;
+        }
+        if (lane == 0) sv[warp] = v, si[warp] = idx;
+        __syncthreads();
+        v = lane < nw ? sv[lane] : -1.f;
+        idx = lane < nw ? si[lane] : 0x7fffffff;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov > v || (ov == v && oi < idx)) v = ov, idx = oi;
+        }
+        const float best = v;
+        const int p = idx;
         if (!(best > 0.f)) {  // exactly singular column (or NaN): keep going, report
             if (threadIdx.x == 0) {
                 piv[k0 + j] = k0 + j;
@@ -167,7 +155,7 @@ __global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(float* __restrict_
             base[(size_t)j * ld + c] = base[(size_t)p * ld + c];
             base[(size_t)p * ld + c] = t;
         }
-        __syncthreads();
+        __syncthreads();  // swapped rows and the reduction slots are settled
         const float inv = 1.0f / base[(size_t)j * ld + j];
         for (int r = j + 1 + threadIdx.x; r < rows; r += blockDim.x) {
             float* row = base + (size_t)r * ld;
@@ -274,13 +262,14 @@ __global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __res
                                                               const int* __restrict__ piv, int n,
                                                               const double* __restrict__ rhs, double* __restrict__ z)
 {
-    extern __shared__ float y[];
+    extern __shared__ float y[];  // y[n], then the pivots as int[n]
+    int* sp = reinterpret_cast<int*>(y + n);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) y[i] = (float)rhs[i];
+    for (int i = tid; i < n; i += blockDim.x) y[i] = (float)rhs[i], sp[i] = piv[i];
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0)  // the row exchanges in order, on shared memory
         for (int j = 0; j < n; ++j) {
-            const int p = piv[j];
+            const int p = sp[j];
             if (p != j) {
                 const float t = y[j];
                 y[j] = y[p];
@@ -471,7 +460,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     }
     VPM_CU(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(n * sizeof(float))));
+                                (int)(n * (sizeof(float) + sizeof(int)))));
     for (int k0 = 0; k0 < n; k0 += pnb) {
         const int nb = n - k0 < pnb ? n - k0 : pnb;
         trace_launch();
@@ -502,7 +491,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         return VPM_ERR_NOT_CONVERGED;
     }
     trace_launch();
-    lu_solve_kernel<<<1, LU_THREADS, n * sizeof(float), st>>>(LU, piv, n, b, x);
+    lu_solve_kernel<<<1, LU_THREADS, n * (sizeof(float) + sizeof(int)), st>>>(LU, piv, n, b, x);
     double h[4];
     double best = INFINITY;
     for (int it = 0;; ++it) {
@@ -524,7 +513,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
             return VPM_ERR_NOT_CONVERGED;
         }
         trace_launch();
-        lu_solve_kernel<<<1, LU_THREADS, n * sizeof(float), st>>>(LU, piv, n, r, d);
+        lu_solve_kernel<<<1, LU_THREADS, n * (sizeof(float) + sizeof(int)), st>>>(LU, piv, n, r, d);
         trace_launch();
         add_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, d, n);
     }
