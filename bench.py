@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=None,
+                    help="seconds of oracle work per CPU-baseline sample (default 12; reference arm: 60 s over all steps)")
     return ap.parse_args()
 
 
@@ -142,21 +143,30 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def max_over_ranks(dist, ms, device):
+    """The slowest rank's time: every rank's timed region ends when the last one does."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world_size, units_per_rank_step, steps, total_ms):
+    """Units that all ranks processed (each rank runs its own replica) per second."""
+    return world_size * units_per_rank_step * steps / (total_ms * 1e-3)
+
+
 def run_reference(args):
     ws, rank, local = dist_info()
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("gloo")
-        if rank != 0:
-            dist.barrier()
-            dist.destroy_process_group()
-            return
+    if ws > 1 and rank != 0:
+        return  # the oracle runs once, on rank 0's host cores; the other ranks exit without work
     from paper_2511_11430_gb300 import synth
 
     w = synth.make(args.config) if args.particles is None else synth.make(args.config, n=args.particles)
     cores = host_cores()
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = args.cpu_seconds if args.cpu_seconds is not None else max(2.0, 60.0 / max(1, args.steps + args.warmup))
     rates = []
     for i in range(args.warmup + args.steps):
         r, k, dt = oracle_rate(w, per_step, cores)
@@ -175,11 +185,6 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------
@@ -257,10 +262,7 @@ def run_ours(args):
             tr = {k: api.trace_read(k) for k in (_lib.VPM_TRACE_ALL, _lib.VPM_TRACE_SWEEP, _lib.VPM_TRACE_ADJOINT,
                                                  _lib.VPM_TRACE_PSE, _lib.VPM_TRACE_SWEEP_VEL)}
             api.trace_enable(False)
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), tr
+        return max_over_ranks(dist, total, dev), tr
 
     prm_c = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=True)
     prm_p = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=False)
@@ -273,12 +275,12 @@ def run_ours(args):
     total_ms, tr = timed(prm_c, args.steps, args.warmup, trace=True)
     clk = clocks.stop() if clocks else None
     ms_step = total_ms / args.steps
-    value = ws_n * pairs_step * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(ws_n, pairs_step, args.steps, total_ms)
 
     plain = None
     if not args.no_plain:
         pm, _ = timed(prm_p, max(3, args.steps // 2), 1)
-        plain = {"value": ws_n * pairs_step * max(3, args.steps // 2) / (pm * 1e-3), "unit": UNIT,
+        plain = {"value": whole_job_rate(ws_n, pairs_step, max(3, args.steps // 2), pm), "unit": UNIT,
                  "ms_per_step": pm / max(3, args.steps // 2), "dtype": "f32 (plain accumulation)"}
 
     # roofline of the dominant kernel: the particle + segment u + grad u sweep
@@ -340,14 +342,12 @@ def run_ours(args):
             e2e_step()
         e1.record(st)
         e1.synchronize()
-        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
         h2d = (xh.numel() + Gh.numel()) * 8 + volh.numel() * 4 + sum(h.numel() * 4 for h in host_in)
         d2h = (xo.numel() + Go.numel() + gho.numel()) * 8 + (dxo.numel() + dGo.numel()) * 4
-        e2e = {"value": ws_n * pairs_step * ksteps / (float(t.item()) * 1e-3), "unit": UNIT,
+        e2e = {"value": whole_job_rate(ws_n, pairs_step, ksteps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": float(t.item()) / ksteps}
+               "ms_per_step": e2e_ms / ksteps}
 
     # error at the stated tolerance, on a sample (outside every timed region)
     err = None
@@ -372,7 +372,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        rate, k, dt = oracle_rate(w, args.cpu_seconds, cores)
+        rate, k, dt = oracle_rate(w, 12.0 if args.cpu_seconds is None else args.cpu_seconds, cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{k} sampled targets x all {n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)"}
 

@@ -44,8 +44,13 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB_PATH)
+            # VPM_ORACLE_LIB points at another build of vpm_oracle.c (the mutation tests
+            # use it to check that the pins catch planted mistakes).
+            path = os.environ.get("VPM_ORACLE_LIB")
+            if not path:
+                build()
+                path = _LIB_PATH
+            lib = ctypes.CDLL(path)
             P = ctypes.POINTER(ctypes.c_double)
             i64 = ctypes.c_int64
             d = ctypes.c_double

@@ -1,0 +1,61 @@
+"""The oracle's pins are strong enough to catch plausible mistakes: each mutation
+below plants one (a dropped factor, a wrong sign, an index swapped, a wrong
+coefficient) in a copy of oracle/vpm_oracle.c, builds it, and runs the pin tests
+against it in a subprocess; every mutant must make at least one pin fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "vpm_oracle.c")
+PINS = ["tests/test_oracle_blob.py", "tests/test_oracle_segments.py", "tests/test_oracle_local.py",
+        "tests/test_oracle_rk3_lu_adjoint.py"]
+
+MUTATIONS = {
+    "taylor_denominator": ("qs += term / (2.0 * k + 3.0);", "qs += term / (2.0 * k + 5.0);"),
+    "closed_form_drops_rho": ("const double g = erf(rho / sqrt(2.0)) - SQRT_2_OVER_PI * rho * e;",
+                              "const double g = erf(rho / sqrt(2.0)) - SQRT_2_OVER_PI * e;"),
+    "kernel_2pi": ("*K = q / (4.0 * PI * s3);", "*K = q / (2.0 * PI * s3);"),
+    "cross_sign": ("out[0] = p[1] * q[2] - p[2] * q[1];", "out[0] = p[2] * q[1] - p[1] * q[2];"),
+    "gradient_transposed": ("Ji[3 * a + b] += K * t + H * c[a] * r[b];", "Ji[3 * a + b] += K * t + H * c[b] * r[a];"),
+    "segment_d_sign": ("const double d = dot(r0, r1) / n1 - dot(r0, r2) / n2;",
+                       "const double d = dot(r0, r1) / n1 + dot(r0, r2) / n2;"),
+    "vatistas_core_length": ("const double e = pow(rc * L, 2.0 * vn);", "const double e = pow(rc, 2.0 * vn);"),
+    "vreman_delta": ("be[i][j] = delta * delta * s;", "be[i][j] = delta * s;"),
+    "stretch_not_transposed": ("t += classic ? Jp[3 * a + b] * G[b] : Jp[3 * b + a] * G[b];",
+                               "t += classic ? Jp[3 * a + b] * G[b] : Jp[3 * a + b] * G[b];"),
+    "pse_factor": ("p[3 * i + a] = 2.0 / (sigma * sigma) * acc[a];", "p[3 * i + a] = 1.0 / (sigma * sigma) * acc[a];"),
+    "rk3_coefficient": ("-153.0 / 128.0", "-153.0 / 126.0"),
+    "lu_no_pivoting": ("if (fabs(A[n * i + k]) > fabs(A[n * piv + k])) piv = i;", "if (0) piv = i;"),
+    "adjoint_sign": ("ax[b] -= t;", "ax[b] += t;"),
+    "aic_normal_index": ("A[n * k + l] = dot(tot, &normal[4 * k]);", "A[n * k + l] = dot(tot, &normal[4 * l]);"),
+}
+
+
+def _run_pins(src_text, tmp_path):
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src_text)
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib), str(mutant), "-lm"],
+                   check=True)
+    env = dict(os.environ, VPM_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=ROOT,
+                          env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.slow
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    res = _run_pins(open(SRC).read(), tmp_path)
+    assert res.returncode == 0, res.stdout[-2000:]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    res = _run_pins(src.replace(old, new), tmp_path)
+    assert res.returncode != 0, f"no pin caught mutation {name}:\n{res.stdout[-2000:]}"
