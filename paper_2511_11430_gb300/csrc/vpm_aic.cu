@@ -4,11 +4,15 @@
 //  * aic_build: A[k][l] = u(ring l, unit circulation)(y_k) . n_k, each ring the four
 //    Vatistas-cored segments of its corners; b[k] = -(v_rel,k + w_k) . n_k in FP64.
 //  * aic_solve: A factored once in FP32 by a blocked right-looking LU with partial
-//    pivoting (panel kernel, triangular solve of the block row, FP32 update of the
-//    trailing matrix), then iterative refinement: the residual r = b - A x is formed
-//    in FP64 from the FP32 matrix, the correction solved with the FP32 factors and
-//    added to x in FP64, until the normwise backward error is below tol.
+//    pivoting (panel kernel with one block barrier per column, row exchanges and the
+//    block row U12 in one kernel, FP32 update of the trailing matrix), then iterative
+//    refinement: the residual r = b - A x is formed in FP64 from the FP32 matrix, the
+//    correction solved with the FP32 factors (read through a transposed copy so that
+//    the substitutions load coalesced columns) and added to x in FP64, until the
+//    normwise backward error is below tol.
 #include <math.h>
+
+#include <algorithm>
 
 #include "vpm_internal.h"
 
@@ -91,128 +95,370 @@ cudaError_t run_aic_build(const float* rings, const float* colloc, const float* 
 
 // ---------------------------------------------------------------------------
 // FP32 LU with partial pivoting, panel width NB.
+//
+// Per panel [k0, k0 + nb): lu_panel_kernel factors the panel's columns (one block),
+// lu_rows_kernel applies the panel's row exchanges to every other column and forms
+// the block row U12 = L11^-1 A12, lu_update_kernel updates A22 -= L21 U12.  The
+// result is LAPACK's: P A = L U with the row exchanges applied to whole rows.
 // ---------------------------------------------------------------------------
 constexpr int NB = 32;
-constexpr int LU_THREADS = 1024;
+constexpr int LU_THREADS = 1024;  // the triangular solves
 
-// Factors columns [k0, k0 + nb) of rows [k0, n) in place with partial pivoting (one
-// block).  The panel is held in shared memory (rows padded to nb + 1 floats) when it
-// fits, else worked on in global memory; only the panel's own columns are swapped
-// here, the other columns by lu_laswp_kernel.
-template <bool SMEM>
-__global__ void __launch_bounds__(LU_THREADS) lu_panel_kernel(float* __restrict__ A, int n, int k0, int nb,
-                                                              int* __restrict__ piv, int* __restrict__ info)
+// The end of a panel, after a barrier that made the final position map `pos2phys`
+// visible (and with *nmov zeroed before it): lists the changed positions as (source,
+// destination) moves -- at most 2 nb, the panel's own rows and the rows they displaced
+// -- and applies them to the permutation.
+template <int NT>
+__device__ __forceinline__ void panel_moves(const int* pos2phys, int rows, int k0, int* __restrict__ perm,
+                                            int* __restrict__ moves, int* nmov)
 {
-    extern __shared__ float P[];
-    __shared__ float sv[32];
-    __shared__ int si[32];
-    const int rows = n - k0, ld = SMEM ? nb + 1 : n;
-    float* base = SMEM ? P : A + (size_t)k0 * n + k0;
-    if (SMEM) {
-        for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
-            const int r = e / nb, c = e % nb;
-            P[r * ld + c] = A[(size_t)(k0 + r) * n + k0 + c];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < rows; i += NT) {
+        const int s = pos2phys[i];
+        if (s != i) {
+            const int m = atomicAdd(nmov, 1);
+            moves[1 + 2 * m] = s;
+            moves[2 + 2 * m] = i;
         }
-        __syncthreads();
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < nb; ++j) {
-        // pivot: per-warp candidates, one barrier, then every warp reduces the candidates itself
-        float v = -1.f;
-        int idx = 0x7fffffff;
-        for (int r = j + threadIdx.x; r < rows; r += blockDim.x) {
-            const float a = fabsf(base[(size_t)r * ld + j]);
-            if (a > v || (a == v && r < idx)) v = a, idx = r;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ov > v || (ov == v && oi < idx)) v = ov, idx = oi;
-        }
-        if (lane == 0) sv[warp] = v, si[warp] = idx;
-        __syncthreads();
-        v = lane < nw ? sv[lane] : -1.f;
-        idx = lane < nw ? si[lane] : 0x7fffffff;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ov > v || (ov == v && oi < idx)) v = ov, idx = oi;
-        }
-        const float best = v;
-        const int p = idx;
-        if (!(best > 0.f)) {  // exactly singular column (or NaN): keep going, report
-            if (threadIdx.x == 0) {
-                piv[k0 + j] = k0 + j;
-                if (*info == 0) *info = k0 + j + 1;
-            }
-            __syncthreads();
-            continue;
-        }
-        if (threadIdx.x == 0) piv[k0 + j] = k0 + p;
-        if (p != j && threadIdx.x < nb) {
-            const int c = threadIdx.x;
-            const float t = base[(size_t)j * ld + c];
-            base[(size_t)j * ld + c] = base[(size_t)p * ld + c];
-            base[(size_t)p * ld + c] = t;
-        }
-        __syncthreads();  // swapped rows and the reduction slots are settled
-        const float inv = 1.0f / base[(size_t)j * ld + j];
-        for (int r = j + 1 + threadIdx.x; r < rows; r += blockDim.x) {
-            float* row = base + (size_t)r * ld;
-            const float l = row[j] * inv;
-            row[j] = l;
-            for (int c = j + 1; c < nb; ++c) row[c] = fmaf(-l, base[(size_t)j * ld + c], row[c]);
-        }
-        __syncthreads();
-    }
-    if (SMEM) {
-        for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
-            const int r = e / nb, c = e % nb;
-            A[(size_t)(k0 + r) * n + k0 + c] = P[r * ld + c];
-        }
-    }
-}
-
-// Applies the row exchanges of panel [k0, k0 + nb) to every column outside it.
-__global__ void __launch_bounds__(256) lu_laswp_kernel(float* __restrict__ A, int n, int k0, int nb,
-                                                       const int* __restrict__ piv)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n - nb) return;
-    if (c >= k0) c += nb;
-    for (int j = k0; j < k0 + nb; ++j) {
-        const int p = piv[j];
-        if (p != j) {
-            const float t = A[(size_t)j * n + c];
-            A[(size_t)j * n + c] = A[(size_t)p * n + c];
-            A[(size_t)p * n + c] = t;
-        }
-    }
-}
-
-// U12 = L11^-1 A12 for the block row [k0, k0+nb), columns [k0+nb, n): one thread per column.
-__global__ void __launch_bounds__(256) lu_trsm_kernel(float* __restrict__ A, int n, int k0, int nb)
-{
-    __shared__ float L[NB][NB + 1];
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        const int i = e / nb, p = e % nb;
-        L[i][p] = A[(size_t)(k0 + i) * n + k0 + p];
     }
     __syncthreads();
-    const int c = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    float x[NB];
+    const int cnt = *nmov;
+    int pv = 0;
+    if (tid < cnt) pv = perm[k0 + moves[1 + 2 * tid]];
+    __syncthreads();  // every move's source is read before any destination is written
+    if (tid < cnt) perm[k0 + moves[2 + 2 * tid]] = pv;
+    if (tid == 0) moves[0] = cnt;
+}
+
+// Factors columns [k0, k0 + nb) of rows [k0, n) with partial pivoting (one block of
+// PANEL_THREADS).  The panel is copied into rows of PLD floats (16-byte aligned, so a
+// row is updated with float4 accesses), the first `srows` of them in shared memory and
+// the rest in the global scratch `pscratch`.  Rows never move while the panel is
+// worked on: thread t owns physical rows t, t + PANEL_THREADS, ..., and the row
+// exchanges are kept as a logical-position <-> physical-row map (thread 0 only), so
+// that a column costs one block barrier:
+//   1. each thread measures column j on its live rows; a 32-bit key orders |a| and
+//      puts NaN below every number (0 = no live row); the warp takes the maximum with
+//      redux.sync, the lowest lane holding it wins, and the warp publishes that row's
+//      copy, key and index in a slot of a two-deep ring;
+//   2. one barrier; every warp reduces the published keys the same way, so all
+//      threads know the pivot row and read it from the winning slot;
+//   3. every thread eliminates column j from its live rows.
+// The ring is two deep because slot j & 1 is rewritten only at column j + 2, after the
+// barrier of column j + 1, by which time every thread has finished using it.  At the
+// end the rows are written back in their logical order, the positions that changed
+// are listed as (source, destination) moves for lu_rows_kernel, and the permutation
+// `perm` (original row index of each position) is updated with the same moves.
+// A column whose largest candidate is not positive (all zero or NaN) sets *info to
+// its 1-based index (first such column) and is not eliminated.
+constexpr int PANEL_THREADS = 512;
+constexpr int PANEL_WARPS = PANEL_THREADS / 32;
+constexpr int PLD = NB + 4;
+static_assert(VPM_MAX_AIC <= 32 * PANEL_THREADS, "row ownership mask is 32 bits");
+
+template <bool ALL_SMEM>
+__global__ void __launch_bounds__(PANEL_THREADS, 1) lu_panel_kernel(float* __restrict__ A, int n, int k0, int nb,
+                                                                 int* __restrict__ info, int* __restrict__ perm,
+                                                                 int* __restrict__ moves, float* pscratch, int srows)
+{
+    constexpr int NT = PANEL_THREADS;
+    extern __shared__ __align__(16) float psm[];  // srows * PLD floats, then pos2phys[rows], phys2pos[rows]
+    __shared__ __align__(16) float crow[2][PANEL_WARPS][NB];
+    __shared__ unsigned ckey[2][PANEL_WARPS];
+    __shared__ int cidx[2][PANEL_WARPS];
+    __shared__ float cpiv[2][PANEL_WARPS];
+    __shared__ int nmov;
+    const int rows = n - k0;
+    int* pos2phys = reinterpret_cast<int*>(psm + (size_t)srows * PLD);
+    int* phys2pos = pos2phys + rows;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Calls f with row r of the panel copy.  The two branches give the compiler a
+    // shared-memory and a global pointer, so each access is a plain shared or global
+    // one (ALL_SMEM: every row is in shared memory).
+    auto with_row = [&](int r, auto&& f) {
+        if (ALL_SMEM || r < srows) return f(psm + (size_t)r * PLD);
+        return f(pscratch + (size_t)(r - srows) * PLD);
+    };
+    if (k0 == 0) {
+        for (int i = tid; i < n; i += NT) perm[i] = i;
+        if (tid == 0) *info = 0;
+    }
+    const int nmine = tid < rows ? (rows - 1 - tid) / NT + 1 : 0;
+    for (int t = 0; t < nmine; ++t) {  // my rows: 32 independent loads each, then float4 stores
+        const int r = tid + t * NT;
+        const float* src = A + (size_t)(k0 + r) * n + k0;
+        float v[NB];
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        if (i < nb) {
-            float s = A[(size_t)(k0 + i) * n + c];
+        for (int c = 0; c < NB; ++c) v[c] = c < nb ? src[c] : 0.f;  // a narrow last panel is zero-filled
+        with_row(r, [&](float* row) {
 #pragma unroll
-            for (int p = 0; p < NB; ++p)
-                if (p < i) s -= L[i][p] * x[p];
-            x[i] = s;
-            A[(size_t)(k0 + i) * n + c] = s;
+            for (int c4 = 0; c4 < NB / 4; ++c4)
+                reinterpret_cast<float4*>(row)[c4] = make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+        });
+    }
+    for (int i = tid; i < rows; i += NT) pos2phys[i] = i, phys2pos[i] = i;
+    if (tid == 0) nmov = 0;
+    __syncthreads();
+
+    unsigned done = 0;  // bit t: my row tid + t * NT is a pivot row already
+    for (int j = 0; j < nb; ++j) {
+        unsigned key = 0;
+        int rb = 0;
+        for (int t = 0; t < nmine; ++t) {
+            if (done >> t & 1u) continue;
+            const int r = tid + t * NT;
+            const float v = with_row(r, [&](float* row) { return fabsf(row[j]); });
+            const unsigned k = v == v ? __float_as_uint(v) + 2u : 1u;
+            if (k > key) key = k, rb = r;
+        }
+        const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+        const int wl = __ffs(__ballot_sync(0xffffffffu, key == wmax)) - 1;
+        const int wr = __shfl_sync(0xffffffffu, rb, wl);
+        __syncwarp();  // the lanes' row updates are visible to the whole warp
+        // the candidate row with its columns <= j zeroed (those keep their values in the
+        // elimination), and its entry in column j
+        if (lane < NB / 4)
+            with_row(wr, [&](float* row) {
+                float4 v = reinterpret_cast<const float4*>(row)[lane];
+                const int c = 4 * lane;
+                if (c <= j) v.x = 0.f;
+                if (c + 1 <= j) v.y = 0.f;
+                if (c + 2 <= j) v.z = 0.f;
+                if (c + 3 <= j) v.w = 0.f;
+                reinterpret_cast<float4*>(crow[j & 1][warp])[lane] = v;
+                if (lane == (j >> 2)) cpiv[j & 1][warp] = row[j];
+            });
+        if (lane == 0) ckey[j & 1][warp] = wmax, cidx[j & 1][warp] = wr;
+        __syncthreads();
+        const unsigned k2 = lane < PANEL_WARPS ? ckey[j & 1][lane] : 0u;
+        const unsigned bmax = __reduce_max_sync(0xffffffffu, k2);
+        const int ws = __ffs(__ballot_sync(0xffffffffu, lane < PANEL_WARPS && k2 == bmax)) - 1;
+        const int q = cidx[j & 1][ws];
+        const bool ok = bmax > 2u;  // the column's largest |a| is a positive number
+        if ((q & (NT - 1)) == tid) done |= 1u << (q / NT);
+        if (tid == 0) {
+            const int pos = phys2pos[q], x = pos2phys[j];
+            pos2phys[j] = q, pos2phys[pos] = x;
+            phys2pos[q] = j, phys2pos[x] = pos;
+            if (!ok && *info == 0) *info = k0 + j + 1;
+        }
+        if (ok) {
+            const float4* u4 = reinterpret_cast<const float4*>(crow[j & 1][ws]);
+            const int c4s = j >> 2;
+            float4 uu[NB / 4];
+#pragma unroll
+            for (int c4 = 0; c4 < NB / 4; ++c4) uu[c4] = u4[c4];
+            const float rp = __frcp_rn(cpiv[j & 1][ws]);
+            for (int t = 0; t < nmine; ++t) {
+                if (done >> t & 1u) continue;
+                with_row(tid + t * NT, [&](float* row) {
+                    const float l = row[j] * rp;
+                    row[j] = l;
+                    const float ml = -l;
+#pragma unroll
+                    for (int c4 = 0; c4 < NB / 4; ++c4) {
+                        if (c4 < c4s) continue;  // the same for every thread
+                        float4 a = reinterpret_cast<float4*>(row)[c4];
+                        a.x = fmaf(ml, uu[c4].x, a.x);
+                        a.y = fmaf(ml, uu[c4].y, a.y);
+                        a.z = fmaf(ml, uu[c4].z, a.z);
+                        a.w = fmaf(ml, uu[c4].w, a.w);
+                        reinterpret_cast<float4*>(row)[c4] = a;
+                    }
+                });
+            }
         }
     }
+    __syncthreads();  // the position map is final and every row is eliminated
+    for (int t = 0; t < nmine; ++t) {  // my rows, to their logical positions
+        const int r = tid + t * NT;
+        float* dst = A + (size_t)(k0 + phys2pos[r]) * n + k0;
+        with_row(r, [&](float* row) {
+#pragma unroll
+            for (int c4 = 0; c4 < NB / 4; ++c4) {
+                const float4 v = reinterpret_cast<const float4*>(row)[c4];
+                if (4 * c4 < nb) dst[4 * c4] = v.x;
+                if (4 * c4 + 1 < nb) dst[4 * c4 + 1] = v.y;
+                if (4 * c4 + 2 < nb) dst[4 * c4 + 2] = v.z;
+                if (4 * c4 + 3 < nb) dst[4 * c4 + 3] = v.w;
+            }
+        });
+    }
+    panel_moves<NT>(pos2phys, rows, k0, perm, moves, &nmov);
+}
+
+// The same factorisation for panels of at most R * NT rows with every row in
+// registers.  Thread t owns physical rows t + i * NT (i < R) as 32 registers each,
+// rotated so that register c holds column j + c while column j is worked on: the
+// elimination of column j writes register c from register c + 1,
+//   a[c] = a[c + 1] - l * u[c + 1],
+// so every register index is a compile-time constant while the column loop is an
+// ordinary loop (a small body that stays in the instruction cache).  The multiplier
+// l of each row goes to the shared-memory buffer Lb[row][column]; the pivot row's
+// remaining entries (its U row) to Ub[j][column].  Pivot search, publication and the
+// one barrier per column are those of lu_panel_kernel.  The panel is read and written
+// back with coalesced row accesses staged through Lb.
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1) lu_panel_reg_kernel(float* __restrict__ A, int n, int k0, int nb,
+                                                             int* __restrict__ info, int* __restrict__ perm,
+                                                             int* __restrict__ moves)
+{
+    constexpr int NW = NT / 32;
+    constexpr int LDL = NB + 1;
+    static_assert(NW <= 32, "one warp reduces the published candidates");
+    extern __shared__ float Lb[];  // [rows][LDL], then pos2phys[rows], phys2pos[rows]
+    __shared__ __align__(16) float crow[2][NW][NB];
+    __shared__ float Ub[NB][NB + 1];
+    __shared__ unsigned ckey[2][NW];
+    __shared__ int cidx[2][NW];
+    __shared__ int nmov;
+    const int rows = n - k0;
+    int* pos2phys = reinterpret_cast<int*>(Lb + (size_t)rows * LDL);
+    int* phys2pos = pos2phys + rows;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (k0 == 0) {
+        for (int i = tid; i < n; i += NT) perm[i] = i;
+        if (tid == 0) *info = 0;
+    }
+    // stage the panel in Lb: a warp per row, a lane per column, eight rows in flight
+    for (int r0 = warp; r0 < rows; r0 += 8 * NW) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = r0 + k * NW;
+            v[k] = (r < rows && lane < nb) ? A[(size_t)(k0 + r) * n + k0 + lane] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (r0 + k * NW < rows) Lb[(size_t)(r0 + k * NW) * LDL + lane] = v[k];
+    }
+    for (int i = tid; i < rows; i += NT) pos2phys[i] = i, phys2pos[i] = i;
+    if (tid == 0) nmov = 0;
+    __syncthreads();
+    float a[R][NB];
+    unsigned live = 0;  // bit i: my row tid + i * NT exists and is not a pivot row yet
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int r = tid + i * NT;
+        if (r < rows) live |= 1u << i;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) a[i][c] = r < rows ? Lb[(size_t)r * LDL + c] : 0.f;
+    }
+    // (each thread only ever writes Lb rows it owns, which it has just read)
+    for (int j = 0; j < nb; ++j) {
+        unsigned key = 0;
+        int ib = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (live >> i & 1u) {
+                const float v = fabsf(a[i][0]);
+                const unsigned k = v == v ? __float_as_uint(v) + 2u : 1u;
+                if (k > key) key = k, ib = i;
+            }
+        }
+        const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+        const int wl = __ffs(__ballot_sync(0xffffffffu, key == wmax)) - 1;
+        if (lane == wl) {
+            float4* dst = reinterpret_cast<float4*>(crow[j & 1][warp]);
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+                if (ib == i)
+#pragma unroll
+                    for (int c4 = 0; c4 < NB / 4; ++c4)
+                        dst[c4] = make_float4(a[i][4 * c4], a[i][4 * c4 + 1], a[i][4 * c4 + 2], a[i][4 * c4 + 3]);
+            ckey[j & 1][warp] = wmax;
+            cidx[j & 1][warp] = tid + ib * NT;
+        }
+        __syncthreads();
+        const unsigned k2 = lane < NW ? ckey[j & 1][lane] : 0u;
+        const unsigned bmax = __reduce_max_sync(0xffffffffu, k2);
+        const int ws = __ffs(__ballot_sync(0xffffffffu, lane < NW && k2 == bmax)) - 1;
+        const int q = cidx[j & 1][ws];
+        const bool ok = bmax > 2u;  // the column's largest |a| is a positive number
+        const float* u = crow[j & 1][ws];
+        if ((q % NT) == tid) live &= ~(1u << (q / NT));
+        if (tid == 0) {
+            const int pos = phys2pos[q], x = pos2phys[j];
+            pos2phys[j] = q, pos2phys[pos] = x;
+            phys2pos[q] = j, phys2pos[x] = pos;
+            if (!ok && *info == 0) *info = k0 + j + 1;
+        }
+        if (warp == (j % NW) && j + lane < nb) Ub[j][j + lane] = u[lane];
+        const float rp = ok ? __frcp_rn(u[0]) : 0.f;
+        float ml[R];  // minus the multipliers; zero for rows that are not live
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const bool lv = live >> i & 1u;
+            const float l = ok ? a[i][0] * rp : a[i][0];
+            if (lv) Lb[(size_t)(tid + i * NT) * LDL + j] = l;
+            ml[i] = (lv && ok) ? -l : 0.f;
+        }
+        // a[c] = a[c + 1] - l u[c + 1], with u read four entries at a time; registers at or
+        // beyond nb - j - 1 hold no column of the panel after this step and are skipped
+        float4 u0 = reinterpret_cast<const float4*>(u)[0];
+#pragma unroll
+        for (int c4 = 0; c4 < NB / 4; ++c4) {
+            if (4 * c4 >= nb - 1 - j) break;  // the same for every thread
+            const float4 u1 = c4 + 1 < NB / 4 ? reinterpret_cast<const float4*>(u)[c4 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float un[4] = {u0.y, u0.z, u0.w, u1.x};
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = 4 * c4 + e;
+                    a[i][c] = c + 1 < NB ? fmaf(ml[i], un[e], a[i][c + 1]) : 0.f;
+                }
+            u0 = u1;
+        }
+    }
+    __syncthreads();  // Lb, Ub and the position map are final
+    // logical row i: its multipliers from Lb, and for i < nb its U row from Ub
+    for (int i = warp; i < rows; i += NW) {
+        const int ph = pos2phys[i];
+        const float v = (i < nb && lane >= i) ? Ub[i][lane] : Lb[(size_t)ph * LDL + lane];
+        if (lane < nb) A[(size_t)(k0 + i) * n + k0 + lane] = v;
+    }
+    panel_moves<NT>(pos2phys, rows, k0, perm, moves, &nmov);
+}
+
+// For every column c outside the panel: moves the panel's exchanged rows
+// (A[k0 + dst][c] = old A[k0 + src][c], all sources read first); for c right of the
+// panel also solves L11 x = A12[:, c] (unit lower, forward substitution) in place.
+constexpr int ROWS_THREADS = 128;
+__global__ void __launch_bounds__(ROWS_THREADS, 4) lu_rows_kernel(float* __restrict__ A, int n, int k0, int nb,
+                                                               const int* __restrict__ moves)
+{
+    __shared__ int src[2 * NB], dst[2 * NB];
+    __shared__ float L[NB][NB + 1];
+    const int cnt = moves[0];
+    for (int m = threadIdx.x; m < cnt; m += ROWS_THREADS) src[m] = moves[1 + 2 * m], dst[m] = moves[2 + 2 * m];
+    for (int e = threadIdx.x; e < NB * NB; e += ROWS_THREADS) {
+        const int i = e / NB, p = e - i * NB;
+        L[i][p] = (i < nb && p < nb) ? A[(size_t)(k0 + i) * n + k0 + p] : 0.f;
+    }
+    __syncthreads();
+    int c = blockIdx.x * ROWS_THREADS + threadIdx.x;
+    if (c >= n - nb) return;
+    if (c >= k0) c += nb;
+    float v[2 * NB];
+#pragma unroll
+    for (int m = 0; m < 2 * NB; ++m)
+        if (m < cnt) v[m] = A[(size_t)(k0 + src[m]) * n + c];
+#pragma unroll
+    for (int m = 0; m < 2 * NB; ++m)
+        if (m < cnt) A[(size_t)(k0 + dst[m]) * n + c] = v[m];
+    if (c < k0) return;  // a column of L: exchanges only
+    float x[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) x[i] = i < nb ? A[(size_t)(k0 + i) * n + c] : 0.f;
+#pragma unroll
+    for (int p = 0; p < NB - 1; ++p) {  // column-oriented: x[i] -= L[i][p] x[p] for i > p
+#pragma unroll
+        for (int i = p + 1; i < NB; ++i) x[i] = fmaf(-L[i][p], x[p], x[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+        if (i < nb) A[(size_t)(k0 + i) * n + c] = x[i];
 }
 
 // A22 -= L21 U12 over rows/cols [k0+nb, n): 64x64 output tile per block, 4x4 per thread.
@@ -255,96 +501,134 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
     }
 }
 
-// Solves (LU) z = P r in FP32 for a FP64 right-hand side, one block, the vector in
-// shared memory; z returned in FP64.  Each 32-row diagonal block is solved by one
-// warp, then every thread updates one remaining row with a 32-long dot product.
-__global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __restrict__ LU,
-                                                              const int* __restrict__ piv, int n,
-                                                              const double* __restrict__ rhs, double* __restrict__ z)
+// T = LU^T (32x32 tiles through shared memory), so that the solves read the factors
+// column by column with coalesced loads.
+__global__ void __launch_bounds__(256) lu_transpose_kernel(const float* __restrict__ LU, float* __restrict__ T,
+                                                           int n)
 {
-    extern __shared__ float y[];  // y[n], then the pivots as int[n]
-    int* sp = reinterpret_cast<int*>(y + n);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) y[i] = (float)rhs[i], sp[i] = piv[i];
+    __shared__ float t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = by + k, c = bx + threadIdx.x;
+        if (r < n && c < n) t[k][threadIdx.x] = LU[(size_t)r * n + c];
+    }
     __syncthreads();
-    if (tid == 0)  // the row exchanges in order, on shared memory
-        for (int j = 0; j < n; ++j) {
-            const int p = sp[j];
-            if (p != j) {
-                const float t = y[j];
-                y[j] = y[p];
-                y[p] = t;
-            }
-        }
-    __syncthreads();
-    // forward: L (unit lower)
-    for (int b0 = 0; b0 < n; b0 += 32) {
-        const int bn = min(32, n - b0);
-        if (warp == 0) {
-            float v = lane < bn ? y[b0 + lane] : 0.f;
-            const float* row = LU + (size_t)(b0 + (lane < bn ? lane : 0)) * n + b0;
-            float lr[32];
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = bx + k, c = by + threadIdx.x;  // T[r][c] = LU[c][r]
+        if (r < n && c < n) T[(size_t)r * n + c] = t[threadIdx.x][k];
+    }
+}
+
+// Solves (LU) z = P r in FP32 for a FP64 right-hand side (one block, the vector in
+// shared memory) and writes z, or adds it to `out` when `accumulate` is set; both in
+// FP64.  T = LU^T, so column p of the factors is the contiguous row p of T.  The
+// substitution runs over 32-row diagonal blocks: warp 0 solves the block (lane = row,
+// a shuffle per column), then every thread updates one remaining row with a 32-long
+// dot product.  Nothing the loads of a step fetch depends on the solution, so each
+// thread issues its first row's 32 factor entries (coalesced across the warp) and one
+// entry of the next diagonal block before the block is solved; the diagonal blocks
+// are staged in shared memory one step ahead.
+__device__ __forceinline__ float solve_dot(const float* col, int n, const float* yb, int bn)
+{
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int p = 0;
+    for (; p + 4 <= bn; p += 4) {
+        s0 = fmaf(col[(size_t)p * n], yb[p], s0);
+        s1 = fmaf(col[(size_t)(p + 1) * n], yb[p + 1], s1);
+        s2 = fmaf(col[(size_t)(p + 2) * n], yb[p + 2], s2);
+        s3 = fmaf(col[(size_t)(p + 3) * n], yb[p + 3], s3);
+    }
+    for (; p < bn; ++p) s0 = fmaf(col[(size_t)p * n], yb[p], s0);
+    return (s0 + s1) + (s2 + s3);
+}
+
+// sum_p t[p] yb[p] over a 32-entry block of the solution (16-byte aligned, read as float4).
+__device__ __forceinline__ float dot32(const float* t, const float* yb)
+{
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-            for (int p = 0; p < 32; ++p) lr[p] = p < bn ? row[p] : 0.f;  // all loads in flight at once
+    for (int p4 = 0; p4 < 8; ++p4) {
+        const float4 v = reinterpret_cast<const float4*>(yb)[p4];
+        s0 = fmaf(t[4 * p4], v.x, s0);
+        s1 = fmaf(t[4 * p4 + 1], v.y, s1);
+        s0 = fmaf(t[4 * p4 + 2], v.z, s0);
+        s1 = fmaf(t[4 * p4 + 3], v.w, s1);
+    }
+    return s0 + s1;
+}
+
+// Element (tid / 32, tid % 32) of the diagonal block starting at c0 (zero outside it).
+__device__ __forceinline__ float diag_entry(const float* __restrict__ T, int n, int c0)
+{
+    const int p = threadIdx.x >> 5, r = threadIdx.x & 31, cn = min(32, n - c0);
+    return (c0 >= 0 && c0 < n && p < cn && r < cn) ? T[(size_t)(c0 + p) * n + c0 + r] : 0.f;
+}
+
+__global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __restrict__ T,
+                                                              const int* __restrict__ perm, int n,
+                                                              const double* __restrict__ rhs,
+                                                              double* __restrict__ out, int accumulate)
+{
+    extern __shared__ __align__(16) float y[];  // n entries and 32 zeros: a partial block reads zeros past n
+    __shared__ float dblk[2][32][33];  // [slot][column p][row r] of a diagonal block
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nblk = (n + 31) / 32;
+    for (int i = tid; i < n + 32; i += LU_THREADS) y[i] = i < n ? (float)rhs[perm[i]] : 0.f;
+    dblk[0][tid >> 5][tid & 31] = diag_entry(T, n, 0);
+    __syncthreads();
+    // forward: L (unit lower), blocks in increasing order
+    for (int k = 0; k < nblk; ++k) {
+        const int b0 = 32 * k, bn = min(32, n - b0), i0 = b0 + bn + tid;
+        float t0[32];
+#pragma unroll
+        for (int p = 0; p < 32; ++p) t0[p] = (i0 < n && p < bn) ? T[(size_t)(b0 + p) * n + i0] : 0.f;
+        const float dn = diag_entry(T, n, k + 1 < nblk ? b0 + 32 : -1);
+        if (warp == 0) {
+            const float(*D)[33] = dblk[k & 1];
+            float v = lane < bn ? y[b0 + lane] : 0.f;
 #pragma unroll
             for (int p = 0; p < 32; ++p) {
                 const float yp = __shfl_sync(0xffffffffu, v, p);
-                if (lane > p && lane < bn) v = fmaf(-lr[p], yp, v);
+                if (lane > p) v = fmaf(-D[p][lane], yp, v);
             }
             if (lane < bn) y[b0 + lane] = v;
         }
+        dblk[(k + 1) & 1][tid >> 5][tid & 31] = dn;
         __syncthreads();
-        for (int i = b0 + bn + tid; i < n; i += blockDim.x) {
-            const float* row = LU + (size_t)i * n + b0;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int p = 0;
-            for (; p + 4 <= bn; p += 4) {
-                s0 = fmaf(row[p], y[b0 + p], s0);
-                s1 = fmaf(row[p + 1], y[b0 + p + 1], s1);
-                s2 = fmaf(row[p + 2], y[b0 + p + 2], s2);
-                s3 = fmaf(row[p + 3], y[b0 + p + 3], s3);
-            }
-            for (; p < bn; ++p) s0 = fmaf(row[p], y[b0 + p], s0);
-            y[i] -= (s0 + s1) + (s2 + s3);
-        }
+        if (i0 < n) y[i0] -= dot32(t0, y + b0);
+        for (int i = i0 + LU_THREADS; i < n; i += LU_THREADS) y[i] -= solve_dot(T + (size_t)b0 * n + i, n, y + b0, bn);
         __syncthreads();
     }
-    // backward: U
-    for (int b1 = n; b1 > 0; b1 -= 32) {
-        const int b0 = max(0, b1 - 32), bn = b1 - b0;
-        if (warp == 0) {
-            float v = lane < bn ? y[b0 + lane] : 0.f;
-            const float* row = LU + (size_t)(b0 + (lane < bn ? lane : 0)) * n + b0;
-            float lr[32];
+    // backward: U, blocks in decreasing order
+    dblk[0][tid >> 5][tid & 31] = diag_entry(T, n, 32 * (nblk - 1));
+    __syncthreads();
+    for (int k = nblk - 1, s = 0; k >= 0; --k, ++s) {
+        const int b0 = 32 * k, bn = min(32, n - b0), i0 = tid;
+        float t0[32];
 #pragma unroll
-            for (int p = 0; p < 32; ++p) lr[p] = p < bn ? row[p] : 1.f;
+        for (int p = 0; p < 32; ++p) t0[p] = (i0 < b0 && p < bn) ? T[(size_t)(b0 + p) * n + i0] : 0.f;
+        const float dn = diag_entry(T, n, k > 0 ? b0 - 32 : -1);
+        if (warp == 0) {
+            const float(*D)[33] = dblk[s & 1];
+            float v = lane < bn ? y[b0 + lane] : 0.f;
+            const float rd = lane < bn ? 1.0f / D[lane][lane] : 0.f;
 #pragma unroll
             for (int p = 31; p >= 0; --p) {
                 if (p < bn) {
-                    if (lane == p) v /= lr[p];
+                    if (lane == p) v *= rd;
                     const float yp = __shfl_sync(0xffffffffu, v, p);
-                    if (lane < p) v = fmaf(-lr[p], yp, v);
+                    if (lane < p) v = fmaf(-D[p][lane], yp, v);
                 }
             }
             if (lane < bn) y[b0 + lane] = v;
         }
+        dblk[(s + 1) & 1][tid >> 5][tid & 31] = dn;
         __syncthreads();
-        for (int i = tid; i < b0; i += blockDim.x) {
-            const float* row = LU + (size_t)i * n + b0;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int p = 0;
-            for (; p + 4 <= bn; p += 4) {
-                s0 = fmaf(row[p], y[b0 + p], s0);
-                s1 = fmaf(row[p + 1], y[b0 + p + 1], s1);
-                s2 = fmaf(row[p + 2], y[b0 + p + 2], s2);
-                s3 = fmaf(row[p + 3], y[b0 + p + 3], s3);
-            }
-            for (; p < bn; ++p) s0 = fmaf(row[p], y[b0 + p], s0);
-            y[i] -= (s0 + s1) + (s2 + s3);
-        }
+        if (i0 < b0) y[i0] -= dot32(t0, y + b0);
+        for (int i = i0 + LU_THREADS; i < b0; i += LU_THREADS) y[i] -= solve_dot(T + (size_t)b0 * n + i, n, y + b0, bn);
         __syncthreads();
     }
-    for (int i = tid; i < n; i += blockDim.x) z[i] = (double)y[i];
+    for (int i = tid; i < n; i += LU_THREADS) out[i] = accumulate ? out[i] + (double)y[i] : (double)y[i];
 }
 
 // r = b - A x in FP64 (A's FP32 entries promoted exactly); also row |A| sums on the first pass.
@@ -401,30 +685,34 @@ __global__ void __launch_bounds__(1024) norms_kernel(const double* __restrict__ 
     }
 }
 
-__global__ void add_kernel(double* __restrict__ x, const double* __restrict__ d, int n)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] += d[i];
-}
 
 namespace {
 struct AicWs {
-    size_t lu, piv, info, r, d, rowabs, norms, bytes;
+    size_t lu, t, perm, moves, info, pscratch, r, rowabs, norms, bytes;
 };
 AicWs aic_layout(int n)
 {
     Carve cv;
     AicWs w;
     w.lu = cv.take((size_t)n * n * sizeof(float));
-    w.piv = cv.take((size_t)n * sizeof(int));
+    w.t = cv.take((size_t)n * n * sizeof(float));
+    w.perm = cv.take((size_t)n * sizeof(int));
+    w.moves = cv.take((1 + 4 * NB) * sizeof(int));
     w.info = cv.take(sizeof(int));
+    w.pscratch = cv.take((size_t)n * PLD * sizeof(float));
     w.r = cv.take((size_t)n * sizeof(double));
-    w.d = cv.take((size_t)n * sizeof(double));
     w.rowabs = cv.take((size_t)n * sizeof(double));
     w.norms = cv.take(4 * sizeof(double));
     w.bytes = cv.off;
     return w;
 }
+
+// Dynamic shared memory of the panel kernel: the two position maps and as many
+// panel rows as fit; the remaining rows go to the global scratch.  Panels of at most
+// PANEL_REG_ROWS rows use the register kernel (two rows per thread).
+constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
+constexpr int PANEL_REG_NT = 640;
+constexpr int PANEL_REG_ROWS = 2 * PANEL_REG_NT;
 }  // namespace
 
 size_t aic_workspace(int n) { return aic_layout(n).bytes; }
@@ -437,51 +725,66 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     if (n == 0) return VPM_OK;
     const AicWs L = aic_layout(n);
     float* LU = reinterpret_cast<float*>(ws + L.lu);
-    int* piv = reinterpret_cast<int*>(ws + L.piv);
+    float* T = reinterpret_cast<float*>(ws + L.t);
+    int* perm = reinterpret_cast<int*>(ws + L.perm);
+    int* moves = reinterpret_cast<int*>(ws + L.moves);
     int* info = reinterpret_cast<int*>(ws + L.info);
+    float* pscratch = reinterpret_cast<float*>(ws + L.pscratch);
     double* r = reinterpret_cast<double*>(ws + L.r);
-    double* d = reinterpret_cast<double*>(ws + L.d);
     double* rowabs = reinterpret_cast<double*>(ws + L.rowabs);
     double* norms = reinterpret_cast<double*>(ws + L.norms);
-#define VPM_CU(call)                                 \
-    do {                                             \
-        if ((call) != cudaSuccess) {                 \
+#define VPM_CU(call)                                       \
+    do {                                                   \
+        if ((call) != cudaSuccess) {                       \
             *msg = cudaGetErrorString(cudaGetLastError()); \
-            return VPM_ERR_CUDA;                     \
-        }                                            \
+            return VPM_ERR_CUDA;                           \
+        }                                                  \
     } while (0)
     VPM_CU(cudaMemcpyAsync(LU, A, (size_t)n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    VPM_CU(cudaMemsetAsync(info, 0, sizeof(int), st));
-    // panel width 32 when the panel fits in shared memory, else 16, else a global-memory panel
-    const int maxsm = 200 * 1024;
-    const int pnb = ((size_t)n * 33 * sizeof(float) <= (size_t)maxsm) ? 32 : 16;
-    const bool psmem = (size_t)n * (pnb + 1) * sizeof(float) <= (size_t)maxsm;
-    if (psmem) {
-        VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    }
-    VPM_CU(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(n * (sizeof(float) + sizeof(int)))));
-    for (int k0 = 0; k0 < n; k0 += pnb) {
-        const int nb = n - k0 < pnb ? n - k0 : pnb;
+    VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PANEL_SMEM_MAX));
+    VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PANEL_SMEM_MAX));
+    VPM_CU(cudaFuncSetAttribute(lu_panel_reg_kernel<1, PANEL_REG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PANEL_SMEM_MAX));
+    VPM_CU(cudaFuncSetAttribute(lu_panel_reg_kernel<2, PANEL_REG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PANEL_SMEM_MAX));
+    const size_t solve_smem = (size_t)(n + 32) * sizeof(float);
+    VPM_CU(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem));
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int nb = n - k0 < NB ? n - k0 : NB, rows = n - k0;
+        const size_t maps = (size_t)2 * rows * sizeof(int);
         trace_launch();
-        if (psmem)
-            lu_panel_kernel<true><<<1, LU_THREADS, (size_t)(n - k0) * (nb + 1) * sizeof(float), st>>>(LU, n, k0, nb,
-                                                                                                     piv, info);
+        if (rows <= PANEL_REG_ROWS) {
+            const size_t rsmem = maps + (size_t)rows * (NB + 1) * sizeof(float);
+            if (rows <= PANEL_REG_NT)
+                lu_panel_reg_kernel<1, PANEL_REG_NT><<<1, PANEL_REG_NT, rsmem, st>>>(LU, n, k0, nb, info, perm, moves);
+            else
+                lu_panel_reg_kernel<2, PANEL_REG_NT><<<1, PANEL_REG_NT, rsmem, st>>>(LU, n, k0, nb, info, perm, moves);
+            goto panel_done;
+        }
+        {
+        const int srows = (int)std::min<size_t>(rows, (PANEL_SMEM_MAX - maps) / (PLD * sizeof(float)));
+        const size_t psmem = maps + (size_t)srows * PLD * sizeof(float);
+        if (srows == rows)
+            lu_panel_kernel<true><<<1, PANEL_THREADS, psmem, st>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
         else
-            lu_panel_kernel<false><<<1, LU_THREADS, 0, st>>>(LU, n, k0, nb, piv, info);
+            lu_panel_kernel<false><<<1, PANEL_THREADS, psmem, st>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
+        }
+    panel_done:
         if (n - nb > 0) {
             trace_launch();
-            lu_laswp_kernel<<<(n - nb + 255) / 256, 256, 0, st>>>(LU, n, k0, nb, piv);
+            lu_rows_kernel<<<(n - nb + ROWS_THREADS - 1) / ROWS_THREADS, ROWS_THREADS, 0, st>>>(LU, n, k0, nb, moves);
         }
         const int rest = n - k0 - nb;
         if (rest > 0) {
-            trace_launch();
-            lu_trsm_kernel<<<(rest + 255) / 256, 256, 0, st>>>(LU, n, k0, nb);
             dim3 g((rest + 63) / 64, (rest + 63) / 64);
             trace_launch();
             lu_update_kernel<<<g, 256, 0, st>>>(LU, n, k0, nb);
         }
     }
+    trace_launch();
+    lu_transpose_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(LU, T, n);
     VPM_CU(cudaGetLastError());
     int hinfo = 0;
     VPM_CU(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -491,9 +794,8 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         return VPM_ERR_NOT_CONVERGED;
     }
     trace_launch();
-    lu_solve_kernel<<<1, LU_THREADS, n * (sizeof(float) + sizeof(int)), st>>>(LU, piv, n, b, x);
+    lu_solve_kernel<<<1, LU_THREADS, solve_smem, st>>>(T, perm, n, b, x, 0);
     double h[4];
-    double best = INFINITY;
     for (int it = 0;; ++it) {
         trace_launch();
         residual_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, b, x, n, r, it == 0 ? rowabs : nullptr);
@@ -504,7 +806,6 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         VPM_CU(cudaStreamSynchronize(st));
         const double den = h[3] * h[1] + h[2];
         const double be = den > 0.0 ? h[0] / den : (h[0] > 0.0 ? INFINITY : 0.0);
-        best = be < best ? be : best;
         if (iters) *iters = it;
         if (berr) *berr = be;
         if (be <= tol) return VPM_OK;
@@ -513,9 +814,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
             return VPM_ERR_NOT_CONVERGED;
         }
         trace_launch();
-        lu_solve_kernel<<<1, LU_THREADS, n * (sizeof(float) + sizeof(int)), st>>>(LU, piv, n, r, d);
-        trace_launch();
-        add_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, d, n);
+        lu_solve_kernel<<<1, LU_THREADS, solve_smem, st>>>(T, perm, n, r, x, 1);
     }
 #undef VPM_CU
 }

@@ -171,6 +171,34 @@ def test_aic_solve_large_random_and_not_converged(api):
         api.aic_solve(to_dev(Z), to_dev(np.ones(4)), tol=1e-12)
 
 
+@pytest.mark.parametrize("n,kind", [(1, "gauss"), (31, "gauss"), (33, "perm"), (100, "gauss"), (257, "perm"),
+                                    (1500, "gauss")])
+def test_aic_solve_needs_pivoting(api, n, kind):
+    """General matrices whose factorisation needs row exchanges: Gaussian entries, or a
+    row-permuted near-identity (zero diagonal entries, so elimination without exchanges
+    fails).  n = 1500 factors its first panels with the panel held in global memory."""
+    rng = np.random.default_rng(n)
+    if kind == "gauss":
+        A = rng.normal(size=(n, n)).astype(np.float32)
+    else:
+        A = (rng.permutation(np.eye(n)) @ (np.eye(n) + 0.3 * rng.normal(size=(n, n)) / n ** 0.5)).astype(np.float32)
+    b = rng.normal(size=n)
+    x, it, be = api.aic_solve(to_dev(A), to_dev(b), tol=1e-12, max_iter=30)
+    assert be <= 1e-12
+    A64 = A.astype(np.float64)
+    xr = np.linalg.solve(A64, b)
+    cond = np.linalg.cond(A64)
+    assert rel_l2(x.cpu().numpy(), xr) <= max(1e-10, 10 * cond * 1e-12)
+
+
+def test_aic_solve_zero_column_is_reported(api):
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(100, 100)).astype(np.float32)
+    A[:, 40] = 0.0  # singular: the elimination meets an all-zero column at index 40
+    with pytest.raises(Exception, match="singular"):
+        api.aic_solve(to_dev(A), to_dev(rng.normal(size=100)), tol=1e-12)
+
+
 @pytest.mark.parametrize("compensated", [True, False])
 def test_backward_vs_oracle_adjoint(api, compensated):
     w = synth.make(4, n=5000)
