@@ -55,6 +55,8 @@ def _load():
             i64 = ctypes.c_int64
             d = ctypes.c_double
             i = ctypes.c_int
+            IP = ctypes.POINTER(ctypes.c_int)
+            LP = ctypes.POINTER(ctypes.c_int64)
             sig = {
                 "orc_blob_gF": [P, i64, P, P],
                 "orc_p2p": [P, P, i64, P, i64, d, P, P],
@@ -68,11 +70,14 @@ def _load():
                 "orc_aic_rhs": [P, P, P, i64, P],
                 "orc_lu_solve": [P, P, i64, P],
                 "orc_p2p_adjoint": [P, P, i64, P, i64, d, P, P, P],
+                "orc_wake_convert": [P, P, P, P, IP, IP, i64, d, i, i, i64, P, P, LP],
+                "orc_wake_row_edges": [P, P, P, i64, P, P, P, P, IP, IP],
             }
+            rtype = {"orc_lu_solve": ctypes.c_int, "orc_wake_convert": ctypes.c_int64}
             for name, args in sig.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
-                fn.restype = ctypes.c_int if name == "orc_lu_solve" else None
+                fn.restype = rtype.get(name)
             _lib = lib
     return _lib
 
@@ -222,3 +227,45 @@ def p2p_adjoint(pos, strength, tgt, sigma, g):
     dx, dG = np.zeros((ns, 3)), np.zeros((ns, 3))
     _load().orc_p2p_adjoint(_p(pos), _p(strength), ns, _p(tgt), tgt.shape[0], float(sigma), _p(g), _p(dx), _p(dG))
     return dx, dG
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def wake_convert(a, b, gamma, gamma_nb, has_nb, trailed, ds_tip, n_tip, n_shed=1):
+    """Particles (x [n][3], G [n][3]) and per-edge counts from wake edges (Eq. 6-8)."""
+    a, b = _f64(a).reshape(-1, 3), _f64(b).reshape(-1, 3)
+    m = a.shape[0]
+    g = _f64(gamma).ravel()
+    gnb = _f64(np.zeros(m) if gamma_nb is None else gamma_nb).ravel()
+    hn = np.ascontiguousarray(np.zeros(m) if has_nb is None else has_nb, dtype=np.int32)
+    tr = np.ascontiguousarray(trailed, dtype=np.int32)
+    counts = np.zeros(m, dtype=np.int64)
+    lib = _load()
+    cap = 0
+    x = np.zeros((1, 3))
+    G = np.zeros((1, 3))
+    total = lib.orc_wake_convert(_p(a), _p(b), _p(g), _p(gnb), _ip(hn), _ip(tr), m, float(ds_tip), int(n_tip),
+                                 int(n_shed), cap, _p(x), _p(G), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    total = int(counts.sum())
+    x = np.zeros((max(total, 1), 3))
+    G = np.zeros((max(total, 1), 3))
+    got = lib.orc_wake_convert(_p(a), _p(b), _p(g), _p(gnb), _ip(hn), _ip(tr), m, float(ds_tip), int(n_tip),
+                               int(n_shed), total, _p(x), _p(G), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    assert got == total
+    return x[:total], G[:total], counts
+
+
+def wake_row_edges(U, D, gamma):
+    """Edges of one wake panel row (U, D node lines [S+1][3], panel circulations [S])."""
+    U, D = _f64(U).reshape(-1, 3), _f64(D).reshape(-1, 3)
+    g = _f64(gamma).ravel()
+    S = g.size
+    ne = 3 * S + 1
+    a, b = np.zeros((ne, 3)), np.zeros((ne, 3))
+    ge, gnb = np.zeros(ne), np.zeros(ne)
+    hn = np.zeros(ne, dtype=np.int32)
+    tr = np.zeros(ne, dtype=np.int32)
+    _load().orc_wake_row_edges(_p(U), _p(D), _p(g), S, _p(a), _p(b), _p(ge), _p(gnb), _ip(hn), _ip(tr))
+    return a, b, ge, gnb, hn, tr

@@ -537,3 +537,100 @@ void orc_p2p_adjoint(const double* pos, const double* str, int64_t n_src, const 
         }
     }
 }
+
+/* ------------------------------------------------------------------------------
+ * Wake panel -> particle conversion (Sec. II.C, Eq. 6-8).
+ *
+ * An edge is one straight vortex line of the wake lattice, from a to b, owned by the
+ * wake panel of circulation gamma (the ring's circulation runs along a -> b).  Its
+ * circulation difference (Eq. 7) is gamma - gamma_nb when the panel on the other side
+ * of the edge is converted together with it (has_nb), else gamma.  The edge becomes
+ * n particles of strength Delta Gamma (b - a) / n (Eq. 6).  A trailed (streamwise)
+ * edge gets n = ceil(|b - a| / ds_tip * n_tip) particles (Eq. 8, the adaptive count
+ * scaled on the tip edge of length ds_tip that carries n_tip); a shed (spanwise) edge
+ * gets n_shed (n_shed = n_tip = 1 and ds_tip = |b - a| is the conventional strategy).
+ *
+ * Readings: the paper places the particles along the edge without stating where; they
+ * sit at the centres of the n equal pieces, x_k = a + (k + 1/2)/n (b - a).  The count
+ * is computed in double precision as ceil((len / ds_tip) * n_tip) with
+ * len = sqrt(dx*dx + dy*dy + dz*dz) (no contraction; the library takes the same
+ * integer decision in the same precision).  Particles are written edge by edge.
+ *
+ * Edges a[m][3], b[m][3]; outputs x[cap][3], G[cap][3], counts[m].  Returns the number
+ * of particles, or -1 (nothing written) if it exceeds cap.
+ * ------------------------------------------------------------------------------ */
+static int64_t wake_count(const double* a, const double* b, int trailed, double ds_tip, int n_tip, int n_shed)
+{
+    if (!trailed) return n_shed;
+    const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    const double len = sqrt(dx * dx + dy * dy + dz * dz);
+    const double v = ceil((len / ds_tip) * (double)n_tip);
+    return v < 1.0 ? 1 : (int64_t)v;  /* a zero-length edge still gets one particle (of zero strength) */
+}
+
+int64_t orc_wake_convert(const double* a, const double* b, const double* gamma, const double* gamma_nb,
+                         const int* has_nb, const int* trailed, int64_t m, double ds_tip, int n_tip, int n_shed,
+                         int64_t cap, double* x, double* G, int64_t* counts)
+{
+    int64_t total = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        counts[i] = wake_count(&a[3 * i], &b[3 * i], trailed[i], ds_tip, n_tip, n_shed);
+        total += counts[i];
+    }
+    if (total > cap) return -1;
+    int64_t o = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        const double* ai = &a[3 * i];
+        const double* bi = &b[3 * i];
+        const double dG = (has_nb && has_nb[i]) ? gamma[i] - gamma_nb[i] : gamma[i]; /* Eq. 7 */
+        const double d[3] = {bi[0] - ai[0], bi[1] - ai[1], bi[2] - ai[2]};
+        const int64_t n = counts[i];
+        for (int64_t k = 0; k < n; ++k, ++o) {
+            const double t = ((double)k + 0.5) / (double)n;
+            for (int c = 0; c < 3; ++c) {
+                x[3 * o + c] = ai[c] + t * d[c];
+                G[3 * o + c] = (dG * d[c]) / (double)n; /* Eq. 6 */
+            }
+        }
+    }
+    return total;
+}
+
+/* The edges of one wake panel row for its conversion.  The row has S panels between
+ * an upstream node line U[0..S] (towards the blade) and a downstream line D[0..S];
+ * panel p is the ring U[p] -> U[p+1] -> D[p+1] -> D[p] -> U[p] of circulation
+ * gamma[p].  Edges, in this order (3 S + 1 of them):
+ *   trailed q = 0..S-1: D[q] -> U[q], owned by panel q, neighbour panel q-1 (q > 0);
+ *   trailed S:          U[S] -> D[S], owned by panel S-1, no neighbour;
+ *   shed back p:        D[p+1] -> D[p], owned by panel p, no neighbour (the older row
+ *                       is converted already);
+ *   shed front p:       U[p] -> U[p+1], owned by panel p, no neighbour (the younger row
+ *                       stays a panel row and keeps its own ring, so the converted
+ *                       line carries this ring's strength alone).
+ * U, D [S+1][3]; outputs a, b [3S+1][3], g, gnb [3S+1], has_nb, trailed [3S+1]. */
+void orc_wake_row_edges(const double* U, const double* D, const double* gamma, int64_t S, double* a, double* b,
+                        double* g, double* gnb, int* has_nb, int* trailed)
+{
+    int64_t e = 0;
+    for (int64_t q = 0; q <= S; ++q, ++e) {
+        const int end = q == S;
+        const double* from = end ? &U[3 * q] : &D[3 * q];
+        const double* to = end ? &D[3 * q] : &U[3 * q];
+        memcpy(&a[3 * e], from, 3 * sizeof(double));
+        memcpy(&b[3 * e], to, 3 * sizeof(double));
+        g[e] = end ? gamma[S - 1] : gamma[q];
+        has_nb[e] = (!end && q > 0);
+        gnb[e] = has_nb[e] ? gamma[q - 1] : 0.0;
+        trailed[e] = 1;
+    }
+    for (int64_t p = 0; p < S; ++p, ++e) {
+        memcpy(&a[3 * e], &D[3 * (p + 1)], 3 * sizeof(double));
+        memcpy(&b[3 * e], &D[3 * p], 3 * sizeof(double));
+        g[e] = gamma[p], gnb[e] = 0.0, has_nb[e] = 0, trailed[e] = 0;
+    }
+    for (int64_t p = 0; p < S; ++p, ++e) {
+        memcpy(&a[3 * e], &U[3 * p], 3 * sizeof(double));
+        memcpy(&b[3 * e], &U[3 * (p + 1)], 3 * sizeof(double));
+        g[e] = gamma[p], gnb[e] = 0.0, has_nb[e] = 0, trailed[e] = 0;
+    }
+}

@@ -11,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "vpm_oracle.c")
 PINS = ["tests/test_oracle_blob.py", "tests/test_oracle_segments.py", "tests/test_oracle_local.py",
-        "tests/test_oracle_rk3_lu_adjoint.py"]
+        "tests/test_oracle_rk3_lu_adjoint.py", "tests/test_oracle_wake.py"]
 
 MUTATIONS = {
     "taylor_denominator": ("qs += term / (2.0 * k + 3.0);", "qs += term / (2.0 * k + 5.0);"),
@@ -31,6 +31,12 @@ MUTATIONS = {
     "lu_no_pivoting": ("if (fabs(A[n * i + k]) > fabs(A[n * piv + k])) piv = i;", "if (0) piv = i;"),
     "adjoint_sign": ("ax[b] -= t;", "ax[b] += t;"),
     "aic_normal_index": ("A[n * k + l] = dot(tot, &normal[4 * k]);", "A[n * k + l] = dot(tot, &normal[4 * l]);"),
+    "wake_count_floor": ("const double v = ceil((len / ds_tip) * (double)n_tip);",
+                         "const double v = floor((len / ds_tip) * (double)n_tip);"),
+    "wake_position_offset": ("const double t = ((double)k + 0.5) / (double)n;", "const double t = (double)k / (double)n;"),
+    "wake_neighbour_sign": ("? gamma[i] - gamma_nb[i] : gamma[i]; /* Eq. 7 */", "? gamma[i] + gamma_nb[i] : gamma[i]; /* Eq. 7 */"),
+    "wake_back_edge_direction": ("memcpy(&a[3 * e], &D[3 * (p + 1)], 3 * sizeof(double));\n        memcpy(&b[3 * e], &D[3 * p], 3 * sizeof(double));",
+                                 "memcpy(&a[3 * e], &D[3 * p], 3 * sizeof(double));\n        memcpy(&b[3 * e], &D[3 * (p + 1)], 3 * sizeof(double));"),
 }
 
 
