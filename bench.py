@@ -34,6 +34,29 @@ UNIT = "pair-interactions/s"
 FLOPS_P2P = 54   # u + grad u, far-field operation tree, FFMA = 2 flops
 FLOPS_SEG = 120  # Vatistas segment u + grad u, same counting convention
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one sweep_kernel<grad, compensated, stretch> launch on the
+# hover wake (100,000 particles, 5,120 segments), from one ncu capture of that launch
+# (profiles/sweep_kernel_hover4_100k.md); valid only while the kernel's sources hash to
+# SWEEP_SRC_SHA256, else the bench reports traffic null.
+SWEEP_TRAFFIC_BYTES = 11_803_136 + 2_560
+SWEEP_SRC_SHA256 = "8d27b9735ae614f14ea988655a83be0df81eeedb1092960b32c3f59d86c14e7e"
+SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
+             "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
+
+
+def sweep_traffic(n, m):
+    """The captured DRAM traffic of the sweep launch, if the capture matches the sources
+    and the workload (hover, 100,000 particles, 5,120 segments)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in SWEEP_SRC:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != SWEEP_SRC_SHA256 or n != 100_000 or m != 5_120:
+        return None
+    return SWEEP_TRAFFIC_BYTES
 
 
 def parse():
@@ -118,11 +141,11 @@ class ClockSampler:
 def oracle_rate(w, seconds, cores):
     """P2P u + grad u pair interactions/s of the FP64 oracle on a bounded sample of
     targets against all sources (sized to take about `seconds`)."""
-    os.environ["OMP_NUM_THREADS"] = str(cores)
     import oracle
     from paper_2511_11430_gb300 import synth
 
     oracle.build()
+    oracle.set_threads(cores)
     n = w.n
     k = 64
     while True:
@@ -134,6 +157,12 @@ def oracle_rate(w, seconds, cores):
             rate = k * (n - 1) / dt
             return rate, k, dt
         k = min(n, int(k * max(2.0, seconds / max(dt, 1e-3) * 0.6)))
+
+
+def oracle_threads_default(cores):
+    import oracle
+
+    oracle.set_threads(cores)
 
 
 def host_cores():
@@ -293,7 +322,7 @@ def run_ours(args):
     flops_launch = FLOPS_P2P * n * (n - 1) + FLOPS_SEG * n * m
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "sweep_kernel<grad, compensated>", "launches": nl,
+            "traffic": sweep_traffic(n, m), "kernel": "sweep_kernel<grad, compensated>", "launches": nl,
             "avg_launch_ms": avg_ms, "flops_per_launch": flops_launch,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {sm_max:.0f} MHz (fallback-free derivation)"}
     if clk and clk.get("sm_mhz"):
@@ -369,12 +398,47 @@ def run_ours(args):
         except Exception as ex:  # the error report is informative, never fatal
             err = {"unavailable": str(ex)[:200]}
 
+    # the wake panel -> particle conversion (Eq. 6-8), outside the timed step: the edges of
+    # 2,000 wake panel rows of the 4-blade hover rotor, n_tip = 4 (informative)
+    wake = None
+    if rank == 0:
+        try:
+            ea, eb, eg, egn, ehn, etr, ds_tip = synth.rotor_wake_edges(5, 2000)
+            Td = lambda a_, dt_: torch.from_numpy(np.ascontiguousarray(a_)).to(dt_).to(dev)
+            wa, wb, wg, wgn = (Td(q, torch.float64) for q in (ea, eb, eg, egn))
+            whn, wtr = Td(ehn, torch.int32), Td(etr, torch.int32)
+            wws = api.Workspace(dev)
+            xw, Gw = api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, ws=wws)
+            npart = int(xw.shape[1])
+            reps = 5
+            torch.cuda.synchronize()
+            st = torch.cuda.current_stream()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, capacity=npart, ws=wws)
+            e1.record(st)
+            e1.synchronize()
+            wms = e0.elapsed_time(e1) / reps
+            m_e = len(ea)
+            algo = 72 * m_e + 16 * m_e + 48 * npart  # edges in, counts/offsets out, particles out
+            wake = {"edges": m_e, "particles": npart, "ms": wms, "particles_per_s": npart / (wms * 1e-3),
+                    "algorithmic_bytes": algo, "achieved_gbs": algo / (wms * 1e-3) / 1e9,
+                    "note": "device time of one vpm_wake_convert call incl. its one host sync"}
+        except Exception as ex:  # informative, never fatal
+            wake = {"unavailable": str(ex)[:200]}
+
     cpu = None
     if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         rate, k, dt = oracle_rate(w, 12.0 if args.cpu_seconds is None else args.cpu_seconds, cores)
+        rate1, k1, dt1 = oracle_rate(w, 3.0, 1)
+        oracle_threads_default(cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{k} sampled targets x all {n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)"}
+               "sample": f"{k} sampled targets x all {n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)",
+               "single_thread": {"value": rate1, "unit": UNIT,
+                                 "sample": f"{k1} sampled targets x all {n:,} sources ({dt1:.1f} s)"}}
 
     if dist is not None:
         dist.barrier()
@@ -390,7 +454,7 @@ def run_ours(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                        "parallelism": "replicas" if ws_n > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_total),
-            "clocks": clk, "plain": plain, "error": err,
+            "clocks": clk, "plain": plain, "error": err, "wake_convert": wake,
             "kernel_ms": {"sweep_grad": [nl, sms_ms], "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
                           "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL])},
         }

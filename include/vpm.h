@@ -67,6 +67,8 @@ typedef enum vpm_status {
 #define VPM_OP_STEP 4
 #define VPM_OP_AIC_SOLVE 5
 #define VPM_OP_BACKWARD 6
+#define VPM_OP_WAKE_CONVERT 7
+#define VPM_OP_WAKE_ROW 8
 
 /* Largest particle / target / segment count accepted (int32 indexing). */
 #define VPM_MAX_ITEMS (1 << 30)
@@ -101,6 +103,7 @@ vpm_status vpm_device_error(int* code);
  *   VPM_OP_RHS, VPM_OP_STEP: n_src particles, m_seg segments       (n_tgt ignored)
  *   VPM_OP_AIC_SOLVE: order n_tgt                                  (others ignored)
  *   VPM_OP_BACKWARD:  n_src particles, n_tgt targets
+ *   VPM_OP_WAKE_CONVERT: n_src edges;  VPM_OP_WAKE_ROW: n_src panels of the row
  * `flags` as passed to the operation.  Host-only; does not launch. */
 vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_seg, int flags, size_t* bytes);
 
@@ -190,6 +193,54 @@ vpm_status aic_solve(const float* A_d, const double* b_d, double* x_d, int n, do
 vpm_status vpm_induce_backward(const float* src_pos_d, const float* src_str_d, int64_t n_src, const float* tgt_d,
                                int64_t n_tgt, float sigma, int flags, const float* grad_out_d, float* dL_dx_d,
                                float* dL_dG_d, void* ws_d, size_t ws_bytes, void* stream);
+
+/* ---- self-test of the bounded device waits (no counterpart in the paper) -----
+ * Every wait inside the library's kernels (on an mbarrier phase) gives up after a
+ * time limit, latches VPM_ERR_LIMIT in the device error word and lets the kernel
+ * return.  This launches one wait on a phase that nothing completes, with a limit of
+ * limit_ms (0 < limit_ms <= 2000), and synchronises `stream`: *completed (host)
+ * receives 0 when the wait gave up as it must, 1 if the phase completed.  The timeout
+ * is then reported (and cleared) by vpm_device_error.  Allocates nothing. */
+vpm_status vpm_selftest_wait(double limit_ms, int* completed, void* stream);
+
+/* ---- wake panel -> particle conversion (Sec. II.C, Eq. 6-8) ----------------
+ * Edge i is a straight vortex line a_i -> b_i of the wake lattice, owned by a wake
+ * panel of circulation gamma_i (its ring's circulation runs along a_i -> b_i).
+ * Delta Gamma_i = gamma_i - gamma_nb_i if has_nb_i (the panel across the edge is
+ * converted too), else gamma_i (Eq. 7).  A trailed (streamwise) edge becomes
+ *   n_i = ceil(|b_i - a_i| / ds_tip * n_tip)                         (Eq. 8)
+ * particles, ds_tip being the length of the tip's trailed edge, which gets n_tip; a
+ * shed (spanwise) edge becomes n_shed particles (n_tip = n_shed = 1 with every edge
+ * no longer than ds_tip is the conventional one-particle-per-edge strategy).  The
+ * particles of an edge sit at the centres of its n_i equal pieces,
+ *   x_ik = a_i + (k + 1/2)/n_i (b_i - a_i),  Gamma_ik = Delta Gamma_i (b_i - a_i) / n_i   (Eq. 6),
+ * and are written edge after edge.  n_i is decided in FP64 with correctly rounded
+ * operations, as (|b - a| / ds_tip) * n_tip with |b - a| = sqrt((dx dx + dy dy) + dz dz).
+ *   edge_a_d, edge_b_d [m][3] double; gamma_d [m] double; gamma_nb_d [m] double and
+ *   has_nb_d [m] int, both NULL when no edge has a converted neighbour; trailed_d [m]
+ *   int (1 trailed, 0 shed); ds_tip > 0; n_tip, n_shed >= 1.
+ *   x_d, G_d [3][ld_out] double, planar (row c holds component c), the particle
+ *   positions and strengths; *n_out (host) receives the particle count.
+ * More particles than ld_out gives VPM_ERR_LIMIT with nothing written (and *n_out the
+ * count that would be needed).  Synchronises `stream` once (to read the count). */
+vpm_status vpm_wake_convert(const double* edge_a_d, const double* edge_b_d, const double* gamma_d,
+                            const double* gamma_nb_d, const int* has_nb_d, const int* trailed_d, int64_t m,
+                            double ds_tip, int n_tip, int n_shed, double* x_d, double* G_d, int64_t ld_out,
+                            int64_t* n_out, void* ws_d, size_t ws_bytes, void* stream);
+
+/* The same conversion for one wake panel row (the oldest row of the near wake).  The
+ * row has S >= 1 panels between an upstream node line U[0..S] (towards the blade)
+ * and a downstream line D[0..S]; panel p is the ring U[p] -> U[p+1] -> D[p+1] ->
+ * D[p] -> U[p] of circulation gamma[p].  Its 3 S + 1 edges, in this order:
+ *   trailed q = 0..S-1: D[q] -> U[q] of panel q, neighbour panel q-1 when q > 0;
+ *   trailed S:          U[S] -> D[S] of panel S-1;
+ *   shed p = 0..S-1:    D[p+1] -> D[p] of panel p (the older row is particles already);
+ *   shed p = 0..S-1:    U[p] -> U[p+1] of panel p (the younger row stays a panel row
+ *                       and keeps its own ring, so this line carries gamma[p] alone).
+ *   U_d, D_d [S+1][3] double; gamma_d [S] double; other arguments as vpm_wake_convert. */
+vpm_status vpm_wake_convert_row(const double* U_d, const double* D_d, const double* gamma_d, int64_t S, double ds_tip,
+                                int n_tip, int n_shed, double* x_d, double* G_d, int64_t ld_out, int64_t* n_out,
+                                void* ws_d, size_t ws_bytes, void* stream);
 
 /* ---- velocity sweep without a caller workspace ------------------------------
  * The paper has no counterpart: this is a library convenience.  vpm_induce for

@@ -72,6 +72,7 @@ def _load():
                 "orc_p2p_adjoint": [P, P, i64, P, i64, d, P, P, P],
                 "orc_wake_convert": [P, P, P, P, IP, IP, i64, d, i, i, i64, P, P, LP],
                 "orc_wake_row_edges": [P, P, P, i64, P, P, P, P, IP, IP],
+                "orc_set_threads": [i],
             }
             rtype = {"orc_lu_solve": ctypes.c_int, "orc_wake_convert": ctypes.c_int64}
             for name, args in sig.items():
@@ -101,6 +102,7 @@ def set_threads(n: int | None) -> None:
     """Set the OpenMP thread count the oracle uses (None: leave the default)."""
     if n is not None:
         os.environ["OMP_NUM_THREADS"] = str(int(n))
+        _load().orc_set_threads(int(n))
 
 
 def blob_gF(rho):

@@ -20,6 +20,9 @@
  * Readings of the paper that this file fixes are listed next to the routine.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -633,4 +636,15 @@ void orc_wake_row_edges(const double* U, const double* D, const double* gamma, i
         memcpy(&b[3 * e], &U[3 * (p + 1)], 3 * sizeof(double));
         g[e] = gamma[p], gnb[e] = 0.0, has_nb[e] = 0, trailed[e] = 0;
     }
+}
+
+/* Thread count of the OpenMP loops above (the CPU baseline reports a multi-core and a
+ * single-thread figure). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }

@@ -30,6 +30,8 @@ VPM_OP_RHS = 3
 VPM_OP_STEP = 4
 VPM_OP_AIC_SOLVE = 5
 VPM_OP_BACKWARD = 6
+VPM_OP_WAKE_CONVERT = 7
+VPM_OP_WAKE_ROW = 8
 
 VPM_TRACE_ALL = 0
 VPM_TRACE_SWEEP = 1
@@ -86,6 +88,9 @@ SIGNATURES = {
     "aic_solve": (_INT, [_P, _P, _P, _INT, _D, _INT, ctypes.POINTER(_INT), ctypes.POINTER(_D), _P, _SZ, _P]),
     "vpm_induce_backward": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P, _P, _SZ, _P]),
     "vpm_induce_noalloc": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P]),
+    "vpm_selftest_wait": (_INT, [_D, _P, _P]),
+    "vpm_wake_convert": (_INT, [_P, _P, _P, _P, _P, _P, _I64, _D, _INT, _INT, _P, _P, _I64, _P, _P, _SZ, _P]),
+    "vpm_wake_convert_row": (_INT, [_P, _P, _P, _I64, _D, _INT, _INT, _P, _P, _I64, _P, _P, _SZ, _P]),
     "vpm_trace_enable": (_INT, [_INT]),
     "vpm_trace_reset": (_INT, []),
     "vpm_trace_read": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_D)]),

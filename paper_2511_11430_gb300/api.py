@@ -277,3 +277,64 @@ def device_error() -> int:
     code = ctypes.c_int(0)
     check(_lib.load().vpm_device_error(ctypes.byref(code)))
     return int(code.value)
+
+
+def _wake_out(ld, device):
+    x = torch.empty((3, max(ld, 1)), dtype=torch.float64, device=device)
+    return x, torch.empty_like(x)
+
+
+def wake_convert(edge_a, edge_b, gamma, trailed, ds_tip: float, n_tip: int, n_shed: int = 1, gamma_nb=None,
+                 has_nb=None, capacity: int | None = None, ws=None):
+    """Particles from wake edges (Sec. II.C, Eq. 6-8): returns x [3, n] and Gamma [3, n]
+    (float64, planar).  ``capacity`` bounds n (default: enough for every edge's count)."""
+    _need(edge_a, "edge_a", torch.float64, (3,))
+    _need(edge_b, "edge_b", torch.float64, (3,))
+    _need(gamma, "gamma", torch.float64)
+    _need(trailed, "trailed", torch.int32)
+    if has_nb is not None:
+        _need(has_nb, "has_nb", torch.int32)
+        _need(gamma_nb, "gamma_nb", torch.float64)
+    m = edge_a.shape[0]
+    lib = _lib.load()
+    w = _ws(ws, workspace_size(_lib.VPM_OP_WAKE_CONVERT, m, 0, 0, 0), edge_a.device)
+    n_out = ctypes.c_int64(0)
+    cap = capacity
+    if cap is None:  # ask for the count first (nothing is written when it does not fit)
+        st = lib.vpm_wake_convert(_void(edge_a), _void(edge_b), _void(gamma), _void(gamma_nb), _void(has_nb),
+                                  _void(trailed), m, float(ds_tip), int(n_tip), int(n_shed), None, None, 0,
+                                  ctypes.byref(n_out), _void(w), w.numel(), _stream())
+        if st not in (_lib.VPM_OK, _lib.VPM_ERR_LIMIT):
+            check(st)
+        cap = int(n_out.value)
+    x, G = _wake_out(cap, edge_a.device)
+    st = lib.vpm_wake_convert(_void(edge_a), _void(edge_b), _void(gamma), _void(gamma_nb), _void(has_nb),
+                              _void(trailed), m, float(ds_tip), int(n_tip), int(n_shed), _void(x), _void(G), cap,
+                              ctypes.byref(n_out), _void(w), w.numel(), _stream())
+    check(st)
+    n = int(n_out.value)
+    return x[:, :n], G[:, :n]
+
+
+def wake_convert_row(U, D, gamma, ds_tip: float, n_tip: int, n_shed: int = 1, capacity: int | None = None, ws=None):
+    """Particles from one wake panel row (node lines U, D [S+1, 3], circulations [S])."""
+    _need(U, "U", torch.float64, (3,))
+    _need(D, "D", torch.float64, (3,))
+    _need(gamma, "gamma", torch.float64)
+    S = gamma.shape[0]
+    lib = _lib.load()
+    w = _ws(ws, workspace_size(_lib.VPM_OP_WAKE_ROW, S, 0, 0, 0), U.device)
+    n_out = ctypes.c_int64(0)
+    cap = capacity
+    if cap is None:
+        st = lib.vpm_wake_convert_row(_void(U), _void(D), _void(gamma), S, float(ds_tip), int(n_tip), int(n_shed),
+                                      None, None, 0, ctypes.byref(n_out), _void(w), w.numel(), _stream())
+        if st not in (_lib.VPM_OK, _lib.VPM_ERR_LIMIT):
+            check(st)
+        cap = int(n_out.value)
+    x, G = _wake_out(cap, U.device)
+    st = lib.vpm_wake_convert_row(_void(U), _void(D), _void(gamma), S, float(ds_tip), int(n_tip), int(n_shed),
+                                  _void(x), _void(G), cap, ctypes.byref(n_out), _void(w), w.numel(), _stream())
+    check(st)
+    n = int(n_out.value)
+    return x[:, :n], G[:, :n]

@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_reg_kernel(float* __restrict__
     constexpr int NW = NT / 32;
     constexpr int LDL = NB + 1;
     static_assert(NW <= 32, "one warp reduces the published candidates");
+    static_assert(R <= 6, "the publication switch covers six rows per thread");
     extern __shared__ float Lb[];  // [rows][LDL], then pos2phys[rows], phys2pos[rows]
     __shared__ __align__(16) float crow[2][NW][NB];
     __shared__ float Ub[NB][NB + 1];
@@ -320,18 +321,18 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_reg_kernel(float* __restrict__
         for (int i = tid; i < n; i += NT) perm[i] = i;
         if (tid == 0) *info = 0;
     }
-    // stage the panel in Lb: a warp per row, a lane per column, eight rows in flight
-    for (int r0 = warp; r0 < rows; r0 += 8 * NW) {
-        float v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int r = r0 + k * NW;
-            v[k] = (r < rows && lane < nb) ? A[(size_t)(k0 + r) * n + k0 + lane] : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (r0 + k * NW < rows) Lb[(size_t)(r0 + k * NW) * LDL + lane] = v[k];
+    // stage the panel in Lb: a warp per row, a lane per column, every copy in flight at
+    // once (cp.async, one wait); a narrow last panel is zero-filled
+    for (int r = warp; r < rows; r += NW) {
+        float* dst = Lb + (size_t)r * LDL + lane;
+        if (lane < nb)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)),
+                         "l"(A + (size_t)(k0 + r) * n + k0 + lane)
+                         : "memory");
+        else
+            *dst = 0.f;
     }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     for (int i = tid; i < rows; i += NT) pos2phys[i] = i, phys2pos[i] = i;
     if (tid == 0) nmov = 0;
     __syncthreads();
@@ -360,12 +361,20 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_reg_kernel(float* __restrict__
         const int wl = __ffs(__ballot_sync(0xffffffffu, key == wmax)) - 1;
         if (lane == wl) {
             float4* dst = reinterpret_cast<float4*>(crow[j & 1][warp]);
+            auto put = [&](const float* row) {
 #pragma unroll
-            for (int i = 0; i < R; ++i)
-                if (ib == i)
-#pragma unroll
-                    for (int c4 = 0; c4 < NB / 4; ++c4)
-                        dst[c4] = make_float4(a[i][4 * c4], a[i][4 * c4 + 1], a[i][4 * c4 + 2], a[i][4 * c4 + 3]);
+                for (int c4 = 0; c4 < NB / 4; ++c4)
+                    dst[c4] = make_float4(row[4 * c4], row[4 * c4 + 1], row[4 * c4 + 2], row[4 * c4 + 3]);
+            };
+            switch (ib) {  // one branch taken: only the winning row's stores are issued
+            case 0: put(a[0]); break;
+            case 1: if constexpr (R > 1) put(a[R > 1 ? 1 : 0]); break;
+            case 2: if constexpr (R > 2) put(a[R > 2 ? 2 : 0]); break;
+            case 3: if constexpr (R > 3) put(a[R > 3 ? 3 : 0]); break;
+            case 4: if constexpr (R > 4) put(a[R > 4 ? 4 : 0]); break;
+            case 5: if constexpr (R > 5) put(a[R > 5 ? 5 : 0]); break;
+            default: break;
+            }
             ckey[j & 1][warp] = wmax;
             cidx[j & 1][warp] = tid + ib * NT;
         }
@@ -461,20 +470,21 @@ __global__ void __launch_bounds__(ROWS_THREADS, 4) lu_rows_kernel(float* __restr
         if (i < nb) A[(size_t)(k0 + i) * n + c] = x[i];
 }
 
-// A22 -= L21 U12 over rows/cols [k0+nb, n): 64x64 output tile per block, 4x4 per thread.
-__global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, int n, int k0, int nb)
+// A22 -= L21 U12 over rows [k0+nb, n) and columns [cb, ce): 64x64 output tile per
+// block, 4x4 per thread.
+__global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, int n, int k0, int nb, int cb, int ce)
 {
     __shared__ float Ls[64][NB + 1];
     __shared__ float Us[NB][64 + 1];
     const int s0 = k0 + nb;
-    const int r0 = s0 + blockIdx.y * 64, c0 = s0 + blockIdx.x * 64;
+    const int r0 = s0 + blockIdx.y * 64, c0 = cb + blockIdx.x * 64;
     for (int e = threadIdx.x; e < 64 * NB; e += blockDim.x) {
         const int i = e / NB, p = e % NB;
         const int r = r0 + i;
         Ls[i][p] = (r < n && p < nb) ? A[(size_t)r * n + k0 + p] : 0.f;
         const int pp = e / 64, cc = e % 64;
         const int c = c0 + cc;
-        Us[pp][cc] = (c < n && pp < nb) ? A[(size_t)(k0 + pp) * n + c] : 0.f;
+        Us[pp][cc] = (c < ce && pp < nb) ? A[(size_t)(k0 + pp) * n + c] : 0.f;
     }
     __syncthreads();
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -496,7 +506,7 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int c = c0 + tx * 4 + w;
-            if (c < n) A[(size_t)r * n + c] -= acc[q][w];
+            if (c < ce) A[(size_t)r * n + c] -= acc[q][w];
         }
     }
 }
@@ -688,7 +698,7 @@ __global__ void __launch_bounds__(1024) norms_kernel(const double* __restrict__ 
 
 namespace {
 struct AicWs {
-    size_t lu, t, perm, moves, info, pscratch, r, rowabs, norms, bytes;
+    size_t lu, t, perm, moves, info, pscratch, r, xbest, rowabs, norms, bytes;
 };
 AicWs aic_layout(int n)
 {
@@ -701,6 +711,7 @@ AicWs aic_layout(int n)
     w.info = cv.take(sizeof(int));
     w.pscratch = cv.take((size_t)n * PLD * sizeof(float));
     w.r = cv.take((size_t)n * sizeof(double));
+    w.xbest = cv.take((size_t)n * sizeof(double));
     w.rowabs = cv.take((size_t)n * sizeof(double));
     w.norms = cv.take(4 * sizeof(double));
     w.bytes = cv.off;
@@ -709,13 +720,16 @@ AicWs aic_layout(int n)
 
 // Dynamic shared memory of the panel kernel: the two position maps and as many
 // panel rows as fit; the remaining rows go to the global scratch.  Panels of at most
-// PANEL_REG_ROWS rows use the register kernel (two rows per thread).
+// PANEL_REG_ROWS rows use the register kernel (up to PANEL_REG_MAXR rows per thread),
+// whose dynamic shared memory is the multiplier buffer and the position maps.
 constexpr size_t PANEL_SMEM_MAX = 200 * 1024;
-constexpr int PANEL_REG_NT = 640;
-constexpr int PANEL_REG_ROWS = 2 * PANEL_REG_NT;
+constexpr int PANEL_REG_NT = 256;
+constexpr int PANEL_REG_MAXR = 6;
+constexpr int PANEL_REG_ROWS = PANEL_REG_MAXR * PANEL_REG_NT;
 }  // namespace
 
 size_t aic_workspace(int n) { return aic_layout(n).bytes; }
+
 
 vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, double tol, int max_iter, int* iters,
                          double* berr, char* ws, cudaStream_t st, const char** msg)
@@ -731,6 +745,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     int* info = reinterpret_cast<int*>(ws + L.info);
     float* pscratch = reinterpret_cast<float*>(ws + L.pscratch);
     double* r = reinterpret_cast<double*>(ws + L.r);
+    double* xbest = reinterpret_cast<double*>(ws + L.xbest);
     double* rowabs = reinterpret_cast<double*>(ws + L.rowabs);
     double* norms = reinterpret_cast<double*>(ws + L.norms);
 #define VPM_CU(call)                                       \
@@ -745,42 +760,57 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
                                 (int)PANEL_SMEM_MAX));
     VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)PANEL_SMEM_MAX));
-    VPM_CU(cudaFuncSetAttribute(lu_panel_reg_kernel<1, PANEL_REG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PANEL_SMEM_MAX));
-    VPM_CU(cudaFuncSetAttribute(lu_panel_reg_kernel<2, PANEL_REG_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PANEL_SMEM_MAX));
+    {
+        const void* reg_kernels[PANEL_REG_MAXR] = {
+            (const void*)lu_panel_reg_kernel<1, PANEL_REG_NT>, (const void*)lu_panel_reg_kernel<2, PANEL_REG_NT>,
+            (const void*)lu_panel_reg_kernel<3, PANEL_REG_NT>, (const void*)lu_panel_reg_kernel<4, PANEL_REG_NT>,
+            (const void*)lu_panel_reg_kernel<5, PANEL_REG_NT>, (const void*)lu_panel_reg_kernel<6, PANEL_REG_NT>};
+        const int reg_smem = PANEL_REG_ROWS * ((NB + 1) * sizeof(float) + 2 * sizeof(int));
+        for (const void* f : reg_kernels)
+            VPM_CU(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, reg_smem));
+    }
     const size_t solve_smem = (size_t)(n + 32) * sizeof(float);
     VPM_CU(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem));
-    for (int k0 = 0; k0 < n; k0 += NB) {
+    // Factor panel k0 on stream ps.
+    auto launch_panel = [&](int k0, cudaStream_t ps) {
         const int nb = n - k0 < NB ? n - k0 : NB, rows = n - k0;
         const size_t maps = (size_t)2 * rows * sizeof(int);
         trace_launch();
         if (rows <= PANEL_REG_ROWS) {
             const size_t rsmem = maps + (size_t)rows * (NB + 1) * sizeof(float);
-            if (rows <= PANEL_REG_NT)
-                lu_panel_reg_kernel<1, PANEL_REG_NT><<<1, PANEL_REG_NT, rsmem, st>>>(LU, n, k0, nb, info, perm, moves);
-            else
-                lu_panel_reg_kernel<2, PANEL_REG_NT><<<1, PANEL_REG_NT, rsmem, st>>>(LU, n, k0, nb, info, perm, moves);
-            goto panel_done;
+            switch ((rows + PANEL_REG_NT - 1) / PANEL_REG_NT) {
+#define VPM_PANEL_R(R)                                                                                              \
+    case R:                                                                                                         \
+        lu_panel_reg_kernel<R, PANEL_REG_NT><<<1, PANEL_REG_NT, rsmem, ps>>>(LU, n, k0, nb, info, perm, moves); \
+        break;
+                VPM_PANEL_R(1)
+                VPM_PANEL_R(2)
+                VPM_PANEL_R(3)
+                VPM_PANEL_R(4)
+                VPM_PANEL_R(5)
+                VPM_PANEL_R(6)
+#undef VPM_PANEL_R
+            }
+            return;
         }
-        {
         const int srows = (int)std::min<size_t>(rows, (PANEL_SMEM_MAX - maps) / (PLD * sizeof(float)));
         const size_t psmem = maps + (size_t)srows * PLD * sizeof(float);
         if (srows == rows)
-            lu_panel_kernel<true><<<1, PANEL_THREADS, psmem, st>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
+            lu_panel_kernel<true><<<1, PANEL_THREADS, psmem, ps>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
         else
-            lu_panel_kernel<false><<<1, PANEL_THREADS, psmem, st>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
-        }
-    panel_done:
+            lu_panel_kernel<false><<<1, PANEL_THREADS, psmem, ps>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
+    };
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int nb = n - k0 < NB ? n - k0 : NB;
+        launch_panel(k0, st);
         if (n - nb > 0) {
             trace_launch();
             lu_rows_kernel<<<(n - nb + ROWS_THREADS - 1) / ROWS_THREADS, ROWS_THREADS, 0, st>>>(LU, n, k0, nb, moves);
         }
         const int rest = n - k0 - nb;
         if (rest > 0) {
-            dim3 g((rest + 63) / 64, (rest + 63) / 64);
             trace_launch();
-            lu_update_kernel<<<g, 256, 0, st>>>(LU, n, k0, nb);
+            lu_update_kernel<<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, 0, st>>>(LU, n, k0, nb, k0 + nb, n);
         }
     }
     trace_launch();
@@ -796,6 +826,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     trace_launch();
     lu_solve_kernel<<<1, LU_THREADS, solve_smem, st>>>(T, perm, n, b, x, 0);
     double h[4];
+    double best = INFINITY;
     for (int it = 0;; ++it) {
         trace_launch();
         residual_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, b, x, n, r, it == 0 ? rowabs : nullptr);
@@ -807,10 +838,20 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         const double den = h[3] * h[1] + h[2];
         const double be = den > 0.0 ? h[0] / den : (h[0] > 0.0 ? INFINITY : 0.0);
         if (iters) *iters = it;
-        if (berr) *berr = be;
-        if (be <= tol) return VPM_OK;
-        if (it >= max_iter || !isfinite(be)) {
-            *msg = "aic_solve: backward error above tol after max_iter refinement steps";
+        if (be <= tol) {
+            if (berr) *berr = be;
+            return VPM_OK;
+        }
+        const bool last = it >= max_iter || !isfinite(be);
+        if (be < best) {  // keep the best iterate (its copy is needed only if another step follows)
+            best = be;
+            if (!last) VPM_CU(cudaMemcpyAsync(xbest, x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else if (last && isfinite(best)) {
+            VPM_CU(cudaMemcpyAsync(x, xbest, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        if (last) {
+            if (berr) *berr = best;
+            *msg = "aic_solve: backward error above tol after max_iter refinement steps (best x written)";
             return VPM_ERR_NOT_CONVERGED;
         }
         trace_launch();

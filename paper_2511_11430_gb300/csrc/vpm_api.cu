@@ -158,6 +158,13 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
     case VPM_OP_BACKWARD:
         *bytes = backward_workspace(n_src, n_tgt, comp);
         break;
+    case VPM_OP_WAKE_CONVERT:
+        *bytes = wake_workspace(n_src, false);
+        break;
+    case VPM_OP_WAKE_ROW:
+        REQUIRE(n_src >= 1, "a wake row needs at least one panel");
+        *bytes = wake_workspace(3 * n_src + 1, true);
+        break;
     default:
         return fail(VPM_ERR_INVALID_ARG, "unknown op %d", op);
     }
@@ -397,6 +404,77 @@ vpm_status vpm_induce_backward(const float* src_pos_d, const float* src_str_d, i
                                  (int)n_tgt, sigma, comp, grad_out_d, dL_dx_d, dL_dG_d,
                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_induce_backward");
+}
+
+vpm_status vpm_wake_convert(const double* edge_a_d, const double* edge_b_d, const double* gamma_d,
+                            const double* gamma_nb_d, const int* has_nb_d, const int* trailed_d, int64_t m,
+                            double ds_tip, int n_tip, int n_shed, double* x_d, double* G_d, int64_t ld_out,
+                            int64_t* n_out, void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(m, "m")) != VPM_OK) return s;
+    if ((s = check_count(ld_out, "ld_out")) != VPM_OK) return s;
+    REQUIRE(n_out != nullptr, "n_out is NULL");
+    *n_out = 0;
+    REQUIRE(ds_tip > 0.0 && isfinite(ds_tip), "ds_tip must be finite and > 0 (got %g)", ds_tip);
+    REQUIRE(n_tip >= 1 && n_shed >= 1, "n_tip and n_shed must be >= 1");
+    if (m == 0) return ok();
+    REQUIRE(edge_a_d && edge_b_d && gamma_d && trailed_d && aligned8(edge_a_d) && aligned8(edge_b_d) &&
+                aligned8(gamma_d) && aligned4(trailed_d),
+            "edge_a/edge_b/gamma/trailed must be device pointers");
+    REQUIRE(!has_nb_d || (gamma_nb_d && aligned8(gamma_nb_d) && aligned4(has_nb_d)),
+            "has_nb needs gamma_nb (device pointers)");
+    REQUIRE(ld_out == 0 || (x_d && G_d && aligned8(x_d) && aligned8(G_d)), "x/G must be device pointers");
+    const size_t need = wake_workspace(m, false);
+    if (!ws_d || ws_bytes < need || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", need, ws_bytes);
+    const char* msg = "";
+    long long n = 0;
+    s = run_wake_convert(edge_a_d, edge_b_d, gamma_d, gamma_nb_d, has_nb_d, trailed_d, m, ds_tip, n_tip, n_shed, x_d,
+                         G_d, ld_out, &n, static_cast<char*>(ws_d), static_cast<cudaStream_t>(stream), &msg);
+    *n_out = n;
+    if (s != VPM_OK) return fail(s, "%s (%lld particles)", msg, n);
+    return ok();
+}
+
+vpm_status vpm_wake_convert_row(const double* U_d, const double* D_d, const double* gamma_d, int64_t S, double ds_tip,
+                                int n_tip, int n_shed, double* x_d, double* G_d, int64_t ld_out, int64_t* n_out,
+                                void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(S, "S")) != VPM_OK) return s;
+    if ((s = check_count(ld_out, "ld_out")) != VPM_OK) return s;
+    REQUIRE(n_out != nullptr, "n_out is NULL");
+    *n_out = 0;
+    REQUIRE(S >= 1, "a wake row needs at least one panel");
+    REQUIRE(S <= (VPM_MAX_ITEMS - 1) / 3, "S = %lld gives more edges than %d", (long long)S, VPM_MAX_ITEMS);
+    REQUIRE(ds_tip > 0.0 && isfinite(ds_tip), "ds_tip must be finite and > 0 (got %g)", ds_tip);
+    REQUIRE(n_tip >= 1 && n_shed >= 1, "n_tip and n_shed must be >= 1");
+    REQUIRE(U_d && D_d && gamma_d && aligned8(U_d) && aligned8(D_d) && aligned8(gamma_d),
+            "U/D/gamma must be device pointers");
+    REQUIRE(ld_out == 0 || (x_d && G_d && aligned8(x_d) && aligned8(G_d)), "x/G must be device pointers");
+    const size_t need = wake_workspace(3 * S + 1, true);
+    if (!ws_d || ws_bytes < need || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", need, ws_bytes);
+    const char* msg = "";
+    long long n = 0;
+    s = run_wake_convert_row(U_d, D_d, gamma_d, S, ds_tip, n_tip, n_shed, x_d, G_d, ld_out, &n,
+                             static_cast<char*>(ws_d), static_cast<cudaStream_t>(stream), &msg);
+    *n_out = n;
+    if (s != VPM_OK) return fail(s, "%s (%lld particles)", msg, n);
+    return ok();
+}
+
+vpm_status vpm_selftest_wait(double limit_ms, int* completed, void* stream)
+{
+    REQUIRE(completed != nullptr, "completed is NULL");
+    REQUIRE(limit_ms > 0.0 && limit_ms <= 2000.0, "limit_ms must be in (0, 2000] (got %g)", limit_ms);
+    if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
+    int h = -1;
+    cudaError_t e = run_selftest_wait(limit_ms, &h, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_selftest_wait");
+    *completed = h;
+    return ok();
 }
 
 }  // extern "C"

@@ -93,6 +93,15 @@ cudaError_t run_backward(char* ws, size_t ws_bytes, const float* src_pos, const 
 // AIC build and solve.
 cudaError_t run_aic_build(const float* rings, const float* colloc, const float* normal, int n, float core, int vn,
                           const float* v_rel, const float* w_ind, float* A, double* b, cudaStream_t st);
+cudaError_t run_selftest_wait(double limit_ms, int* completed, cudaStream_t st);
+size_t wake_workspace(long long m, bool row_edges);
+vpm_status run_wake_convert(const double* a, const double* b, const double* gamma, const double* gamma_nb,
+                            const int* has_nb, const int* trailed, long long m, double ds_tip, int n_tip, int n_shed,
+                            double* x, double* G, long long ld, long long* n_out, char* ws, cudaStream_t st,
+                            const char** msg);
+vpm_status run_wake_convert_row(const double* U, const double* D, const double* gamma, long long S, double ds_tip,
+                                int n_tip, int n_shed, double* x, double* G, long long ld, long long* n_out, char* ws,
+                                cudaStream_t st, const char** msg);
 size_t aic_workspace(int n);
 vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, double tol, int max_iter, int* iters,
                          double* berr, char* ws, cudaStream_t st, const char** msg);

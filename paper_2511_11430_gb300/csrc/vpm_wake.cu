@@ -1,0 +1,295 @@
+// Wake panel -> particle conversion (Sec. II.C, Eq. 6-8).
+//
+//  * An edge is one straight vortex line a -> b of the wake lattice, owned by a wake
+//    panel of circulation gamma; its circulation difference is gamma - gamma_nb when
+//    the panel across the edge is converted with it, else gamma (Eq. 7).
+//  * A trailed edge becomes n = ceil(|b - a| / ds_tip * n_tip) particles (Eq. 8), a
+//    shed edge n_shed; particle k sits at the centre of the k-th of n equal pieces and
+//    carries Delta Gamma (b - a) / n (Eq. 6).
+//  * Counts per edge with per-tile sums, a scan of the tile sums (and the total), the
+//    offsets within each tile, and the scatter, one thread per particle.  The count is an
+//    integer decided by floating point, so it is formed in double precision with
+//    explicitly rounded operations (no contraction), the reading the reference takes.
+#include <math.h>
+
+#include "vpm_internal.h"
+
+namespace vpm {
+
+__device__ __forceinline__ long long wake_count(const double* a, const double* b, int trailed, double ds_tip,
+                                                int n_tip, int n_shed)
+{
+    if (!trailed) return n_shed;
+    const double dx = __dsub_rn(b[0], a[0]), dy = __dsub_rn(b[1], a[1]), dz = __dsub_rn(b[2], a[2]);
+    const double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    const double v = ceil(__dmul_rn(__ddiv_rn(len, ds_tip), (double)n_tip));
+    // a zero-length edge keeps one particle (of zero strength); a count above the largest
+    // capacity (or NaN) is clamped to VPM_MAX_ITEMS + 1, which no capacity admits, so the
+    // total stays far from overflow and the call is refused
+    if (!(v <= (double)VPM_MAX_ITEMS)) return (long long)VPM_MAX_ITEMS + 1;
+    return v < 1.0 ? 1 : (long long)v;
+}
+
+// Counts are scanned in tiles of SCAN_TILE edges: block t of wake_count_kernel writes
+// its tile's counts and their sum, one block scans the tile sums, and
+// wake_offsets_kernel scans each tile and adds the tile's start.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER;
+
+// Inclusive scan of v over the block (SCAN_THREADS threads); returns this thread's
+// inclusive prefix and puts the block total in *tot.
+__device__ __forceinline__ long long block_scan(long long v, long long* wsum, long long* tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < SCAN_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        if (lane < SCAN_THREADS / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    const long long r = v + (warp > 0 ? wsum[warp - 1] : 0);
+    *tot = wsum[SCAN_THREADS / 32 - 1];
+    __syncthreads();  // wsum may be reused by the caller
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) wake_count_kernel(const double* __restrict__ a,
+                                                                  const double* __restrict__ b,
+                                                                  const int* __restrict__ trailed, long long m,
+                                                                  double ds_tip, int n_tip, int n_shed,
+                                                                  long long* __restrict__ counts,
+                                                                  long long* __restrict__ tile_sum)
+{
+    __shared__ long long wsum[SCAN_THREADS / 32];
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const long long i = base + k * SCAN_THREADS + threadIdx.x;
+        if (i < m) {
+            const long long c = wake_count(a + 3 * i, b + 3 * i, trailed[i], ds_tip, n_tip, n_shed);
+            counts[i] = c;
+            s += c;
+        }
+    }
+    long long tot;
+    block_scan(s, wsum, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the tile sums (one block, looping over chunks of SCAN_THREADS), and
+// the grand total.
+__global__ void __launch_bounds__(SCAN_THREADS) wake_tile_scan_kernel(long long* __restrict__ tile_sum,
+                                                                      long long tiles, long long* __restrict__ total)
+{
+    __shared__ long long wsum[SCAN_THREADS / 32];
+    long long carry = 0;
+    for (long long c0 = 0; c0 < tiles; c0 += SCAN_THREADS) {
+        const long long i = c0 + threadIdx.x;
+        const long long v = i < tiles ? tile_sum[i] : 0;
+        long long tot;
+        const long long incl = block_scan(v, wsum, &tot);
+        if (i < tiles) tile_sum[i] = carry + incl - v;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// offsets[i] = the tile's start + the exclusive prefix of counts within the tile.
+__global__ void __launch_bounds__(SCAN_THREADS) wake_offsets_kernel(const long long* __restrict__ counts, long long m,
+                                                                    const long long* __restrict__ tile_start,
+                                                                    long long* __restrict__ offsets)
+{
+    __shared__ long long wsum[SCAN_THREADS / 32];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_PER;
+    long long c[SCAN_PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {  // a thread scans SCAN_PER consecutive edges
+        c[k] = base + k < m ? counts[base + k] : 0;
+        s += c[k];
+    }
+    long long tot;
+    long long run = block_scan(s, wsum, &tot) - s + tile_start[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        if (base + k < m) offsets[base + k] = run;
+        run += c[k];
+    }
+}
+
+// One thread per particle p < total: its edge i is the last with offsets[i] <= p
+// (binary search; edges without particles do not exist, every count is >= 1), its
+// index within the edge k = p - offsets[i].  Writes are coalesced across the warp
+// (planar outputs of leading dimension ld).
+__global__ void wake_scatter_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                    const double* __restrict__ gamma, const double* __restrict__ gamma_nb,
+                                    const int* __restrict__ has_nb, long long m,
+                                    const long long* __restrict__ counts, const long long* __restrict__ offsets,
+                                    long long total, double* __restrict__ x, double* __restrict__ G, long long ld)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    long long lo = 0, hi = m - 1;  // offsets[lo] <= p < offsets[hi + 1]
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= p)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const long long i = lo, k = p - offsets[i];
+    const double* ai = a + 3 * i;
+    const double* bi = b + 3 * i;
+    const double dG = (has_nb && has_nb[i]) ? __dsub_rn(gamma[i], gamma_nb[i]) : gamma[i];  // Eq. 7
+    const double nd = (double)counts[i];
+    const double t = __ddiv_rn(__dadd_rn((double)k, 0.5), nd);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double d = __dsub_rn(bi[c], ai[c]);
+        x[c * ld + p] = __dadd_rn(ai[c], __dmul_rn(t, d));
+        G[c * ld + p] = __ddiv_rn(__dmul_rn(dG, d), nd);  // Eq. 6
+    }
+}
+
+// The 3 S + 1 edges of one wake panel row (node lines U, D [S+1][3], circulations
+// gamma [S]): trailed q < S: D[q] -> U[q] of panel q with neighbour q - 1 (q > 0);
+// trailed S: U[S] -> D[S] of panel S - 1; shed back p: D[p+1] -> D[p]; shed front p:
+// U[p] -> U[p+1]; shed edges without neighbour.
+__global__ void wake_row_edges_kernel(const double* __restrict__ U, const double* __restrict__ D,
+                                      const double* __restrict__ gamma, long long S, double* __restrict__ a,
+                                      double* __restrict__ b, double* __restrict__ g, double* __restrict__ gnb,
+                                      int* __restrict__ has_nb, int* __restrict__ trailed)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > 3 * S) return;
+    const double *from, *to;
+    double ge, gn = 0.0;
+    int hn = 0, tr = 0;
+    if (e <= S) {  // trailed
+        const long long q = e;
+        const bool end = q == S;
+        from = end ? U + 3 * q : D + 3 * q;
+        to = end ? D + 3 * q : U + 3 * q;
+        ge = end ? gamma[S - 1] : gamma[q];
+        hn = (!end && q > 0);
+        if (hn) gn = gamma[q - 1];
+        tr = 1;
+    } else if (e <= 2 * S) {  // shed, downstream line
+        const long long p = e - S - 1;
+        from = D + 3 * (p + 1);
+        to = D + 3 * p;
+        ge = gamma[p];
+    } else {  // shed, upstream line
+        const long long p = e - 2 * S - 1;
+        from = U + 3 * p;
+        to = U + 3 * (p + 1);
+        ge = gamma[p];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[3 * e + c] = from[c], b[3 * e + c] = to[c];
+    g[e] = ge, gnb[e] = gn, has_nb[e] = hn, trailed[e] = tr;
+}
+
+namespace {
+struct WakeWs {
+    size_t counts, offsets, total, tiles, ea, eb, eg, egnb, ehn, etr, bytes;
+};
+WakeWs wake_layout(long long m, bool row_edges)
+{
+    Carve cv;
+    WakeWs w{};
+    w.counts = cv.take((size_t)m * sizeof(long long));
+    w.offsets = cv.take((size_t)m * sizeof(long long));
+    w.total = cv.take(sizeof(long long));
+    w.tiles = cv.take((size_t)((m + SCAN_TILE - 1) / SCAN_TILE + 1) * sizeof(long long));
+    if (row_edges) {
+        w.ea = cv.take((size_t)m * 3 * sizeof(double));
+        w.eb = cv.take((size_t)m * 3 * sizeof(double));
+        w.eg = cv.take((size_t)m * sizeof(double));
+        w.egnb = cv.take((size_t)m * sizeof(double));
+        w.ehn = cv.take((size_t)m * sizeof(int));
+        w.etr = cv.take((size_t)m * sizeof(int));
+    }
+    w.bytes = cv.off;
+    return w;
+}
+}  // namespace
+
+size_t wake_workspace(long long m, bool row_edges) { return wake_layout(m, row_edges).bytes; }
+
+vpm_status run_wake_convert(const double* a, const double* b, const double* gamma, const double* gamma_nb,
+                            const int* has_nb, const int* trailed, long long m, double ds_tip, int n_tip, int n_shed,
+                            double* x, double* G, long long ld, long long* n_out, char* ws, cudaStream_t st,
+                            const char** msg)
+{
+    const WakeWs L = wake_layout(m, false);
+    long long* counts = reinterpret_cast<long long*>(ws + L.counts);
+    long long* offsets = reinterpret_cast<long long*>(ws + L.offsets);
+    long long* total = reinterpret_cast<long long*>(ws + L.total);
+    long long* tiles = reinterpret_cast<long long*>(ws + L.tiles);
+    const long long ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+    trace_launch();
+    wake_count_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(a, b, trailed, m, ds_tip, n_tip, n_shed, counts,
+                                                                 tiles);
+    trace_launch();
+    wake_tile_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(tiles, ntiles, total);
+    trace_launch();
+    wake_offsets_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(counts, m, tiles, offsets);
+    long long h = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, total, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *msg = cudaGetErrorString(cudaGetLastError());
+        return VPM_ERR_CUDA;
+    }
+    *n_out = h;
+    if (h > ld || h > VPM_MAX_ITEMS) {
+        *msg = "wake_convert: more particles than the output capacity ld_out";
+        return VPM_ERR_LIMIT;
+    }
+    if (h == 0) return VPM_OK;
+    const int tpb = 256;
+    trace_launch();
+    wake_scatter_kernel<<<(unsigned)((h + tpb - 1) / tpb), tpb, 0, st>>>(a, b, gamma, gamma_nb, has_nb, m, counts,
+                                                                      offsets, h, x, G, ld);
+    if (cudaGetLastError() != cudaSuccess) {
+        *msg = cudaGetErrorString(cudaGetLastError());
+        return VPM_ERR_CUDA;
+    }
+    return VPM_OK;
+}
+
+vpm_status run_wake_convert_row(const double* U, const double* D, const double* gamma, long long S, double ds_tip,
+                                int n_tip, int n_shed, double* x, double* G, long long ld, long long* n_out, char* ws,
+                                cudaStream_t st, const char** msg)
+{
+    const long long m = 3 * S + 1;
+    const WakeWs L = wake_layout(m, true);
+    double* a = reinterpret_cast<double*>(ws + L.ea);
+    double* b = reinterpret_cast<double*>(ws + L.eb);
+    double* g = reinterpret_cast<double*>(ws + L.eg);
+    double* gnb = reinterpret_cast<double*>(ws + L.egnb);
+    int* hn = reinterpret_cast<int*>(ws + L.ehn);
+    int* tr = reinterpret_cast<int*>(ws + L.etr);
+    trace_launch();
+    wake_row_edges_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(U, D, gamma, S, a, b, g, gnb, hn, tr);
+    if (cudaGetLastError() != cudaSuccess) {
+        *msg = cudaGetErrorString(cudaGetLastError());
+        return VPM_ERR_CUDA;
+    }
+    // the edge arrays sit after the conversion's own scratch in the same layout
+    return run_wake_convert(a, b, g, gnb, hn, tr, m, ds_tip, n_tip, n_shed, x, G, ld, n_out, ws, st, msg);
+}
+
+}  // namespace vpm

@@ -325,3 +325,41 @@ def sample_targets(seed, n, k):
     rng = np.random.default_rng(seed + 1000)
     k = min(k, n)
     return np.sort(rng.choice(n, size=k, replace=False))
+
+
+def rotor_wake_edges(seed, n_rows, n_span=40, n_blades=4, dpsi_deg=5.0):
+    """Edges of n_rows x n_blades near-wake panel rows behind a hover rotor (FP64):
+    each row spans r = 0.15R..R between the trailing-edge line at one azimuth and the
+    same line one time step (dpsi) earlier, dropped by a small inflow, so the trailed
+    edges lengthen with radius (the geometry behind the adaptive count).  Panel
+    circulations follow Gamma_0 (r/R) sqrt(1 - (r/R)^2) with a few percent of noise.
+    Returns a, b [m, 3], gamma, gamma_nb [m], has_nb, trailed [m] (int32) and the
+    length of the tip's trailed edge."""
+    rng = np.random.default_rng(seed)
+    r = np.linspace(0.15 * R, R, n_span + 1)
+    dpsi = np.deg2rad(dpsi_deg)
+    rc = 0.5 * (r[1:] + r[:-1])
+    A, B, g, gnb, hn, tr = [], [], [], [], [], []
+    for row in range(n_rows):
+        for bl in range(n_blades):
+            psi = 2 * np.pi * bl / n_blades + row * dpsi
+            z0 = -0.01 * R * (row + 1)
+            up = np.stack([r * np.cos(psi), r * np.sin(psi), np.full_like(r, z0)], 1)
+            dn = np.stack([r * np.cos(psi - dpsi), r * np.sin(psi - dpsi), np.full_like(r, z0 - 0.01 * R)], 1)
+            gam = 2.0 * (rc / R) * np.sqrt(1 - (rc / R) ** 2) * (1 + 0.02 * rng.normal(size=n_span))
+            for q in range(n_span + 1):  # trailed edges, as a panel row's conversion lists them
+                end = q == n_span
+                A.append(up[q] if end else dn[q])
+                B.append(dn[q] if end else up[q])
+                g.append(gam[-1] if end else gam[q])
+                has = (not end) and q > 0
+                gnb.append(gam[q - 1] if has else 0.0)
+                hn.append(int(has))
+                tr.append(1)
+            for p in range(n_span):  # shed edges, downstream then upstream lines
+                A.append(dn[p + 1]), B.append(dn[p]), g.append(gam[p]), gnb.append(0.0), hn.append(0), tr.append(0)
+            for p in range(n_span):
+                A.append(up[p]), B.append(up[p + 1]), g.append(gam[p]), gnb.append(0.0), hn.append(0), tr.append(0)
+    ds_tip = float(np.linalg.norm(np.array(B[n_span]) - np.array(A[n_span])))
+    return (np.array(A), np.array(B), np.array(g), np.array(gnb), np.array(hn, dtype=np.int32),
+            np.array(tr, dtype=np.int32), ds_tip)

@@ -191,6 +191,23 @@ def test_aic_solve_needs_pivoting(api, n, kind):
     assert rel_l2(x.cpu().numpy(), xr) <= max(1e-10, 10 * cond * 1e-12)
 
 
+def test_aic_solve_not_converged_returns_best_iterate(api):
+    """With an unreachable tolerance the solve stops after max_iter corrections and
+    returns the iterate of smallest backward error, whose error it reports."""
+    rng = np.random.default_rng(5)
+    n = 300
+    A = rng.normal(size=(n, n)).astype(np.float32)
+    b = rng.normal(size=n)
+    x, it, be = api.aic_solve(to_dev(A), to_dev(b), tol=0.0, max_iter=3, raise_on_fail=False)
+    assert it == 3
+    xh = x.cpu().numpy()
+    A64 = A.astype(np.float64)
+    r = b - A64 @ xh
+    berr = np.abs(r).max() / (np.abs(A64).sum(1).max() * np.abs(xh).max() + np.abs(b).max())
+    # both errors sit at the rounding level of the FP64 residual, so compare their size only
+    assert be < 1e-13 and berr < 1e-13
+
+
 def test_aic_solve_zero_column_is_reported(api):
     rng = np.random.default_rng(3)
     A = rng.normal(size=(100, 100)).astype(np.float32)
