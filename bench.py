@@ -72,7 +72,52 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=None,
                     help="seconds of oracle work per CPU-baseline sample (default 12; reference arm: 60 s over all steps)")
+    ap.add_argument("--part", choices=["aic", "wake"], default=None,
+                    help="time one component alone (for profiling; prints a text line, not the JSON contract)")
     return ap.parse_args()
+
+
+def run_part(args):
+    """One component of the step, repeated --steps times after --warmup: the AIC build +
+    solve of the hover blade lattice, or the conversion of 2,000 hover wake rows."""
+    import torch
+
+    from paper_2511_11430_gb300 import api, build, synth
+
+    build.build()
+    def T(a, dt=None):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return (t if dt is None else t.to(dt)).cuda()
+    if args.part == "aic":
+        w = synth.make(args.config, n=1000)
+        rings, colloc, normal, vrel = T(w.rings), T(w.colloc), T(w.normal), T(w.v_rel)
+        wsb = api.Workspace()
+
+        def once():
+            A, b = api.aic_build(rings, colloc, normal, w.seg_core, 2, v_rel=vrel)
+            return api.aic_solve(A, b, tol=1e-12, max_iter=30, ws=wsb)
+        what = f"aic_build + aic_solve, n = {w.n_ctrl}"
+    else:
+        ea, eb, eg, egn, ehn, etr, ds_tip = synth.rotor_wake_edges(5, 2000)
+        wa, wb, wg, wgn = (T(q, torch.float64) for q in (ea, eb, eg, egn))
+        whn, wtr = T(ehn, torch.int32), T(etr, torch.int32)
+        wsb = api.Workspace()
+        npart = int(api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, ws=wsb)[0].shape[1])
+
+        def once():
+            return api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, capacity=npart, ws=wsb)
+        what = f"wake_convert, {len(ea)} edges -> {npart} particles"
+    for _ in range(args.warmup):
+        once()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        once()
+    e1.record()
+    e1.synchronize()
+    print(f"{what}: {e0.elapsed_time(e1) / max(args.steps, 1):.3f} ms per call", flush=True)
 
 
 def dist_info():
@@ -465,7 +510,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.part is not None:
+        run_part(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -194,6 +194,34 @@ vpm_status vpm_induce_backward(const float* src_pos_d, const float* src_str_d, i
                                int64_t n_tgt, float sigma, int flags, const float* grad_out_d, float* dL_dx_d,
                                float* dL_dG_d, void* ws_d, size_t ws_bytes, void* stream);
 
+/* ---- the near wake between conversions (Sec. II.C) -------------------------
+ * A near wake of R panel rows per blade (nb blades, S panels across the span) lies
+ * between R + 1 node lines, line 0 at the blades' trailing edges; nodes_d holds them as
+ * [R + 1][nb][S + 1][3] double.  Row r, blade b, panel p is the ring
+ * U[p] -> U[p+1] -> D[p+1] -> D[p] -> U[p] (U = line r, D = line r + 1) of circulation
+ * gamma_d[(r nb + b) S + p] -- the convention of vpm_wake_convert_row, so the oldest
+ * row of blade b converts with U = nodes_d + 3 (S+1) ((R-1) nb + b) and
+ * D = nodes_d + 3 (S+1) (R nb + b).
+ * vpm_wake_segments writes the 4 R nb S segments of the rings for the velocity
+ * kernels (ring segment k of panel i at 4 i + k; seg_a.w = circulation, FP32). */
+vpm_status vpm_wake_segments(const double* nodes_d, const double* gamma_d, int64_t R, int64_t nb, int64_t S,
+                             float* seg_a_d, float* seg_b_d, void* stream);
+
+/* The segments c0 -> c1 -> c2 -> c3 -> c0 of n blade rings (rings_d [n][4][4] float,
+ * corners as for aic_build) carrying the circulations gamma_d [n] double that aic_solve
+ * returns: segment k of ring i at 4 i + k, seg_a.w = circulation (FP32). */
+vpm_status vpm_ring_segments(const float* rings_d, const double* gamma_d, int64_t n, float* seg_a_d, float* seg_b_d,
+                             void* stream);
+
+/* Points [n][3] double (wake nodes) as FP32 targets [n][4] = (x, y, z, 0). */
+vpm_status vpm_points_pack(const double* pts_d, int64_t n, float* tgt_d, void* stream);
+
+/* pts[i] += dt (u[:, i] + u_inf): explicit Euler convection of points [n][3] double by
+ * the velocity u_d [3][n] float (planar, as vpm_induce writes it); u_inf a host
+ * float[3] or NULL. */
+vpm_status vpm_points_advect(double* pts_d, const float* u_d, int64_t n, double dt, const float* u_inf,
+                             void* stream);
+
 /* ---- self-test of the bounded device waits (no counterpart in the paper) -----
  * Every wait inside the library's kernels (on an mbarrier phase) gives up after a
  * time limit, latches VPM_ERR_LIMIT in the device error word and lets the kernel
@@ -210,15 +238,15 @@ vpm_status vpm_selftest_wait(double limit_ms, int* completed, void* stream);
  * converted too), else gamma_i (Eq. 7).  A trailed (streamwise) edge becomes
  *   n_i = ceil(|b_i - a_i| / ds_tip * n_tip)                         (Eq. 8)
  * particles, ds_tip being the length of the tip's trailed edge, which gets n_tip; a
- * shed (spanwise) edge becomes n_shed particles (n_tip = n_shed = 1 with every edge
- * no longer than ds_tip is the conventional one-particle-per-edge strategy).  The
+ * shed (spanwise) edge becomes n_shed particles.  n_tip < 0 selects the conventional
+ * strategy the paper compares against: -n_tip particles on every trailed edge.  The
  * particles of an edge sit at the centres of its n_i equal pieces,
  *   x_ik = a_i + (k + 1/2)/n_i (b_i - a_i),  Gamma_ik = Delta Gamma_i (b_i - a_i) / n_i   (Eq. 6),
  * and are written edge after edge.  n_i is decided in FP64 with correctly rounded
  * operations, as (|b - a| / ds_tip) * n_tip with |b - a| = sqrt((dx dx + dy dy) + dz dz).
  *   edge_a_d, edge_b_d [m][3] double; gamma_d [m] double; gamma_nb_d [m] double and
  *   has_nb_d [m] int, both NULL when no edge has a converted neighbour; trailed_d [m]
- *   int (1 trailed, 0 shed); ds_tip > 0; n_tip, n_shed >= 1.
+ *   int (1 trailed, 0 shed); ds_tip > 0; n_tip != 0; n_shed >= 1.
  *   x_d, G_d [3][ld_out] double, planar (row c holds component c), the particle
  *   positions and strengths; *n_out (host) receives the particle count.
  * More particles than ld_out gives VPM_ERR_LIMIT with nothing written (and *n_out the

@@ -551,7 +551,8 @@ void orc_p2p_adjoint(const double* pos, const double* str, int64_t n_src, const 
  * n particles of strength Delta Gamma (b - a) / n (Eq. 6).  A trailed (streamwise)
  * edge gets n = ceil(|b - a| / ds_tip * n_tip) particles (Eq. 8, the adaptive count
  * scaled on the tip edge of length ds_tip that carries n_tip); a shed (spanwise) edge
- * gets n_shed (n_shed = n_tip = 1 and ds_tip = |b - a| is the conventional strategy).
+ * gets n_shed.  A negative n_tip selects the conventional strategy the paper compares
+ * against: -n_tip particles on every trailed edge whatever its length.
  *
  * Readings: the paper places the particles along the edge without stating where; they
  * sit at the centres of the n equal pieces, x_k = a + (k + 1/2)/n (b - a).  The count
@@ -565,6 +566,7 @@ void orc_p2p_adjoint(const double* pos, const double* str, int64_t n_src, const 
 static int64_t wake_count(const double* a, const double* b, int trailed, double ds_tip, int n_tip, int n_shed)
 {
     if (!trailed) return n_shed;
+    if (n_tip < 0) return -n_tip; /* the conventional strategy: the same count on every trailed edge */
     const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
     const double len = sqrt(dx * dx + dy * dy + dz * dz);
     const double v = ceil((len / ds_tip) * (double)n_tip);

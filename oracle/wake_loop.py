@@ -1,0 +1,113 @@
+"""FP64 CPU reference of the near-wake time loop (Sec. II.A-C) that
+paper_2511_11430_gb300.wake.RotorWake runs through the library.  TEST
+INFRASTRUCTURE ONLY: only tests/ use it.
+
+Every step uses the oracle's own routines (plain FP64 loops in vpm_oracle.c) in
+the same order as the library's driver: blade circulations from the AIC with the
+velocity the particles and the wake rows induce at the control points (textbook LU),
+the near-wake node lines convected by explicit Euler, the particles by one
+low-storage RK3 step (the right-hand side evaluated on the state rounded to FP32,
+the library's precision reading), a new row shed with the trailing-edge panels'
+circulation (Kutta), and the oldest row beyond max_rows converted by Eq. 6-8.  The
+blade geometry is the same synthetic input (rounded to FP32, as the library gets it).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2511_11430_gb300 import synth
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+class OracleRotorWake:
+    def __init__(self, n_blades=2, n_span=20, n_chord=4, sigma=0.02 * synth.R, dt=synth.DT, max_rows=2, n_tip=2,
+                 n_shed=1, adaptive=True, seg_core=None, nu=synth.NU_AIR, c_v=synth.C_V):
+        self.nb, self.S, self.nc = n_blades, n_span, n_chord
+        self.sigma, self.dt, self.max_rows = float(sigma), float(dt), int(max_rows)
+        self.n_tip = int(n_tip) if adaptive else -int(n_tip)
+        self.n_shed = int(n_shed)
+        self.core = float(sigma if seg_core is None else seg_core)
+        self.nu, self.c_v = nu, c_v
+        self.t = 0.0
+        self.x = np.zeros((0, 3))
+        self.G = np.zeros((0, 3))
+        te = self._geometry(0.0)[4]
+        self.nodes = te.reshape(1, self.nb, self.S + 1, 3).copy()
+        self.gammas = np.zeros((0, self.nb, self.S))
+
+    def _geometry(self, t):
+        rings, colloc, normal, vrel, _ = synth.blade_lattice(self.nb, self.S, self.nc, phase=synth.OMEGA * t)
+        te, te_idx = synth.blade_trailing_edge(rings, self.nb, self.S, self.nc)
+        return _f32(rings), _f32(colloc), _f32(normal), _f32(vrel), te, te_idx
+
+    @property
+    def rows(self):
+        return self.gammas.shape[0]
+
+    def _wake_segments(self):
+        sa, sb = [], []
+        for r in range(self.rows):
+            for b in range(self.nb):
+                U, D = self.nodes[r, b], self.nodes[r + 1, b]
+                for p in range(self.S):
+                    c = [U[p], U[p + 1], D[p + 1], D[p]]
+                    for k in range(4):
+                        sa.append([*_f32(c[k]), np.float32(self.gammas[r, b, p])])
+                        sb.append([*_f32(c[(k + 1) % 4]), 0.0])
+        return np.array(sa).reshape(-1, 4), np.array(sb).reshape(-1, 4)
+
+    def _velocity(self, tgt, sa, sb):
+        u = np.zeros((len(tgt), 3))
+        if len(self.x):
+            pos = np.concatenate([_f32(self.x), np.full((len(self.x), 1), np.float32(self.sigma ** 3))], 1)
+            u += oracle.p2p(pos, _f32(self.G), tgt, self.sigma, grad=False)
+        if len(sa):
+            u += oracle.segments(sa, sb, tgt, self.core, 2, grad=False)
+        return u
+
+    def step(self):
+        rings, colloc, normal, vrel, _, te_idx = self._geometry(self.t)
+        wsa, wsb = self._wake_segments()
+        u_c = self._velocity(colloc, wsa, wsb)
+        A = oracle.aic_build(rings, colloc, normal, self.core)
+        b = oracle.aic_rhs(vrel, _f32(u_c), normal)
+        gam = oracle.lu_solve(_f32(A), b)
+        bsa, bsb = synth.ring_segments(rings, _f32(gam))
+        sa = np.concatenate([bsa, wsa]) if len(wsa) else bsa
+        sb = np.concatenate([bsb, wsb]) if len(wsb) else bsb
+        pts = self.nodes.reshape(-1, 3)
+        u_n = self._velocity(pts, sa, sb)
+        x_old, G_old = self.x, self.G
+        self.nodes = (pts + self.dt * _f32(u_n)).reshape(self.nodes.shape)
+        if len(x_old):
+            vol = np.full(len(x_old), np.float32(self.sigma ** 3))
+            self.x, self.G = oracle.step(x_old, G_old, vol, sa, sb, self.sigma, self.dt, nu=self.nu, c_v=self.c_v,
+                                         seg_core=self.core, cast_f32=True)
+        te_next = self._geometry(self.t + self.dt)[4]
+        self.nodes = np.concatenate([te_next.reshape(1, self.nb, self.S + 1, 3), self.nodes])
+        shed = -gam[te_idx.ravel()].reshape(1, self.nb, self.S)
+        self.gammas = np.concatenate([shed, self.gammas])
+        if self.rows > self.max_rows:
+            self._convert_oldest()
+        self.t += self.dt
+        return gam
+
+    def _convert_oldest(self):
+        R = self.rows
+        xs, Gs = [], []
+        for b in range(self.nb):
+            U, D = self.nodes[R - 1, b], self.nodes[R, b]
+            d = D[-1] - U[-1]
+            ds_tip = float(np.sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]))
+            ea, eb, g, gnb, hn, tr = oracle.wake_row_edges(U, D, self.gammas[R - 1, b])
+            xw, Gw, _ = oracle.wake_convert(ea, eb, g, gnb, hn, tr, ds_tip, self.n_tip, self.n_shed)
+            xs.append(xw)
+            Gs.append(Gw)
+        self.x = np.concatenate([self.x] + xs)
+        self.G = np.concatenate([self.G] + Gs)
+        self.nodes = self.nodes[:R]
+        self.gammas = self.gammas[:R - 1]

@@ -89,6 +89,10 @@ SIGNATURES = {
     "vpm_induce_backward": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P, _P, _SZ, _P]),
     "vpm_induce_noalloc": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P]),
     "vpm_selftest_wait": (_INT, [_D, _P, _P]),
+    "vpm_wake_segments": (_INT, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
+    "vpm_points_pack": (_INT, [_P, _I64, _P, _P]),
+    "vpm_ring_segments": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "vpm_points_advect": (_INT, [_P, _P, _I64, _D, _P, _P]),
     "vpm_wake_convert": (_INT, [_P, _P, _P, _P, _P, _P, _I64, _D, _INT, _INT, _P, _P, _I64, _P, _P, _SZ, _P]),
     "vpm_wake_convert_row": (_INT, [_P, _P, _P, _I64, _D, _INT, _INT, _P, _P, _I64, _P, _P, _SZ, _P]),
     "vpm_trace_enable": (_INT, [_INT]),

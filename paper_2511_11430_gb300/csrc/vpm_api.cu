@@ -417,7 +417,7 @@ vpm_status vpm_wake_convert(const double* edge_a_d, const double* edge_b_d, cons
     REQUIRE(n_out != nullptr, "n_out is NULL");
     *n_out = 0;
     REQUIRE(ds_tip > 0.0 && isfinite(ds_tip), "ds_tip must be finite and > 0 (got %g)", ds_tip);
-    REQUIRE(n_tip >= 1 && n_shed >= 1, "n_tip and n_shed must be >= 1");
+    REQUIRE(n_tip != 0 && n_shed >= 1, "n_tip must be nonzero and n_shed >= 1");
     if (m == 0) return ok();
     REQUIRE(edge_a_d && edge_b_d && gamma_d && trailed_d && aligned8(edge_a_d) && aligned8(edge_b_d) &&
                 aligned8(gamma_d) && aligned4(trailed_d),
@@ -449,7 +449,7 @@ vpm_status vpm_wake_convert_row(const double* U_d, const double* D_d, const doub
     REQUIRE(S >= 1, "a wake row needs at least one panel");
     REQUIRE(S <= (VPM_MAX_ITEMS - 1) / 3, "S = %lld gives more edges than %d", (long long)S, VPM_MAX_ITEMS);
     REQUIRE(ds_tip > 0.0 && isfinite(ds_tip), "ds_tip must be finite and > 0 (got %g)", ds_tip);
-    REQUIRE(n_tip >= 1 && n_shed >= 1, "n_tip and n_shed must be >= 1");
+    REQUIRE(n_tip != 0 && n_shed >= 1, "n_tip must be nonzero and n_shed >= 1");
     REQUIRE(U_d && D_d && gamma_d && aligned8(U_d) && aligned8(D_d) && aligned8(gamma_d),
             "U/D/gamma must be device pointers");
     REQUIRE(ld_out == 0 || (x_d && G_d && aligned8(x_d) && aligned8(G_d)), "x/G must be device pointers");
@@ -463,6 +463,53 @@ vpm_status vpm_wake_convert_row(const double* U_d, const double* D_d, const doub
     *n_out = n;
     if (s != VPM_OK) return fail(s, "%s (%lld particles)", msg, n);
     return ok();
+}
+
+vpm_status vpm_wake_segments(const double* nodes_d, const double* gamma_d, int64_t R, int64_t nb, int64_t S,
+                             float* seg_a_d, float* seg_b_d, void* stream)
+{
+    REQUIRE(R >= 0 && nb >= 0 && S >= 0, "R, nb, S must be >= 0");
+    REQUIRE(R * nb * S * 4 <= VPM_MAX_ITEMS, "more than %d segments", VPM_MAX_ITEMS);
+    if (R * nb * S == 0) return ok();
+    REQUIRE(nodes_d && gamma_d && aligned8(nodes_d) && aligned8(gamma_d), "nodes/gamma must be device pointers");
+    REQUIRE(seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d),
+            "seg_a/seg_b must be 16-byte aligned device pointers");
+    cudaError_t e = run_wake_segments(nodes_d, gamma_d, R, nb, S, seg_a_d, seg_b_d, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_wake_segments");
+}
+
+vpm_status vpm_ring_segments(const float* rings_d, const double* gamma_d, int64_t n, float* seg_a_d, float* seg_b_d,
+                             void* stream)
+{
+    REQUIRE(n >= 0 && n <= VPM_MAX_ITEMS / 4, "ring count %lld outside [0, %d]", (long long)n, VPM_MAX_ITEMS / 4);
+    if (n == 0) return ok();
+    REQUIRE(rings_d && gamma_d && aligned16(rings_d) && aligned8(gamma_d), "rings/gamma must be device pointers");
+    REQUIRE(seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d),
+            "seg_a/seg_b must be 16-byte aligned device pointers");
+    cudaError_t e = run_ring_segments(rings_d, gamma_d, n, seg_a_d, seg_b_d, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_ring_segments");
+}
+
+vpm_status vpm_points_pack(const double* pts_d, int64_t n, float* tgt_d, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    if (n == 0) return ok();
+    REQUIRE(pts_d && tgt_d && aligned8(pts_d) && aligned16(tgt_d), "pts/tgt must be device pointers (tgt 16-byte aligned)");
+    cudaError_t e = run_points_pack(pts_d, n, tgt_d, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_points_pack");
+}
+
+vpm_status vpm_points_advect(double* pts_d, const float* u_d, int64_t n, double dt, const float* u_inf,
+                             void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    REQUIRE(isfinite(dt), "dt must be finite");
+    if (n == 0) return ok();
+    REQUIRE(pts_d && u_d && aligned8(pts_d) && aligned4(u_d), "pts/u must be device pointers");
+    cudaError_t e = run_points_advect(pts_d, u_d, n, dt, u_inf, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_points_advect");
 }
 
 vpm_status vpm_selftest_wait(double limit_ms, int* completed, void* stream)

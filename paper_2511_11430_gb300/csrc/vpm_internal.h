@@ -94,6 +94,12 @@ cudaError_t run_backward(char* ws, size_t ws_bytes, const float* src_pos, const 
 cudaError_t run_aic_build(const float* rings, const float* colloc, const float* normal, int n, float core, int vn,
                           const float* v_rel, const float* w_ind, float* A, double* b, cudaStream_t st);
 cudaError_t run_selftest_wait(double limit_ms, int* completed, cudaStream_t st);
+cudaError_t run_wake_segments(const double* nodes, const double* gamma, long long R, long long nb, long long S,
+                              float* seg_a, float* seg_b, cudaStream_t st);
+cudaError_t run_ring_segments(const float* rings, const double* gamma, long long n, float* seg_a, float* seg_b,
+                              cudaStream_t st);
+cudaError_t run_points_pack(const double* pts, long long n, float* tgt, cudaStream_t st);
+cudaError_t run_points_advect(double* pts, const float* u, long long n, double dt, const float* u_inf, cudaStream_t st);
 size_t wake_workspace(long long m, bool row_edges);
 vpm_status run_wake_convert(const double* a, const double* b, const double* gamma, const double* gamma_nb,
                             const int* has_nb, const int* trailed, long long m, double ds_tip, int n_tip, int n_shed,

@@ -20,6 +20,7 @@ __device__ __forceinline__ long long wake_count(const double* a, const double* b
                                                 int n_tip, int n_shed)
 {
     if (!trailed) return n_shed;
+    if (n_tip < 0) return -(long long)n_tip;  // conventional: the same count on every trailed edge
     const double dx = __dsub_rn(b[0], a[0]), dy = __dsub_rn(b[1], a[1]), dz = __dsub_rn(b[2], a[2]);
     const double len = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
     const double v = ceil(__dmul_rn(__ddiv_rn(len, ds_tip), (double)n_tip));
@@ -200,6 +201,107 @@ __global__ void wake_row_edges_kernel(const double* __restrict__ U, const double
 #pragma unroll
     for (int c = 0; c < 3; ++c) a[3 * e + c] = from[c], b[3 * e + c] = to[c];
     g[e] = ge, gnb[e] = gn, has_nb[e] = hn, trailed[e] = tr;
+}
+
+// ---------------------------------------------------------------------------
+// The near wake between conversions: R panel rows per blade between R + 1 node lines
+// (line 0 at the trailing edge), nodes stored [line][blade][S + 1][3] in FP64.
+// ---------------------------------------------------------------------------
+// The four segments of every wake ring: row r, blade b, panel p is the ring
+// U[p] -> U[p+1] -> D[p+1] -> D[p] -> U[p] with U = line r and D = line r + 1,
+// circulation gamma[r][b][p]; segment k of the ring is out[4 ((r nb + b) S + p) + k].
+__global__ void wake_segments_kernel(const double* __restrict__ nodes, const double* __restrict__ gamma, long long R,
+                                     long long nb, long long S, float4* __restrict__ seg_a,
+                                     float4* __restrict__ seg_b)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // panel index (r nb + b) S + p
+    if (i >= R * nb * S) return;
+    const long long p = i % S, rb = i / S;  // rb = r nb + b
+    const long long up = rb * (S + 1) + p, dn = (rb + nb) * (S + 1) + p;
+    const long long c[4] = {up, up + 1, dn + 1, dn};
+    const float g = (float)gamma[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double* a = nodes + 3 * c[k];
+        const double* b = nodes + 3 * c[(k + 1) & 3];
+        seg_a[4 * i + k] = make_float4((float)a[0], (float)a[1], (float)a[2], g);
+        seg_b[4 * i + k] = make_float4((float)b[0], (float)b[1], (float)b[2], 0.f);
+    }
+}
+
+// The four segments c0 -> c1 -> c2 -> c3 -> c0 of blade rings [n][4] (float4 corners)
+// carrying circulations gamma [n] (FP64, as aic_solve returns them).
+__global__ void ring_segments_kernel(const float4* __restrict__ rings, const double* __restrict__ gamma, long long n,
+                                     float4* __restrict__ seg_a, float4* __restrict__ seg_b)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = (float)gamma[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 a = rings[4 * i + k], b = rings[4 * i + ((k + 1) & 3)];
+        seg_a[4 * i + k] = make_float4(a.x, a.y, a.z, g);
+        seg_b[4 * i + k] = make_float4(b.x, b.y, b.z, 0.f);
+    }
+}
+
+cudaError_t run_ring_segments(const float* rings, const double* gamma, long long n, float* seg_a, float* seg_b,
+                              cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    trace_launch();
+    ring_segments_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4*>(rings), gamma, n,
+                                                                      reinterpret_cast<float4*>(seg_a),
+                                                                      reinterpret_cast<float4*>(seg_b));
+    return cudaGetLastError();
+}
+
+// FP32 targets (x, y, z, 0) of n FP64 points [n][3].
+__global__ void points_pack_kernel(const double* __restrict__ pts, long long n, float4* __restrict__ tgt)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tgt[i] = make_float4((float)pts[3 * i], (float)pts[3 * i + 1], (float)pts[3 * i + 2], 0.f);
+}
+
+// pts[i] += dt (u[:, i] + u_inf), u planar [3][n] FP32, pts [n][3] FP64 (explicit Euler).
+__global__ void points_advect_kernel(double* __restrict__ pts, const float* __restrict__ u, long long n, double dt,
+                                     double ux, double uy, double uz)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pts[3 * i] += dt * ((double)u[i] + ux);
+    pts[3 * i + 1] += dt * ((double)u[n + i] + uy);
+    pts[3 * i + 2] += dt * ((double)u[2 * n + i] + uz);
+}
+
+cudaError_t run_wake_segments(const double* nodes, const double* gamma, long long R, long long nb, long long S,
+                              float* seg_a, float* seg_b, cudaStream_t st)
+{
+    const long long np = R * nb * S;
+    if (np == 0) return cudaSuccess;
+    trace_launch();
+    wake_segments_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(nodes, gamma, R, nb, S,
+                                                                       reinterpret_cast<float4*>(seg_a),
+                                                                       reinterpret_cast<float4*>(seg_b));
+    return cudaGetLastError();
+}
+
+cudaError_t run_points_pack(const double* pts, long long n, float* tgt, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    trace_launch();
+    points_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, n, reinterpret_cast<float4*>(tgt));
+    return cudaGetLastError();
+}
+
+cudaError_t run_points_advect(double* pts, const float* u, long long n, double dt, const float* u_inf, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    trace_launch();
+    points_advect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, u, n, dt, u_inf ? u_inf[0] : 0.0,
+                                                                      u_inf ? u_inf[1] : 0.0, u_inf ? u_inf[2] : 0.0);
+    return cudaGetLastError();
 }
 
 namespace {

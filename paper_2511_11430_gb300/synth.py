@@ -363,3 +363,18 @@ def rotor_wake_edges(seed, n_rows, n_span=40, n_blades=4, dpsi_deg=5.0):
     ds_tip = float(np.linalg.norm(np.array(B[n_span]) - np.array(A[n_span])))
     return (np.array(A), np.array(B), np.array(g), np.array(gnb), np.array(hn, dtype=np.int32),
             np.array(tr, dtype=np.int32), ds_tip)
+
+
+def blade_trailing_edge(rings, n_blades, n_span, n_chord):
+    """Trailing-edge node lines [n_blades, n_span + 1, 3] of blade_lattice rings (blades
+    turning with spin +1: ring corners leading-root, trailing-root, trailing-tip,
+    leading-tip), and the indices [n_blades, n_span] of the trailing-edge rings."""
+    idx = np.zeros((n_blades, n_span), dtype=np.int64)
+    te = np.zeros((n_blades, n_span + 1, 3))
+    for b in range(n_blades):
+        for i in range(n_span):
+            k = (b * n_span + i) * n_chord + (n_chord - 1)
+            idx[b, i] = k
+            te[b, i] = rings[k, 1, :3]
+        te[b, n_span] = rings[idx[b, n_span - 1], 2, :3]
+    return te, idx

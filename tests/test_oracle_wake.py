@@ -123,3 +123,16 @@ def test_converted_particles_induce_the_velocity_of_the_panel_row():
         errs.append(np.abs(u - u_ref).max() / np.abs(u_ref).max())
     assert errs[-1] < 1e-3
     assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0  # second order
+
+
+def test_conventional_strategy_gives_every_trailed_edge_the_same_count():
+    """A negative n_tip: -n_tip particles on every trailed edge whatever its length
+    (the uniform strategy Eq. 8 replaces); shed edges keep n_shed."""
+    U, D, gamma = _row()
+    a, b, g, gnb, hn, tr = oracle.wake_row_edges(U, D, gamma)
+    S = gamma.size
+    ds_tip = np.linalg.norm(b[S] - a[S])
+    _, _, conv = oracle.wake_convert(a, b, g, gnb, hn, tr, ds_tip=ds_tip, n_tip=-3, n_shed=1)
+    _, _, adap = oracle.wake_convert(a, b, g, gnb, hn, tr, ds_tip=ds_tip, n_tip=3, n_shed=1)
+    assert all(conv[:S + 1] == 3) and all(conv[S + 1:] == 1)
+    assert adap[S] == 3 and adap[:S + 1].sum() < conv[:S + 1].sum()
