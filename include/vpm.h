@@ -69,6 +69,7 @@ typedef enum vpm_status {
 #define VPM_OP_BACKWARD 6
 #define VPM_OP_WAKE_CONVERT 7
 #define VPM_OP_WAKE_ROW 8
+#define VPM_OP_LOADS 9
 
 /* Largest particle / target / segment count accepted (int32 indexing). */
 #define VPM_MAX_ITEMS (1 << 30)
@@ -104,6 +105,7 @@ vpm_status vpm_device_error(int* code);
  *   VPM_OP_AIC_SOLVE: order n_tgt                                  (others ignored)
  *   VPM_OP_BACKWARD:  n_src particles, n_tgt targets
  *   VPM_OP_WAKE_CONVERT: n_src edges;  VPM_OP_WAKE_ROW: n_src panels of the row
+ *   VPM_OP_LOADS:     m_seg bound segments, n_tgt panels
  * `flags` as passed to the operation.  Host-only; does not launch. */
 vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_seg, int flags, size_t* bytes);
 
@@ -221,6 +223,29 @@ vpm_status vpm_points_pack(const double* pts_d, int64_t n, float* tgt_d, void* s
  * float[3] or NULL. */
 vpm_status vpm_points_advect(double* pts_d, const float* u_d, int64_t n, double dt, const float* u_inf,
                              void* stream);
+
+/* ---- blade loads (Sec. II.A) ----------------------------------------------
+ * Steady part by the Kutta-Joukowski theorem on every bound segment s (panel side),
+ *   F_s = rho Gamma_s (V_s x (b_s - a_s)),  V_s = u_inf - omega x (mid_s - hub) + u_ind(mid_s),
+ * unsteady part at every panel p (unsteady Bernoulli),
+ *   F_p = rho (gamma_p - gamma_prev_p) / dt  A_p n_p,  A_p = |(c2 - c0) x (c3 - c1)| / 2,
+ * summed (FP64, fixed order) into out_d[0..2] = force and out_d[3..5] = moment about
+ * hub.  The caller lists the bound segments: every blade ring's sides with the ring's
+ * circulation (vpm_ring_segments), so that shared sides carry their net circulation,
+ * with the trailing-edge sides given zero circulation (their net circulation with the
+ * wake row shed at the same step vanishes: Kutta condition).
+ *   seg_a_d, seg_b_d [m][4] float (a.w = circulation); u_ind_d [3][m] float, the
+ *   induced velocity at the midpoints (vpm_segment_midpoints gives the targets);
+ *   omega, hub, u_inf host double[3]; rings_d [n][4][4] float, normal_d [n][4]
+ *   float, gamma_d, gamma_prev_d [n] double (gamma_prev_d NULL: no unsteady part);
+ *   out_d 6 doubles on the device.  Workspace: VPM_OP_LOADS. */
+vpm_status vpm_blade_loads(const float* seg_a_d, const float* seg_b_d, int64_t m, const float* u_ind_d,
+                           const double* omega, const double* hub, const double* u_inf, const float* rings_d,
+                           const float* normal_d, const double* gamma_d, const double* gamma_prev_d, int64_t n,
+                           double dt, double rho, double* out_d, void* ws_d, size_t ws_bytes, void* stream);
+
+/* FP32 targets [m][4] = (midpoint, 0) of m segments. */
+vpm_status vpm_segment_midpoints(const float* seg_a_d, const float* seg_b_d, int64_t m, float* tgt_d, void* stream);
 
 /* ---- self-test of the bounded device waits (no counterpart in the paper) -----
  * Every wait inside the library's kernels (on an mbarrier phase) gives up after a

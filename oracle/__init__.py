@@ -73,6 +73,7 @@ def _load():
                 "orc_wake_convert": [P, P, P, P, IP, IP, i64, d, i, i, i64, P, P, LP],
                 "orc_wake_row_edges": [P, P, P, i64, P, P, P, P, IP, IP],
                 "orc_set_threads": [i],
+                "orc_blade_loads": [P, P, i64, P, P, P, P, P, P, P, P, i64, d, d, P],
             }
             rtype = {"orc_lu_solve": ctypes.c_int, "orc_wake_convert": ctypes.c_int64}
             for name, args in sig.items():
@@ -271,3 +272,21 @@ def wake_row_edges(U, D, gamma):
     tr = np.zeros(ne, dtype=np.int32)
     _load().orc_wake_row_edges(_p(U), _p(D), _p(g), S, _p(a), _p(b), _p(ge), _p(gnb), _ip(hn), _ip(tr))
     return a, b, ge, gnb, hn, tr
+
+
+def blade_loads(seg_a, seg_b, u_ind, omega, hub, u_inf, rings, normal, gamma, gamma_prev, dt, rho=1.225):
+    """(force [3], moment about hub [3]) of the bound segments (Kutta-Joukowski) and of the
+    panels' circulation change (unsteady Bernoulli); see orc_blade_loads."""
+    sa, sb = _f64(seg_a, 4), _f64(seg_b, 4)
+    u = _f64(u_ind).reshape(-1, 3)
+    rings = _f64(rings)
+    if rings.shape[-1] == 3:
+        rings = _f64(rings, 4)
+    rings = np.ascontiguousarray(rings.reshape(-1, 4, 4))
+    nrm = _f64(normal, 4)
+    g = _f64(gamma).ravel()
+    gp = None if gamma_prev is None else _f64(gamma_prev).ravel()
+    out = np.zeros(6)
+    _load().orc_blade_loads(_p(sa), _p(sb), sa.shape[0], _p(u), _p(_f64(omega)), _p(_f64(hub)), _p(_f64(u_inf)),
+                            _p(rings), _p(nrm), _p(g), _p(gp), g.size, float(dt), float(rho), _p(out))
+    return out[:3], out[3:]

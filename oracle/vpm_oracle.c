@@ -650,3 +650,60 @@ void orc_set_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------------
+ * Blade loads (Sec. II.A): the steady part by the Kutta-Joukowski theorem on every
+ * bound segment (panel side), F_s = rho Gamma_s (V_s x (b_s - a_s)), V_s the air
+ * velocity relative to the blade at the segment midpoint,
+ *   V_s = u_inf - omega x (mid - hub) + u_ind(mid),
+ * and the unsteady part at the centre of every panel (unsteady Bernoulli),
+ *   F_p = rho (Gamma_p - Gamma_p,prev) / dt  A_p n_p,
+ * A_p the area of the ring's quadrilateral (half the norm of the cross product of its
+ * diagonals).  out[0..2] = total force, out[3..5] = total moment about hub.  The
+ * caller lists the bound segments: every ring's four sides with the ring's
+ * circulation, so that shared sides carry their net circulation, the trailing-edge
+ * sides with zero (their net circulation with the row shed at the same step vanishes).
+ * seg_a [m][4] (a, Gamma), seg_b [m][4]; u_ind [m][3]; rings [n][4][4] corners;
+ * normal [n][4]; gamma, gamma_prev [n] (gamma_prev NULL: no unsteady part).
+ * ------------------------------------------------------------------------------ */
+void orc_blade_loads(const double* sa, const double* sb, int64_t m, const double* u_ind, const double* omega,
+                     const double* hub, const double* u_inf, const double* rings, const double* normal,
+                     const double* gamma, const double* gamma_prev, int64_t n, double dt, double rho, double* out)
+{
+    double F[3] = {0, 0, 0}, M[3] = {0, 0, 0};
+    for (int64_t s = 0; s < m; ++s) {
+        const double* a = &sa[4 * s];
+        const double* b = &sb[4 * s];
+        double mid[3], dl[3], rel[3], w[3], V[3], f[3], mom[3];
+        for (int c = 0; c < 3; ++c) {
+            mid[c] = 0.5 * (a[c] + b[c]);
+            dl[c] = b[c] - a[c];
+            rel[c] = mid[c] - hub[c];
+        }
+        cross(omega, rel, w);
+        for (int c = 0; c < 3; ++c) V[c] = u_inf[c] - w[c] + u_ind[3 * s + c];
+        cross(V, dl, f);
+        for (int c = 0; c < 3; ++c) f[c] *= rho * a[3];
+        cross(rel, f, mom);
+        for (int c = 0; c < 3; ++c) F[c] += f[c], M[c] += mom[c];
+    }
+    if (gamma_prev) {
+        for (int64_t p = 0; p < n; ++p) {
+            const double* r = &rings[16 * p];
+            double d1[3], d2[3], cr[3], ctr[3], rel[3], f[3], mom[3];
+            for (int c = 0; c < 3; ++c) {
+                d1[c] = r[8 + c] - r[c];      /* corner 2 - corner 0 */
+                d2[c] = r[12 + c] - r[4 + c]; /* corner 3 - corner 1 */
+                ctr[c] = 0.25 * (r[c] + r[4 + c] + r[8 + c] + r[12 + c]);
+                rel[c] = ctr[c] - hub[c];
+            }
+            cross(d1, d2, cr);
+            const double area = 0.5 * sqrt(dot(cr, cr));
+            const double k = rho * (gamma[p] - gamma_prev[p]) / dt * area;
+            for (int c = 0; c < 3; ++c) f[c] = k * normal[4 * p + c];
+            cross(rel, f, mom);
+            for (int c = 0; c < 3; ++c) F[c] += f[c], M[c] += mom[c];
+        }
+    }
+    for (int c = 0; c < 3; ++c) out[c] = F[c], out[3 + c] = M[c];
+}

@@ -38,6 +38,9 @@ class OracleRotorWake:
         te = self._geometry(0.0)[4]
         self.nodes = te.reshape(1, self.nb, self.S + 1, 3).copy()
         self.gammas = np.zeros((0, self.nb, self.S))
+        self.rho = 1.225
+        self.gam_prev = None
+        self.history = []
 
     def _geometry(self, t):
         rings, colloc, normal, vrel, _ = synth.blade_lattice(self.nb, self.S, self.nc, phase=synth.OMEGA * t)
@@ -79,6 +82,7 @@ class OracleRotorWake:
         bsa, bsb = synth.ring_segments(rings, _f32(gam))
         sa = np.concatenate([bsa, wsa]) if len(wsa) else bsa
         sb = np.concatenate([bsb, wsb]) if len(wsb) else bsb
+        self._loads(rings, normal, gam, te_idx, bsa, bsb, sa, sb)
         pts = self.nodes.reshape(-1, 3)
         u_n = self._velocity(pts, sa, sb)
         x_old, G_old = self.x, self.G
@@ -95,6 +99,19 @@ class OracleRotorWake:
             self._convert_oldest()
         self.t += self.dt
         return gam
+
+    def _loads(self, rings, normal, gam, te_idx, bsa, bsb, sa, sb):
+        # the bound segments: every side of every blade ring, except the trailing-edge sides,
+        # whose net circulation with the row shed this step is zero (Kutta condition)
+        ba, bb = _f32(bsa).copy(), _f32(bsb)
+        ba[4 * te_idx.ravel() + 1, 3] = 0.0
+        mid = ((ba[:, :3].astype(np.float32) + bb[:, :3].astype(np.float32)) * np.float32(0.5)).astype(np.float64)
+        u_mid = _f32(self._velocity(mid, sa, sb))
+        F, M = oracle.blade_loads(ba, bb, u_mid, [0.0, 0.0, synth.OMEGA], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0], rings,
+                                  normal, gam, self.gam_prev, self.dt, self.rho)
+        q = self.rho * np.pi * synth.R ** 2 * (synth.OMEGA * synth.R) ** 2
+        self.history.append((self.t, F[2] / q, -M[2] / (q * synth.R)))
+        self.gam_prev = gam.copy()
 
     def _convert_oldest(self):
         R = self.rows

@@ -32,6 +32,7 @@ VPM_OP_AIC_SOLVE = 5
 VPM_OP_BACKWARD = 6
 VPM_OP_WAKE_CONVERT = 7
 VPM_OP_WAKE_ROW = 8
+VPM_OP_LOADS = 9
 
 VPM_TRACE_ALL = 0
 VPM_TRACE_SWEEP = 1
@@ -92,6 +93,8 @@ SIGNATURES = {
     "vpm_wake_segments": (_INT, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
     "vpm_points_pack": (_INT, [_P, _I64, _P, _P]),
     "vpm_ring_segments": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "vpm_segment_midpoints": (_INT, [_P, _P, _I64, _P, _P]),
+    "vpm_blade_loads": (_INT, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _D, _D, _P, _P, _SZ, _P]),
     "vpm_points_advect": (_INT, [_P, _P, _I64, _D, _P, _P]),
     "vpm_wake_convert": (_INT, [_P, _P, _P, _P, _P, _P, _I64, _D, _INT, _INT, _P, _P, _I64, _P, _P, _SZ, _P]),
     "vpm_wake_convert_row": (_INT, [_P, _P, _P, _I64, _D, _INT, _INT, _P, _P, _I64, _P, _P, _SZ, _P]),

@@ -161,6 +161,9 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
     case VPM_OP_WAKE_CONVERT:
         *bytes = wake_workspace(n_src, false);
         break;
+    case VPM_OP_LOADS:
+        *bytes = loads_workspace(m_seg, n_tgt);
+        break;
     case VPM_OP_WAKE_ROW:
         REQUIRE(n_src >= 1, "a wake row needs at least one panel");
         *bytes = wake_workspace(3 * n_src + 1, true);
@@ -510,6 +513,43 @@ vpm_status vpm_points_advect(double* pts_d, const float* u_d, int64_t n, double 
     REQUIRE(pts_d && u_d && aligned8(pts_d) && aligned4(u_d), "pts/u must be device pointers");
     cudaError_t e = run_points_advect(pts_d, u_d, n, dt, u_inf, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_points_advect");
+}
+
+vpm_status vpm_segment_midpoints(const float* seg_a_d, const float* seg_b_d, int64_t m, float* tgt_d, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(m, "m")) != VPM_OK) return s;
+    if (m == 0) return ok();
+    REQUIRE(seg_a_d && seg_b_d && tgt_d && aligned16(seg_a_d) && aligned16(seg_b_d) && aligned16(tgt_d),
+            "seg_a/seg_b/tgt must be 16-byte aligned device pointers");
+    cudaError_t e = run_segment_midpoints(seg_a_d, seg_b_d, m, tgt_d, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_segment_midpoints");
+}
+
+vpm_status vpm_blade_loads(const float* seg_a_d, const float* seg_b_d, int64_t m, const float* u_ind_d,
+                           const double* omega, const double* hub, const double* u_inf, const float* rings_d,
+                           const float* normal_d, const double* gamma_d, const double* gamma_prev_d, int64_t n,
+                           double dt, double rho, double* out_d, void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(m, "m")) != VPM_OK) return s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    REQUIRE(omega && hub && u_inf, "omega, hub and u_inf are host double[3]");
+    REQUIRE(out_d && aligned8(out_d), "out must be a device pointer to 6 doubles");
+    REQUIRE(isfinite(rho) && (!gamma_prev_d || (dt > 0.0 && isfinite(dt))), "rho finite; dt > 0 with gamma_prev");
+    REQUIRE(m == 0 || (seg_a_d && seg_b_d && u_ind_d && aligned16(seg_a_d) && aligned16(seg_b_d) && aligned4(u_ind_d)),
+            "seg_a/seg_b (16-byte aligned) and u_ind must be device pointers");
+    REQUIRE(!gamma_prev_d || n == 0 ||
+                (rings_d && normal_d && gamma_d && aligned16(rings_d) && aligned16(normal_d) && aligned8(gamma_d) &&
+                 aligned8(gamma_prev_d)),
+            "rings/normal (16-byte aligned) and gamma must be device pointers");
+    const size_t need = loads_workspace(m, n);
+    if (!ws_d || ws_bytes < need || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", need, ws_bytes);
+    cudaError_t e = run_blade_loads(seg_a_d, seg_b_d, m, u_ind_d, omega, hub, u_inf, rings_d, normal_d, gamma_d,
+                                    gamma_prev_d, gamma_prev_d ? n : 0, dt, rho, out_d, static_cast<char*>(ws_d),
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_blade_loads");
 }
 
 vpm_status vpm_selftest_wait(double limit_ms, int* completed, void* stream)

@@ -100,6 +100,12 @@ cudaError_t run_ring_segments(const float* rings, const double* gamma, long long
                               cudaStream_t st);
 cudaError_t run_points_pack(const double* pts, long long n, float* tgt, cudaStream_t st);
 cudaError_t run_points_advect(double* pts, const float* u, long long n, double dt, const float* u_inf, cudaStream_t st);
+size_t loads_workspace(long long m, long long n);
+cudaError_t run_segment_midpoints(const float* seg_a, const float* seg_b, long long m, float* tgt, cudaStream_t st);
+cudaError_t run_blade_loads(const float* seg_a, const float* seg_b, long long m, const float* u_ind,
+                            const double* omega, const double* hub, const double* u_inf, const float* rings,
+                            const float* normal, const double* gamma, const double* gamma_prev, long long n, double dt,
+                            double rho, double* out, char* ws, cudaStream_t st);
 size_t wake_workspace(long long m, bool row_edges);
 vpm_status run_wake_convert(const double* a, const double* b, const double* gamma, const double* gamma_nb,
                             const int* has_nb, const int* trailed, long long m, double ds_tip, int n_tip, int n_shed,

@@ -66,11 +66,17 @@ __device__ __forceinline__ long long block_scan(long long v, long long* wsum, lo
     return r;
 }
 
+// Also writes every edge's particle strength Delta Gamma (b - a) / n (Eq. 6, 7): the
+// same for all n particles of the edge, so it is formed once here.
 __global__ void __launch_bounds__(SCAN_THREADS) wake_count_kernel(const double* __restrict__ a,
                                                                   const double* __restrict__ b,
+                                                                  const double* __restrict__ gamma,
+                                                                  const double* __restrict__ gamma_nb,
+                                                                  const int* __restrict__ has_nb,
                                                                   const int* __restrict__ trailed, long long m,
                                                                   double ds_tip, int n_tip, int n_shed,
                                                                   long long* __restrict__ counts,
+                                                                  double* __restrict__ strength,
                                                                   long long* __restrict__ tile_sum)
 {
     __shared__ long long wsum[SCAN_THREADS / 32];
@@ -83,6 +89,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) wake_count_kernel(const double* 
             const long long c = wake_count(a + 3 * i, b + 3 * i, trailed[i], ds_tip, n_tip, n_shed);
             counts[i] = c;
             s += c;
+            const double dG = (has_nb && has_nb[i]) ? __dsub_rn(gamma[i], gamma_nb[i]) : gamma[i];  // Eq. 7
+            const double nd = (double)c;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                strength[3 * i + q] = __ddiv_rn(__dmul_rn(dG, __dsub_rn(b[3 * i + q], a[3 * i + q])), nd);  // Eq. 6
         }
     }
     long long tot;
@@ -135,8 +146,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wake_offsets_kernel(const long l
 // index within the edge k = p - offsets[i].  Writes are coalesced across the warp
 // (planar outputs of leading dimension ld).
 __global__ void wake_scatter_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                    const double* __restrict__ gamma, const double* __restrict__ gamma_nb,
-                                    const int* __restrict__ has_nb, long long m,
+                                    const double* __restrict__ strength, long long m,
                                     const long long* __restrict__ counts, const long long* __restrict__ offsets,
                                     long long total, double* __restrict__ x, double* __restrict__ G, long long ld)
 {
@@ -153,14 +163,11 @@ __global__ void wake_scatter_kernel(const double* __restrict__ a, const double* 
     const long long i = lo, k = p - offsets[i];
     const double* ai = a + 3 * i;
     const double* bi = b + 3 * i;
-    const double dG = (has_nb && has_nb[i]) ? __dsub_rn(gamma[i], gamma_nb[i]) : gamma[i];  // Eq. 7
-    const double nd = (double)counts[i];
-    const double t = __ddiv_rn(__dadd_rn((double)k, 0.5), nd);
+    const double t = __ddiv_rn(__dadd_rn((double)k, 0.5), (double)counts[i]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double d = __dsub_rn(bi[c], ai[c]);
-        x[c * ld + p] = __dadd_rn(ai[c], __dmul_rn(t, d));
-        G[c * ld + p] = __ddiv_rn(__dmul_rn(dG, d), nd);  // Eq. 6
+        x[c * ld + p] = __dadd_rn(ai[c], __dmul_rn(t, __dsub_rn(bi[c], ai[c])));
+        G[c * ld + p] = strength[3 * i + c];
     }
 }
 
@@ -306,7 +313,7 @@ cudaError_t run_points_advect(double* pts, const float* u, long long n, double d
 
 namespace {
 struct WakeWs {
-    size_t counts, offsets, total, tiles, ea, eb, eg, egnb, ehn, etr, bytes;
+    size_t counts, offsets, total, tiles, strength, ea, eb, eg, egnb, ehn, etr, bytes;
 };
 WakeWs wake_layout(long long m, bool row_edges)
 {
@@ -316,6 +323,7 @@ WakeWs wake_layout(long long m, bool row_edges)
     w.offsets = cv.take((size_t)m * sizeof(long long));
     w.total = cv.take(sizeof(long long));
     w.tiles = cv.take((size_t)((m + SCAN_TILE - 1) / SCAN_TILE + 1) * sizeof(long long));
+    w.strength = cv.take((size_t)m * 3 * sizeof(double));
     if (row_edges) {
         w.ea = cv.take((size_t)m * 3 * sizeof(double));
         w.eb = cv.take((size_t)m * 3 * sizeof(double));
@@ -343,8 +351,9 @@ vpm_status run_wake_convert(const double* a, const double* b, const double* gamm
     long long* tiles = reinterpret_cast<long long*>(ws + L.tiles);
     const long long ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
     trace_launch();
-    wake_count_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(a, b, trailed, m, ds_tip, n_tip, n_shed, counts,
-                                                                 tiles);
+    double* strength = reinterpret_cast<double*>(ws + L.strength);
+    wake_count_kernel<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(a, b, gamma, gamma_nb, has_nb, trailed, m, ds_tip,
+                                                                 n_tip, n_shed, counts, strength, tiles);
     trace_launch();
     wake_tile_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(tiles, ntiles, total);
     trace_launch();
@@ -363,8 +372,8 @@ vpm_status run_wake_convert(const double* a, const double* b, const double* gamm
     if (h == 0) return VPM_OK;
     const int tpb = 256;
     trace_launch();
-    wake_scatter_kernel<<<(unsigned)((h + tpb - 1) / tpb), tpb, 0, st>>>(a, b, gamma, gamma_nb, has_nb, m, counts,
-                                                                      offsets, h, x, G, ld);
+    wake_scatter_kernel<<<(unsigned)((h + tpb - 1) / tpb), tpb, 0, st>>>(a, b, strength, m, counts, offsets, h, x,
+                                                                      G, ld);
     if (cudaGetLastError() != cudaSuccess) {
         *msg = cudaGetErrorString(cudaGetLastError());
         return VPM_ERR_CUDA;

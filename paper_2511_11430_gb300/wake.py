@@ -12,7 +12,12 @@ Each step of ``RotorWake.step``:
      trailing-edge line of t, carrying the trailing-edge panels' circulation (Kutta
      condition; upstream rows keep their strength);
   5. the oldest row beyond ``max_rows`` converted into particles (Eq. 6-8; adaptive
-     counts, or the conventional uniform count with ``adaptive=False``) and appended.
+     counts, or the conventional uniform count with ``adaptive=False``) and appended;
+  6. the blade loads at time t: Kutta-Joukowski on every bound segment (the blade rings'
+     sides but the trailing-edge ones, whose net circulation with the row shed at this
+     step vanishes) with the velocity relative to the blade at its midpoint, and the
+     unsteady Bernoulli term of every panel; thrust and torque coefficients C_T = T / (rho pi R^2 (Omega R)^2),
+     C_Q = Q / (rho pi R^3 (Omega R)^2) are kept in ``history``.
 
 Rows use the ring convention of vpm_wake_convert_row (U[p] -> U[p+1] -> D[p+1] ->
 D[p]); the blade's trailing-edge segments run root -> tip, so a row shed behind a panel
@@ -55,6 +60,9 @@ class RotorWake:
         self.nodes = _dev(te, torch.float64, self.dev).reshape(1, self.nb, self.S + 1, 3).contiguous()
         self.gammas = torch.zeros((0, self.nb, self.S), dtype=torch.float64, device=self.dev)
         self.converted = 0  # particles created so far
+        self.rho = 1.225
+        self.gam_prev = None
+        self.history = []  # (t, C_T, C_Q) per step
 
     # ---- geometry (prescribed rotation: synthetic input) -------------------------
     def _geometry_host(self, t):
@@ -113,6 +121,7 @@ class RotorWake:
                                     api._stream()))
         seg_a = torch.cat([bsa, wsa]).contiguous()
         seg_b = torch.cat([bsb, wsb]).contiguous()
+        self._loads(lib, rings, normal, gam_b, te_idx, bsa, bsb, seg_a, seg_b, pos, strn)
         # 3. convect the node lines, advance the particles
         pts = self.nodes.reshape(-1, 3)
         npts = pts.shape[0]
@@ -135,6 +144,29 @@ class RotorWake:
         self.t += self.dt
         self.steps += 1
         return gam_b
+
+    def _loads(self, lib, rings, normal, gam_b, te_idx, bsa, bsb, seg_a, seg_b, pos, strn):
+        # the bound segments: every side of every blade ring, except the trailing-edge sides,
+        # whose net circulation with the row shed this step is zero (Kutta condition)
+        ba = bsa.clone()
+        ba[torch.from_numpy(4 * te_idx.ravel() + 1).to(self.dev), 3] = 0.0
+        bb = bsb
+        m = ba.shape[0]
+        mid = torch.empty((m, 4), dtype=torch.float32, device=self.dev)
+        check(lib.vpm_segment_midpoints(api._void(ba), api._void(bb), m, api._void(mid), api._stream()))
+        u_mid = self._velocity(mid, seg_a, seg_b, pos, strn).contiguous()
+        out = torch.empty(6, dtype=torch.float64, device=self.dev)
+        D3 = ctypes.c_double * 3
+        n = rings.shape[0]
+        w = self.ws.get(api.workspace_size(_lib.VPM_OP_LOADS, 0, n, m, 0))
+        check(lib.vpm_blade_loads(api._void(ba), api._void(bb), m, api._void(u_mid), D3(0.0, 0.0, synth.OMEGA),
+                                  D3(0.0, 0.0, 0.0), D3(0.0, 0.0, 0.0), api._void(rings), api._void(normal),
+                                  api._void(gam_b), api._void(self.gam_prev), n, ctypes.c_double(self.dt),
+                                  ctypes.c_double(self.rho), api._void(out), api._void(w), w.numel(), api._stream()))
+        F = out.cpu().numpy()
+        q = self.rho * np.pi * synth.R ** 2 * (synth.OMEGA * synth.R) ** 2
+        self.history.append((self.t, F[2] / q, -F[5] / (q * synth.R)))
+        self.gam_prev = gam_b.clone()
 
     def _convert_oldest(self):
         R = self.rows

@@ -1,7 +1,7 @@
-"""The near-wake time loop (shedding, convection, conversion: Sec. II.A-C) run through
-the library against the FP64 oracle loop on a small rotor: blade circulations each
-step, the particle count after conversions (an integer decided in FP64 on both sides),
-and the converted and convected particles."""
+"""The near-wake time loop (shedding, convection, conversion, loads: Sec. II.A-C) run
+through the library against the FP64 oracle loop on a small rotor: blade circulations
+and thrust/torque coefficients each step, the particle count after conversions (an
+integer decided in FP64 on both sides), and the converted and convected particles."""
 import numpy as np
 import pytest
 
@@ -36,6 +36,9 @@ def test_rotor_wake_loop_matches_oracle(wake_mod, adaptive):
     assert rel_l2(g.x.cpu().numpy().T, o.x) <= 1e-6
     assert rel_l2(g.G.cpu().numpy().T, o.G) <= 2e-5
     assert rel_l2(g.nodes.cpu().numpy(), o.nodes) <= 1e-6
+    hg, ho = np.array(g.history), np.array(o.history)
+    np.testing.assert_allclose(hg[:, 1], ho[:, 1], rtol=1e-4, atol=1e-8)  # C_T per step
+    np.testing.assert_allclose(hg[:, 2], ho[:, 2], rtol=1e-3, atol=1e-3 * np.abs(ho[:, 2]).max())  # C_Q
 
 
 def test_adaptive_conversion_creates_fewer_particles(wake_mod):

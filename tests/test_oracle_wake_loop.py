@@ -34,3 +34,40 @@ def test_conversions_keep_zero_net_circulation_and_adaptive_is_leaner():
     # the conventional count is exact: n_tip per trailed edge, n_shed per shed edge
     S, nb = kw["n_span"], kw["n_blades"]
     assert len(c.x) == nb * ((S + 1) * 4 + 2 * S * 1)
+
+
+def test_kutta_joukowski_pins():
+    """A closed ring in a uniform stream carries no force; one straight bound segment of
+    circulation Gamma and length L across a stream V carries rho Gamma |V| L along V x dl;
+    a panel whose circulation grows at dGamma/dt gets rho dGamma/dt A along its normal."""
+    import oracle
+
+    ring = np.array([[[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]]], float)
+    a, b = synth.ring_segments(ring, np.array([2.0]))
+    nrm = np.array([[0.0, 0.0, 1.0, 0.0]])
+    F, _ = oracle.blade_loads(a, b, np.zeros((4, 3)), [0, 0, 0], [0, 0, 0], [3.0, 1.0, 0.5], ring, nrm, [2.0], None,
+                              1e-3, rho=1.2)
+    np.testing.assert_allclose(F, 0.0, atol=1e-14)
+    sa = np.array([[0.0, 0.0, 0.0, 1.5]])
+    sb = np.array([[0.0, 2.0, 0.0, 0.0]])
+    F, M = oracle.blade_loads(sa, sb, np.zeros((1, 3)), [0, 0, 0], [0, 0, 0], [10.0, 0.0, 0.0], ring, nrm, [0.0],
+                              None, 1e-3, rho=1.2)
+    np.testing.assert_allclose(F, [0.0, 0.0, 1.2 * 1.5 * 10.0 * 2.0], rtol=1e-15)  # (10,0,0) x (0,2,0) = +z
+    np.testing.assert_allclose(M, np.cross([0.0, 1.0, 0.0], F), rtol=1e-15)
+    F, _ = oracle.blade_loads(sa[:0], sb[:0], np.zeros((0, 3)), [0, 0, 0], [0, 0, 0], [0, 0, 0], ring, nrm, [3.0],
+                              [1.0], 0.5, rho=1.2)
+    np.testing.assert_allclose(F, [0.0, 0.0, 1.2 * (3.0 - 1.0) / 0.5 * 1.0], rtol=1e-15)
+
+
+def test_rotor_thrust_builds_up_to_the_momentum_theory_range():
+    """Started impulsively, the synthetic rotor's thrust coefficient grows as the starting
+    vortex leaves the trailing edge and settles in the range blade-element momentum
+    theory gives for 8 deg collective and this solidity (C_T of order 0.01)."""
+    o = OracleRotorWake(n_blades=2, n_span=12, n_chord=3, max_rows=4, n_tip=3)
+    for _ in range(10):
+        o.step()
+    ct = np.array([h[1] for h in o.history])
+    cq = np.array([h[2] for h in o.history])
+    assert ct[-1] > ct[2] > 0
+    assert 0.004 < ct[-1] < 0.02
+    assert 0.0 < cq[-1] < 0.1 * ct[-1]
