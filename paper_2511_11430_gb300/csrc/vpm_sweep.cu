@@ -257,27 +257,39 @@ __device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4
     }
 }
 
-// s += J_tile^T Gamma_i (times 4 pi) from a tile's partial S and G': the far
-// tiles and segment tiles, whose stretching does not cancel.
+// The tile's sums without stretching (a far particle tile or a segment tile) into the
+// fold rows of the stretching sweep: rows 0..13 copied, rows 14..16 set to the tile's
+// transposed stretching J_tile^T Gamma_i (times 4 pi), formed from its partial S and
+// G' -- for these tiles the two terms do not cancel.  The target's own strength is
+// read here, after the tile's loop, so that it is not held in registers through it.
 template <bool GRAD, bool STRETCH>
-__device__ __forceinline__ void stretch_from_tile(Acc<GRAD, STRETCH>& a, const Own& o)
+__device__ __forceinline__ void finish_tile(Acc<GRAD, STRETCH>& a, const Acc<GRAD, false>& t, const float4* tstr,
+                                            int i0, int i1, int n_tgt)
 {
-    if (!STRETCH) return;
-    const f2 Sx = a.v[3], Sy = a.v[4], Sz = a.v[5];
-    const f2 Gxx = a.v[6], Gxy = a.v[7], Gxz = a.v[8], Gyx = a.v[9], Gyy = a.v[10], Gyz = a.v[11], Gzx = a.v[12],
-             Gzy = a.v[13];
+    static_assert(GRAD || !STRETCH, "stretching needs the gradient sums");
+#pragma unroll
+    for (int q = 0; q < Acc<GRAD, false>::N; ++q) a.v[q] = t.v[q];
+    if constexpr (STRETCH) {
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+    if (i0 < n_tgt) g0 = tstr[i0];
+    if (i1 < n_tgt) g1 = tstr[i1];
+    const f2 ogx = make_float2(g0.x, g1.x), ogy = make_float2(g0.y, g1.y), ogz = make_float2(g0.z, g1.z);
+    const f2 Sx = t.v[3], Sy = t.v[4], Sz = t.v[5];
+    const f2 Gxx = t.v[6], Gxy = t.v[7], Gxz = t.v[8], Gyx = t.v[9], Gyy = t.v[10], Gyz = t.v[11], Gzx = t.v[12],
+             Gzy = t.v[13];
     const f2 Gzz = mul2(add2(Gxx, Gyy), splat(-1.f));
     const f2 m3 = splat(-3.f);
     // Gamma_i x S - 3 G'^T Gamma_i
-    const f2 tx = sub2(mul2(o.gy, Sz), mul2(o.gz, Sy));
-    const f2 ty = sub2(mul2(o.gz, Sx), mul2(o.gx, Sz));
-    const f2 tz = sub2(mul2(o.gx, Sy), mul2(o.gy, Sx));
-    const f2 gx = fma2(Gzx, o.gz, fma2(Gyx, o.gy, mul2(Gxx, o.gx)));
-    const f2 gy = fma2(Gzy, o.gz, fma2(Gyy, o.gy, mul2(Gxy, o.gx)));
-    const f2 gz = fma2(Gzz, o.gz, fma2(Gyz, o.gy, mul2(Gxz, o.gx)));
-    a.v[14] = add2(a.v[14], fma2(m3, gx, tx));
-    a.v[15] = add2(a.v[15], fma2(m3, gy, ty));
-    a.v[16] = add2(a.v[16], fma2(m3, gz, tz));
+    const f2 tx = sub2(mul2(ogy, Sz), mul2(ogz, Sy));
+    const f2 ty = sub2(mul2(ogz, Sx), mul2(ogx, Sz));
+    const f2 tz = sub2(mul2(ogx, Sy), mul2(ogy, Sx));
+    const f2 gx = fma2(Gzx, ogz, fma2(Gyx, ogy, mul2(Gxx, ogx)));
+    const f2 gy = fma2(Gzy, ogz, fma2(Gyy, ogy, mul2(Gxy, ogx)));
+    const f2 gz = fma2(Gzz, ogz, fma2(Gyz, ogy, mul2(Gxz, ogx)));
+    a.v[14] = fma2(m3, gx, tx);
+    a.v[15] = fma2(m3, gy, ty);
+    a.v[16] = fma2(m3, gz, tz);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -478,7 +490,6 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
     // ---------------- consumers ----------------
     const int ct = warp * 32 + lane;  // consumer thread index
     Acc<GRAD, STRETCH> acc;
-    Own own{zero2(), zero2(), zero2()};
     f2 X = zero2(), Y = zero2(), Z = zero2();
     int t = t0, k = k0, cur_t = -1;
     auto zero_run = [&]() {
@@ -504,14 +515,6 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
             X = make_float2(p0.x, p1.x);
             Y = make_float2(p0.y, p1.y);
             Z = make_float2(p0.z, p1.z);
-            if (STRETCH) {
-                float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
-                if (v0) g0 = A.tstr[i0];
-                if (v1) g1 = A.tstr[i1];
-                own.gx = make_float2(g0.x, g1.x);
-                own.gy = make_float2(g0.y, g1.y);
-                own.gz = make_float2(g0.z, g1.z);
-            }
             warp_two_boxes(make_float3(p0.x, p0.y, p0.z), v0, make_float3(p1.x, p1.y, p1.z), v1, wbox[warp]);
         }
         if (!mbar_wait_bounded(&full[s], r & 1, A.dev_err, WAIT_LIMIT)) {
@@ -524,24 +527,43 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
         }
 
         const float4* src = stage + (size_t)s * BUF_F4;
-        acc.zero();
-        bool near_tile = false;
+        // Far particle tiles and segment tiles accumulate without the stretching rows and
+        // the target strengths (fewer live registers in their loops); finish_tile adds the
+        // stretching from the tile's sums afterwards.  Near particle tiles accumulate the
+        // stretching pair by pair (it cancels there) with the strengths loaded for them.
+        const int ti0 = t * TGT_TILE + warp * 64 + lane, ti1 = ti0 + 32;
         if (k < sk.np) {
             const int cnt = min(SRC_TILE, A.n_src - k * SRC_TILE);
             const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
-            near_tile = boxes_near(wbox[warp], tlo, thi, A.nc.far2);
-            if (near_tile)
+            if (boxes_near(wbox[warp], tlo, thi, A.nc.far2)) {
+                Own own{zero2(), zero2(), zero2()};
+                if (STRETCH) {
+                    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+                    if (ti0 < A.n_tgt) g0 = A.tstr[ti0];
+                    if (ti1 < A.n_tgt) g1 = A.tstr[ti1];
+                    own.gx = make_float2(g0.x, g1.x);
+                    own.gy = make_float2(g0.y, g1.y);
+                    own.gz = make_float2(g0.z, g1.z);
+                }
+                acc.zero();
                 particle_tile<GRAD, STRETCH, true>(acc, src, cnt, X, Y, Z, A.nc, own);
-            else
-                particle_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.nc, own);
+            } else {
+                Acc<GRAD, false> tf;
+                tf.zero();
+                particle_tile<GRAD, false, false>(tf, src, cnt, X, Y, Z, A.nc, Own{});
+                finish_tile<GRAD, STRETCH>(acc, tf, A.tstr, ti0, ti1, A.n_tgt);
+            }
         } else {
             const int cnt = min(SRC_TILE, A.m_seg - (k - sk.np) * SRC_TILE);
             const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
             const float margin = 1e-3f * tlo.w;
+            Acc<GRAD, false> tf;
+            tf.zero();
             if (A.core_pos && !boxes_near(wbox[warp], tlo, thi, margin * margin))
-                segment_tile<GRAD, STRETCH, true>(acc, src, cnt, X, Y, Z, A.vn);
+                segment_tile<GRAD, false, true>(tf, src, cnt, X, Y, Z, A.vn);
             else
-                segment_tile<GRAD, STRETCH, false>(acc, src, cnt, X, Y, Z, A.vn);
+                segment_tile<GRAD, false, false>(tf, src, cnt, X, Y, Z, A.vn);
+            finish_tile<GRAD, STRETCH>(acc, tf, A.tstr, ti0, ti1, A.n_tgt);
         }
         __syncwarp();
         if (lane == 0) {  // the last warp to finish with stage s refills it with unit i + SWEEP_STAGES
@@ -553,7 +575,6 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
                 if (unit_ahead(t, k, SWEEP_STAGES, kk)) issue(kk, s, r + 1);
             }
         }
-        if (!near_tile) stretch_from_tile<GRAD, STRETCH>(acc, own);
         // fold this tile's sums into the running sums
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
