@@ -38,8 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # hover wake (100,000 particles, 5,120 segments), from one ncu capture of that launch
 # (profiles/sweep_kernel_hover4_100k.md); valid only while the kernel's sources hash to
 # SWEEP_SRC_SHA256, else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = 11_803_136 + 2_560
-SWEEP_SRC_SHA256 = "8d27b9735ae614f14ea988655a83be0df81eeedb1092960b32c3f59d86c14e7e"
+SWEEP_TRAFFIC_BYTES = 11_831_552 + 13_824
+SWEEP_SRC_SHA256 = "75bfd40168c575533e0c8f9dc118a88d2297f89978654a95be638c8db5f43945"
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 
