@@ -251,6 +251,8 @@ def wake_convert(a, b, gamma, gamma_nb, has_nb, trailed, ds_tip, n_tip, n_shed=1
     G = np.zeros((1, 3))
     total = lib.orc_wake_convert(_p(a), _p(b), _p(g), _p(gnb), _ip(hn), _ip(tr), m, float(ds_tip), int(n_tip),
                                  int(n_shed), cap, _p(x), _p(G), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if total == -2:
+        raise ValueError("wake_convert: an edge's particle count is not finite or above 2^30")
     total = int(counts.sum())
     x = np.zeros((max(total, 1), 3))
     G = np.zeros((max(total, 1), 3))

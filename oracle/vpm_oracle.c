@@ -561,7 +561,8 @@ void orc_p2p_adjoint(const double* pos, const double* str, int64_t n_src, const 
  * integer decision in the same precision).  Particles are written edge by edge.
  *
  * Edges a[m][3], b[m][3]; outputs x[cap][3], G[cap][3], counts[m].  Returns the number
- * of particles, or -1 (nothing written) if it exceeds cap.
+ * of particles, -1 (nothing written) if it exceeds cap, or -2 (nothing written) if an
+ * edge's count is not a finite number of at most 2^30 (NaN or runaway edge lengths).
  * ------------------------------------------------------------------------------ */
 static int64_t wake_count(const double* a, const double* b, int trailed, double ds_tip, int n_tip, int n_shed)
 {
@@ -570,6 +571,7 @@ static int64_t wake_count(const double* a, const double* b, int trailed, double 
     const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
     const double len = sqrt(dx * dx + dy * dy + dz * dz);
     const double v = ceil((len / ds_tip) * (double)n_tip);
+    if (!(v <= 1073741824.0)) return -1; /* not a finite count of at most 2^30 particles: refused */
     return v < 1.0 ? 1 : (int64_t)v;  /* a zero-length edge still gets one particle (of zero strength) */
 }
 
@@ -580,6 +582,7 @@ int64_t orc_wake_convert(const double* a, const double* b, const double* gamma, 
     int64_t total = 0;
     for (int64_t i = 0; i < m; ++i) {
         counts[i] = wake_count(&a[3 * i], &b[3 * i], trailed[i], ds_tip, n_tip, n_shed);
+        if (counts[i] < 0) return -2; /* an edge whose count is not finite (NaN or huge lengths) */
         total += counts[i];
     }
     if (total > cap) return -1;

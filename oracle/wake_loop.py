@@ -9,7 +9,10 @@ the near-wake node lines convected by explicit Euler, the particles by one
 low-storage RK3 step (the right-hand side evaluated on the state rounded to FP32,
 the library's precision reading), a new row shed with the trailing-edge panels'
 circulation (Kutta), and the oldest row beyond max_rows converted by Eq. 6-8.  The
-blade geometry is the same synthetic input (rounded to FP32, as the library gets it).
+blade geometry and motion are the same synthetic input (rounded to FP32, as the
+library gets it): hover, or forward flight with the pitch and flapping schedules of
+Eq. 12 form and a free stream, which convects the node lines and the particles and
+enters the loads with each blade's own angular velocity.
 """
 from __future__ import annotations
 
@@ -24,10 +27,14 @@ def _f32(a):
 
 
 class OracleRotorWake:
-    def __init__(self, n_blades=2, n_span=20, n_chord=4, sigma=0.02 * synth.R, dt=synth.DT, max_rows=2, n_tip=2,
-                 n_shed=1, adaptive=True, seg_core=None, nu=synth.NU_AIR, c_v=synth.C_V):
+    def __init__(self, n_blades=2, n_span=20, n_chord=4, sigma=None, dt=None, max_rows=2, n_tip=2,
+                 n_shed=1, adaptive=True, seg_core=None, nu=synth.NU_AIR, c_v=synth.C_V, kin=None):
+        self.kin = synth.Kinematics() if kin is None else kin
         self.nb, self.S, self.nc = n_blades, n_span, n_chord
+        sigma = 0.02 * self.kin.radius if sigma is None else sigma
+        dt = np.deg2rad(5.0) / self.kin.omega if dt is None else dt
         self.sigma, self.dt, self.max_rows = float(sigma), float(dt), int(max_rows)
+        self.u_inf = _f32(self.kin.u_inf)
         self.n_tip = int(n_tip) if adaptive else -int(n_tip)
         self.n_shed = int(n_shed)
         self.core = float(sigma if seg_core is None else seg_core)
@@ -43,9 +50,8 @@ class OracleRotorWake:
         self.history = []
 
     def _geometry(self, t):
-        rings, colloc, normal, vrel, _ = synth.blade_lattice(self.nb, self.S, self.nc, phase=synth.OMEGA * t)
-        te, te_idx = synth.blade_trailing_edge(rings, self.nb, self.S, self.nc)
-        return _f32(rings), _f32(colloc), _f32(normal), _f32(vrel), te, te_idx
+        L = synth.rotor_lattice(self.kin, t, self.nb, self.S, self.nc)
+        return _f32(L.rings), _f32(L.colloc), _f32(L.normal), _f32(L.v_rel), L.te, L.te_idx, L.omega_b
 
     @property
     def rows(self):
@@ -73,7 +79,7 @@ class OracleRotorWake:
         return u
 
     def step(self):
-        rings, colloc, normal, vrel, _, te_idx = self._geometry(self.t)
+        rings, colloc, normal, vrel, _, te_idx, omega_b = self._geometry(self.t)
         wsa, wsb = self._wake_segments()
         u_c = self._velocity(colloc, wsa, wsb)
         A = oracle.aic_build(rings, colloc, normal, self.core)
@@ -82,15 +88,15 @@ class OracleRotorWake:
         bsa, bsb = synth.ring_segments(rings, _f32(gam))
         sa = np.concatenate([bsa, wsa]) if len(wsa) else bsa
         sb = np.concatenate([bsb, wsb]) if len(wsb) else bsb
-        self._loads(rings, normal, gam, te_idx, bsa, bsb, sa, sb)
+        self._loads(rings, normal, gam, te_idx, omega_b, bsa, bsb, sa, sb)
         pts = self.nodes.reshape(-1, 3)
         u_n = self._velocity(pts, sa, sb)
         x_old, G_old = self.x, self.G
-        self.nodes = (pts + self.dt * _f32(u_n)).reshape(self.nodes.shape)
+        self.nodes = (pts + self.dt * (_f32(u_n) + self.u_inf)).reshape(self.nodes.shape)
         if len(x_old):
             vol = np.full(len(x_old), np.float32(self.sigma ** 3))
             self.x, self.G = oracle.step(x_old, G_old, vol, sa, sb, self.sigma, self.dt, nu=self.nu, c_v=self.c_v,
-                                         seg_core=self.core, cast_f32=True)
+                                         seg_core=self.core, u_inf=self.u_inf, cast_f32=True)
         te_next = self._geometry(self.t + self.dt)[4]
         self.nodes = np.concatenate([te_next.reshape(1, self.nb, self.S + 1, 3), self.nodes])
         shed = -gam[te_idx.ravel()].reshape(1, self.nb, self.S)
@@ -100,17 +106,24 @@ class OracleRotorWake:
         self.t += self.dt
         return gam
 
-    def _loads(self, rings, normal, gam, te_idx, bsa, bsb, sa, sb):
+    def _loads(self, rings, normal, gam, te_idx, omega_b, bsa, bsb, sa, sb):
         # the bound segments: every side of every blade ring, except the trailing-edge sides,
         # whose net circulation with the row shed this step is zero (Kutta condition)
         ba, bb = _f32(bsa).copy(), _f32(bsb)
         ba[4 * te_idx.ravel() + 1, 3] = 0.0
         mid = ((ba[:, :3].astype(np.float32) + bb[:, :3].astype(np.float32)) * np.float32(0.5)).astype(np.float64)
         u_mid = _f32(self._velocity(mid, sa, sb))
-        F, M = oracle.blade_loads(ba, bb, u_mid, [0.0, 0.0, synth.OMEGA], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0], rings,
-                                  normal, gam, self.gam_prev, self.dt, self.rho)
-        q = self.rho * np.pi * synth.R ** 2 * (synth.OMEGA * synth.R) ** 2
-        self.history.append((self.t, F[2] / q, -M[2] / (q * synth.R)))
+        F, M = np.zeros(3), np.zeros(3)
+        nr = len(rings) // self.nb
+        for b in range(self.nb):  # each blade with its own angular velocity about the hub
+            r, s = slice(b * nr, (b + 1) * nr), slice(4 * b * nr, 4 * (b + 1) * nr)
+            Fb, Mb = oracle.blade_loads(ba[s], bb[s], u_mid[s], omega_b[b], [0.0, 0.0, 0.0], self.u_inf, rings[r],
+                                        normal[r], gam[r], None if self.gam_prev is None else self.gam_prev[r],
+                                        self.dt, self.rho)
+            F, M = F + Fb, M + Mb
+        Rr, W = self.kin.radius, self.kin.omega
+        q = self.rho * np.pi * Rr ** 2 * (W * Rr) ** 2
+        self.history.append((self.t, F[2] / q, -M[2] / (q * Rr)))
         self.gam_prev = gam.copy()
 
     def _convert_oldest(self):

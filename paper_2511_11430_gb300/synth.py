@@ -158,6 +158,114 @@ def blade_lattice(n_blades, n_span, n_chord, chord=R / 6, root=0.15 * R, pitch_d
     return rings, colloc, normal, vrel, gam
 
 
+@dataclass(frozen=True)
+class Kinematics:
+    """Prescribed motion of a rotor with rigid rectangular blades (Sec. IV.B, Eq. 12 form).
+
+    Blade b sits at azimuth psi_b = Omega t + 2 pi b / N_b (psi = 0 downstream, +x;
+    rotation counter-clockwise about +z seen from above).  Its pitch and flap angles
+    follow first-harmonic schedules in psi_b [deg]:
+        theta(psi) = theta_0 + theta_1c cos psi + theta_1s sin psi   (plus the twist),
+        beta(psi)  = beta_0  + beta_1c  cos psi + beta_1s  sin psi.
+    The flap hinge and the feathering axis pass through the hub (a teetering hub: no
+    hinge offset).  The linear twist adds twist (r/R - twist_ref) to the pitch.  The
+    free stream (mu Omega R, 0, 0) lies in the disk plane (no shaft tilt)."""
+    radius: float = R
+    chord: float = R / 6
+    root: float = 0.15 * R
+    omega: float = OMEGA
+    theta: tuple = (8.0, 0.0, 0.0)
+    beta: tuple = (0.0, 0.0, 0.0)
+    twist: float = 0.0
+    twist_ref: float = 0.75
+    mu: float = 0.0
+
+    @property
+    def u_inf(self):
+        return (self.mu * self.omega * self.radius, 0.0, 0.0)
+
+
+# The AH-1G main rotor of the forward-flight case: geometry of its table of rotor
+# properties (2 blades, R 6.7 m, c 0.7283 m, -10 deg linear twist, root cut-out 0.154 R),
+# the pitch and flapping schedules of Eq. 12, advance ratio 0.19 and tip Mach number
+# 0.65 (speed of sound 340.3 m/s).
+AH1G = Kinematics(radius=6.7, chord=0.7283, root=0.154 * 6.7, omega=0.65 * 340.3 / 6.7, theta=(6.0, 1.7, -5.5),
+                  beta=(0.0, 2.13, -0.15), twist=-10.0, mu=0.19)
+
+
+@dataclass
+class RotorLattice:
+    rings: np.ndarray    # [nr, 4, 3] corners, ordered as blade_lattice's
+    colloc: np.ndarray   # [nr, 3]
+    normal: np.ndarray   # [nr, 3]
+    v_rel: np.ndarray    # [nr, 3] free stream minus the blade's velocity at the control point
+    omega_b: np.ndarray  # [n_blades, 3] angular velocity of each blade (about the hub)
+    te: np.ndarray       # [n_blades, n_span + 1, 3] trailing-edge node lines
+    te_idx: np.ndarray   # [n_blades, n_span] trailing-edge ring indices
+
+
+def _harmonic(c, psi):
+    """(value, d/dpsi) of c0 + c1c cos psi + c1s sin psi, c in degrees, result in radians."""
+    v = c[0] + c[1] * np.cos(psi) + c[2] * np.sin(psi)
+    d = -c[1] * np.sin(psi) + c[2] * np.cos(psi)
+    return np.deg2rad(v), np.deg2rad(d)
+
+
+def rotor_lattice(kin: Kinematics, t, n_blades, n_span, n_chord, hub=(0.0, 0.0, 0.0)) -> RotorLattice:
+    """The vortex-ring lattice of the blades of ``kin`` at time t.
+
+    Each blade is placed by three rotations about axes through the hub: pitch about
+    the blade axis, flap about the hinge axis e_r x e_z, azimuth about e_z.  Its
+    angular velocity is therefore the sum Omega e_z + beta' (e_r x e_z) + theta'
+    e_r,flapped (each rate d/dt of the schedule), and every point x of the blade moves
+    with omega_b x (x - hub).  Panel layout as in blade_lattice (rings a quarter panel
+    chord aft, control points at the three-quarter chord); with twist the rings are
+    not planar and each control point takes the normal of the local chord line.
+    """
+    W, Rr, c = kin.omega, kin.radius, kin.chord
+    hubv = np.asarray(hub, dtype=np.float64)
+    ez = np.array([0.0, 0.0, 1.0])
+    u_inf = np.asarray(kin.u_inf)
+    r_nodes = np.linspace(kin.root, Rr, n_span + 1)
+    xi = np.linspace(0.0, c, n_chord + 1)
+    dxi = c / n_chord
+    rings, colloc, normal, vrel, omegas = [], [], [], [], []
+    for b in range(n_blades):
+        psi = W * t + 2.0 * np.pi * b / n_blades
+        er = np.array([np.cos(psi), np.sin(psi), 0.0])
+        tg = np.array([-np.sin(psi), np.cos(psi), 0.0])  # direction of travel
+        beta, dbeta = _harmonic(kin.beta, psi)
+        theta, dtheta = _harmonic(kin.theta, psi)
+        erf = np.cos(beta) * er + np.sin(beta) * ez  # flapped blade axis
+        nf = np.cos(beta) * ez - np.sin(beta) * er   # flapped disk normal
+        om = W * ez + W * dbeta * np.cross(er, ez) + W * dtheta * erf
+        omegas.append(om)
+
+        def cdir(r):  # leading -> trailing edge at radius r
+            a = theta + np.deg2rad(kin.twist) * (r / Rr - kin.twist_ref)
+            return -tg * np.cos(a) - nf * np.sin(a)
+
+        def pt(r, s):
+            return hubv + r * erf + (s - 0.25 * c) * cdir(r)
+
+        for i in range(n_span):
+            r0, r1 = r_nodes[i], r_nodes[i + 1]
+            rm = 0.5 * (r0 + r1)
+            nrm = np.cross(cdir(rm), erf)
+            nrm /= np.linalg.norm(nrm)
+            for j in range(n_chord):
+                s0, s1 = xi[j] + 0.25 * dxi, xi[j + 1] + 0.25 * dxi
+                rings.append([pt(r0, s0), pt(r0, s1), pt(r1, s1), pt(r1, s0)])
+                y = pt(rm, xi[j] + 0.75 * dxi)
+                colloc.append(y)
+                normal.append(nrm)
+                vrel.append(u_inf - np.cross(om, y - hubv))
+    rings = np.asarray(rings)
+    te, te_idx = blade_trailing_edge(rings, n_blades, n_span, n_chord)
+    return RotorLattice(rings=rings, colloc=np.asarray(colloc), normal=np.asarray(normal), v_rel=np.asarray(vrel),
+                        omega_b=np.asarray(omegas), te=te, te_idx=te_idx)
+
+
 def ring_segments(rings, gam):
     """The four straight segments c0->c1->c2->c3->c0 of every ring, carrying its circulation."""
     nr = rings.shape[0]

@@ -1,13 +1,15 @@
-"""A hover rotor shedding its near wake and converting it into vortex particles
-(Sec. II.A-C), driven through the C ABI.
+"""A rotor shedding its near wake and converting it into vortex particles (Sec. II.A-C),
+in hover or in forward flight with prescribed pitch and flapping (Eq. 12 form), driven
+through the C ABI.
 
 Each step of ``RotorWake.step``:
-  1. the blade lattice at time t (prescribed rotation, synthetic geometry);
+  1. the blade lattice at time t (prescribed motion ``synth.Kinematics``: rotation,
+     collective and cyclic pitch, flapping, free stream; synthetic geometry);
   2. the velocity the particles and the near-wake rows induce at the control points,
      the AIC build and solve for the blade circulations (Neumann condition);
-  3. the near-wake node lines convected by the local velocity (explicit Euler) and the
-     particles advanced by one low-storage RK3 step, both with the blade rings and the
-     wake rings frozen as Vatistas-cored segments;
+  3. the near-wake node lines convected by the local velocity plus the free stream
+     (explicit Euler) and the particles advanced by one low-storage RK3 step, both with
+     the blade rings and the wake rings frozen as Vatistas-cored segments;
   4. a new wake row shed between the trailing edge at t + dt and the convected
      trailing-edge line of t, carrying the trailing-edge panels' circulation (Kutta
      condition; upstream rows keep their strength);
@@ -15,9 +17,12 @@ Each step of ``RotorWake.step``:
      counts, or the conventional uniform count with ``adaptive=False``) and appended;
   6. the blade loads at time t: Kutta-Joukowski on every bound segment (the blade rings'
      sides but the trailing-edge ones, whose net circulation with the row shed at this
-     step vanishes) with the velocity relative to the blade at its midpoint, and the
-     unsteady Bernoulli term of every panel; thrust and torque coefficients C_T = T / (rho pi R^2 (Omega R)^2),
-     C_Q = Q / (rho pi R^3 (Omega R)^2) are kept in ``history``.
+     step vanishes) with the velocity relative to the blade at its midpoint (free stream
+     minus the blade's own motion omega_b x r plus the induced velocity; one call per
+     blade, each with its angular velocity), and the unsteady Bernoulli term of every
+     panel; thrust and torque coefficients C_T = T / (rho pi R^2 (Omega R)^2),
+     C_Q = Q / (rho pi R^3 (Omega R)^2) (thrust along the shaft +z, torque about it) are
+     kept in ``history``.
 
 Rows use the ring convention of vpm_wake_convert_row (U[p] -> U[p+1] -> D[p+1] ->
 D[p]); the blade's trailing-edge segments run root -> tip, so a row shed behind a panel
@@ -39,16 +44,23 @@ def _dev(a, dtype, device):
 
 
 class RotorWake:
-    def __init__(self, n_blades=2, n_span=20, n_chord=4, sigma=0.02 * synth.R, dt=synth.DT, max_rows=2, n_tip=2,
+    def __init__(self, n_blades=2, n_span=20, n_chord=4, sigma=None, dt=None, max_rows=2, n_tip=2,
                  n_shed=1, adaptive=True, compensated=True, seg_core=None, nu=synth.NU_AIR, c_v=synth.C_V,
-                 device="cuda"):
+                 kin=None, device="cuda"):
+        """sigma defaults to 0.02 R, dt to 5 deg of azimuth; kin to the hover rotor
+        (synth.Kinematics(): 8 deg collective, no flapping, no free stream)."""
+        self.kin = synth.Kinematics() if kin is None else kin
         self.nb, self.S, self.nc = n_blades, n_span, n_chord
+        sigma = 0.02 * self.kin.radius if sigma is None else sigma
+        dt = np.deg2rad(5.0) / self.kin.omega if dt is None else dt
         self.sigma, self.dt, self.max_rows = float(sigma), float(dt), int(max_rows)
+        self.u_inf = tuple(float(np.float32(v)) for v in self.kin.u_inf)  # the library's FP32 free stream
         self.n_tip = int(n_tip) if adaptive else -int(n_tip)
         self.n_shed = int(n_shed)
         self.core = float(sigma if seg_core is None else seg_core)
         self.dev = torch.device(device)
-        self.prm = api.Params(sigma=self.sigma, nu=nu, c_v=c_v, seg_core=self.core, compensated=compensated)
+        self.prm = api.Params(sigma=self.sigma, nu=nu, c_v=c_v, seg_core=self.core, u_inf=self.u_inf,
+                              compensated=compensated)
         self.compensated = compensated
         self.t = 0.0
         self.steps = 0
@@ -56,7 +68,7 @@ class RotorWake:
         self.x = torch.zeros((3, 0), dtype=torch.float64, device=self.dev)
         self.G = torch.zeros((3, 0), dtype=torch.float64, device=self.dev)
         self.vol = torch.zeros((0,), dtype=torch.float32, device=self.dev)
-        te, _ = self._geometry_host(0.0)[4:6]
+        te = self._geometry_host(0.0)[4]
         self.nodes = _dev(te, torch.float64, self.dev).reshape(1, self.nb, self.S + 1, 3).contiguous()
         self.gammas = torch.zeros((0, self.nb, self.S), dtype=torch.float64, device=self.dev)
         self.converted = 0  # particles created so far
@@ -64,14 +76,13 @@ class RotorWake:
         self.gam_prev = None
         self.history = []  # (t, C_T, C_Q) per step
 
-    # ---- geometry (prescribed rotation: synthetic input) -------------------------
+    # ---- geometry (prescribed motion: synthetic input) ---------------------------
     def _geometry_host(self, t):
-        rings, colloc, normal, vrel, _ = synth.blade_lattice(self.nb, self.S, self.nc, phase=synth.OMEGA * t)
-        te, te_idx = synth.blade_trailing_edge(rings, self.nb, self.S, self.nc)
-        r4 = np.zeros(rings.shape[:2] + (4,))
-        r4[..., :3] = rings
+        L = synth.rotor_lattice(self.kin, t, self.nb, self.S, self.nc)
+        r4 = np.zeros(L.rings.shape[:2] + (4,))
+        r4[..., :3] = L.rings
         pad = lambda a: np.concatenate([a, np.zeros((a.shape[0], 1))], 1)
-        return r4, pad(colloc), pad(normal), pad(vrel), te, te_idx
+        return r4, pad(L.colloc), pad(L.normal), pad(L.v_rel), L.te, L.te_idx, L.omega_b
 
     @property
     def rows(self) -> int:
@@ -103,7 +114,7 @@ class RotorWake:
 
     def step(self):
         lib = _lib.load()
-        r4, colloc, normal, vrel, _, te_idx = self._geometry_host(self.t)
+        r4, colloc, normal, vrel, _, te_idx, omega_b = self._geometry_host(self.t)
         rings = _dev(r4, torch.float32, self.dev)
         colloc, normal, vrel = (_dev(a, torch.float32, self.dev) for a in (colloc, normal, vrel))
         pos = strn = None
@@ -121,15 +132,15 @@ class RotorWake:
                                     api._stream()))
         seg_a = torch.cat([bsa, wsa]).contiguous()
         seg_b = torch.cat([bsb, wsb]).contiguous()
-        self._loads(lib, rings, normal, gam_b, te_idx, bsa, bsb, seg_a, seg_b, pos, strn)
+        self._loads(lib, rings, normal, gam_b, te_idx, omega_b, bsa, bsb, seg_a, seg_b, pos, strn)
         # 3. convect the node lines, advance the particles
         pts = self.nodes.reshape(-1, 3)
         npts = pts.shape[0]
         tgt = torch.empty((npts, 4), dtype=torch.float32, device=self.dev)
         check(lib.vpm_points_pack(api._void(pts), npts, api._void(tgt), api._stream()))
         u_n = self._velocity(tgt, seg_a, seg_b, pos, strn).contiguous()
-        check(lib.vpm_points_advect(api._void(pts), api._void(u_n), npts, ctypes.c_double(self.dt), None,
-                                    api._stream()))
+        check(lib.vpm_points_advect(api._void(pts), api._void(u_n), npts, ctypes.c_double(self.dt),
+                                    (ctypes.c_float * 3)(*self.u_inf), api._stream()))
         if self.n > 0:
             api.step(self.x, self.G, self.vol, seg_a, seg_b, self.prm, self.dt, ws=self.ws)
         # 4. shed a row behind the trailing edge of t + dt
@@ -145,7 +156,7 @@ class RotorWake:
         self.steps += 1
         return gam_b
 
-    def _loads(self, lib, rings, normal, gam_b, te_idx, bsa, bsb, seg_a, seg_b, pos, strn):
+    def _loads(self, lib, rings, normal, gam_b, te_idx, omega_b, bsa, bsb, seg_a, seg_b, pos, strn):
         # the bound segments: every side of every blade ring, except the trailing-edge sides,
         # whose net circulation with the row shed this step is zero (Kutta condition)
         ba = bsa.clone()
@@ -154,18 +165,26 @@ class RotorWake:
         m = ba.shape[0]
         mid = torch.empty((m, 4), dtype=torch.float32, device=self.dev)
         check(lib.vpm_segment_midpoints(api._void(ba), api._void(bb), m, api._void(mid), api._stream()))
-        u_mid = self._velocity(mid, seg_a, seg_b, pos, strn).contiguous()
-        out = torch.empty(6, dtype=torch.float64, device=self.dev)
+        u_mid = self._velocity(mid, seg_a, seg_b, pos, strn)
+        # one call per blade: each blade moves with its own angular velocity about the hub
+        nr = rings.shape[0] // self.nb
+        ms = 4 * nr
+        out = torch.empty((self.nb, 6), dtype=torch.float64, device=self.dev)
         D3 = ctypes.c_double * 3
-        n = rings.shape[0]
-        w = self.ws.get(api.workspace_size(_lib.VPM_OP_LOADS, 0, n, m, 0))
-        check(lib.vpm_blade_loads(api._void(ba), api._void(bb), m, api._void(u_mid), D3(0.0, 0.0, synth.OMEGA),
-                                  D3(0.0, 0.0, 0.0), D3(0.0, 0.0, 0.0), api._void(rings), api._void(normal),
-                                  api._void(gam_b), api._void(self.gam_prev), n, ctypes.c_double(self.dt),
-                                  ctypes.c_double(self.rho), api._void(out), api._void(w), w.numel(), api._stream()))
-        F = out.cpu().numpy()
-        q = self.rho * np.pi * synth.R ** 2 * (synth.OMEGA * synth.R) ** 2
-        self.history.append((self.t, F[2] / q, -F[5] / (q * synth.R)))
+        w = self.ws.get(api.workspace_size(_lib.VPM_OP_LOADS, 0, nr, ms, 0))
+        for b in range(self.nb):
+            r0, s0 = b * nr, b * ms
+            um = u_mid[:, s0:s0 + ms].contiguous()
+            gp = None if self.gam_prev is None else self.gam_prev[r0:r0 + nr]
+            check(lib.vpm_blade_loads(api._void(ba[s0:]), api._void(bb[s0:]), ms, api._void(um), D3(*omega_b[b]),
+                                      D3(0.0, 0.0, 0.0), D3(*self.u_inf), api._void(rings[r0:]),
+                                      api._void(normal[r0:]), api._void(gam_b[r0:]), api._void(gp), nr,
+                                      ctypes.c_double(self.dt), ctypes.c_double(self.rho), api._void(out[b]),
+                                      api._void(w), w.numel(), api._stream()))
+        F = out.sum(0).cpu().numpy()
+        Rr, W = self.kin.radius, self.kin.omega
+        q = self.rho * np.pi * Rr ** 2 * (W * Rr) ** 2
+        self.history.append((self.t, F[2] / q, -F[5] / (q * Rr)))
         self.gam_prev = gam_b.clone()
 
     def _convert_oldest(self):

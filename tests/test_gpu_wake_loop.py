@@ -1,5 +1,6 @@
 """The near-wake time loop (shedding, convection, conversion, loads: Sec. II.A-C) run
-through the library against the FP64 oracle loop on a small rotor: blade circulations
+through the library against the FP64 oracle loop on a small rotor, in hover and in the
+forward flight of the AH-1G case (Eq. 12 schedules, free stream): blade circulations
 and thrust/torque coefficients each step, the particle count after conversions (an
 integer decided in FP64 on both sides), and the converted and convected particles."""
 import numpy as np
@@ -22,9 +23,13 @@ def wake_mod():
     return wake
 
 
-@pytest.mark.parametrize("adaptive", [True, False])
-def test_rotor_wake_loop_matches_oracle(wake_mod, adaptive):
+@pytest.mark.parametrize("adaptive, flight", [(True, "hover"), (False, "hover"), (True, "ah1g"), (False, "ah1g")])
+def test_rotor_wake_loop_matches_oracle(wake_mod, adaptive, flight):
     kw = dict(n_blades=2, n_span=12, n_chord=3, max_rows=2, n_tip=3, n_shed=1, adaptive=adaptive)
+    if flight == "ah1g":  # forward flight: Eq. 12 pitch and flapping, advance ratio 0.19, 10 deg steps
+        from paper_2511_11430_gb300 import synth
+
+        kw.update(kin=synth.AH1G, dt=np.deg2rad(10.0) / synth.AH1G.omega)
     g = wake_mod.RotorWake(**kw)
     o = OracleRotorWake(**kw)
     for _ in range(6):
