@@ -70,6 +70,7 @@ typedef enum vpm_status {
 #define VPM_OP_WAKE_CONVERT 7
 #define VPM_OP_WAKE_ROW 8
 #define VPM_OP_LOADS 9
+#define VPM_OP_TREE 10
 
 /* Largest particle / target / segment count accepted (int32 indexing). */
 #define VPM_MAX_ITEMS (1 << 30)
@@ -106,6 +107,7 @@ vpm_status vpm_device_error(int* code);
  *   VPM_OP_BACKWARD:  n_src particles, n_tgt targets
  *   VPM_OP_WAKE_CONVERT: n_src edges;  VPM_OP_WAKE_ROW: n_src panels of the row
  *   VPM_OP_LOADS:     m_seg bound segments, n_tgt panels
+ *   VPM_OP_TREE:      n_src particles (vpm_tree_induce)
  * `flags` as passed to the operation.  Host-only; does not launch. */
 vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_seg, int flags, size_t* bytes);
 
@@ -122,6 +124,23 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
 vpm_status vpm_induce(const float* src_pos_d, const float* src_str_d, int64_t n_src, const float* tgt_d,
                       int64_t n_tgt, float sigma, int flags, float* u_d, float* grad_u_d, void* ws_d,
                       size_t ws_bytes, void* stream);
+
+/* ---- Sec. II.B: the fast summation, as a treecode --------------------------
+ * u and grad u at every particle from all the others, as vpm_induce with the
+ * particles as targets, in O(n log n) work.  Sec. II.B evaluates these sums with a
+ * Cartesian fast multipole method; this is its treecode form: far clusters enter by
+ * the Cartesian Taylor expansion of the point-vortex potential sum_j Gamma_j / |x - x_j|
+ * to order `order` (moments up to |k| = order), near ones by the direct sum.
+ * Clusters are runs of the particles sorted along a Morton curve, halved down to
+ * leaves of at most 64; a cluster is far from a target leaf when the sum of their
+ * radii is below theta times the distance of their centres and every pair is at
+ * least 7 sigma apart (where the Gaussian blob equals the point vortex in FP32).
+ * theta = 0 opens every cluster: the direct sum (plain FP32 accumulation).  The
+ * truncation error falls as theta^(order + 1).
+ *   pos_d, str_d [n][4] particles; u_d [3][n]; grad_u_d [9][n] or NULL;
+ *   0 <= theta <= 1; order in {2, 3, 4}.  Workspace: VPM_OP_TREE (n_src = n). */
+vpm_status vpm_tree_induce(const float* pos_d, const float* str_d, int64_t n, float sigma, float theta, int order,
+                           float* u_d, float* grad_u_d, void* ws_d, size_t ws_bytes, void* stream);
 
 /* ---- Sec. II.A: straight vortex segments with a Vatistas core ------------
  * The finite-segment Biot-Savart law with |r1 x r2|^2 replaced by

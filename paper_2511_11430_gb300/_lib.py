@@ -33,6 +33,7 @@ VPM_OP_BACKWARD = 6
 VPM_OP_WAKE_CONVERT = 7
 VPM_OP_WAKE_ROW = 8
 VPM_OP_LOADS = 9
+VPM_OP_TREE = 10
 
 VPM_TRACE_ALL = 0
 VPM_TRACE_SWEEP = 1
@@ -82,6 +83,7 @@ SIGNATURES = {
     "vpm_workspace_size": (_INT, [_INT, _I64, _I64, _I64, _INT, ctypes.POINTER(_SZ)]),
     "vpm_induce": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P, _SZ, _P]),
     "vpm_segments_induce": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _INT, _P, _P, _P, _SZ, _P]),
+    "vpm_tree_induce": (_INT, [_P, _P, _I64, _F, _F, _INT, _P, _P, _P, _SZ, _P]),
     "vpm_rhs": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _P, _P, _P, _P, _SZ, _P]),
     "vpm_pack_state": (_INT, [_P, _P, _P, _I64, _P, _P, _P]),
     "vpm_step": (_INT, [_P, _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _D, _P, _SZ, _P]),

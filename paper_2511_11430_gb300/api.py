@@ -97,6 +97,22 @@ def induce(src_pos, src_str, tgt, sigma: float, compensated: bool = True, grad: 
     return (u, g) if grad else u
 
 
+def tree_induce(pos, strength, sigma: float, theta: float = 0.5, order: int = 4, grad: bool = True, ws=None):
+    """Velocity (and gradient) at every particle from all the others by the treecode
+    (vpm_tree_induce): far clusters by their Taylor expansion of order ``order``,
+    near ones by the direct sum; theta = 0 gives the direct sum."""
+    _need(pos, "pos", torch.float32, (4,))
+    _need(strength, "strength", torch.float32, (4,))
+    n = pos.shape[0]
+    dev = pos.device
+    u = torch.empty((3, n), dtype=torch.float32, device=dev)
+    g = torch.empty((9, n), dtype=torch.float32, device=dev) if grad else None
+    w = _ws(ws, workspace_size(_lib.VPM_OP_TREE, n), dev)
+    check(_lib.load().vpm_tree_induce(_void(pos), _void(strength), n, float(sigma), float(theta), int(order),
+                                      _void(u), _void(g), _void(w), w.numel(), _stream()))
+    return (u, g) if grad else u
+
+
 def segments_induce(seg_a, seg_b, tgt, core: float, vatistas_n: int = 2, compensated: bool = True,
                     grad: bool = True, ws=None):
     """Velocity (and gradient) at ``tgt`` induced by Vatistas-cored straight segments (Sec. II.A)."""

@@ -168,6 +168,11 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
         REQUIRE(n_src >= 1, "a wake row needs at least one panel");
         *bytes = wake_workspace(3 * n_src + 1, true);
         break;
+    case VPM_OP_TREE: {
+        const cudaError_t e = tree_workspace(n_src, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "vpm_workspace_size(VPM_OP_TREE): sort scratch query");
+        break;
+    }
     default:
         return fail(VPM_ERR_INVALID_ARG, "unknown op %d", op);
     }
@@ -209,6 +214,29 @@ vpm_status vpm_induce(const float* src_pos_d, const float* src_str_d, int64_t n_
     cudaError_t e = run_sweep(p, static_cast<char*>(ws_d), tgt_d, src_pos_d, src_str_d, nullptr, nullptr, sigma, 0.f,
                               2, o, st);
     return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_induce");
+}
+
+vpm_status vpm_tree_induce(const float* pos_d, const float* str_d, int64_t n, float sigma, float theta, int order,
+                           float* u_d, float* grad_u_d, void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    REQUIRE(sigma > 0.f && isfinite(sigma), "sigma must be finite and > 0 (got %g)", (double)sigma);
+    REQUIRE(theta >= 0.f && theta <= 1.f, "theta must lie in [0, 1] (got %g)", (double)theta);
+    REQUIRE(order >= 2 && order <= 4, "order must be 2, 3 or 4 (got %d)", order);
+    if (n == 0) return ok();
+    REQUIRE(pos_d && str_d && aligned16(pos_d) && aligned16(str_d), "pos/str must be 16-byte aligned device pointers");
+    REQUIRE(u_d && aligned4(u_d), "u must be a 4-byte aligned device pointer");
+    REQUIRE(!grad_u_d || aligned4(grad_u_d), "grad_u misaligned");
+    size_t need = 0;
+    const cudaError_t eq = tree_workspace(n, &need);
+    if (eq != cudaSuccess) return cuda_fail(eq, "vpm_tree_induce: sort scratch query");
+    if (!ws_d || ws_bytes < need || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", need, ws_bytes);
+    if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
+    cudaError_t e = run_tree_induce(pos_d, str_d, n, sigma, theta, order, u_d, grad_u_d, static_cast<char*>(ws_d),
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_tree_induce");
 }
 
 vpm_status vpm_segments_induce(const float* seg_a_d, const float* seg_b_d, int64_t m, const float* tgt_d,

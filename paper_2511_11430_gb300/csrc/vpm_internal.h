@@ -114,6 +114,9 @@ vpm_status run_wake_convert(const double* a, const double* b, const double* gamm
 vpm_status run_wake_convert_row(const double* U, const double* D, const double* gamma, long long S, double ds_tip,
                                 int n_tip, int n_shed, double* x, double* G, long long ld, long long* n_out, char* ws,
                                 cudaStream_t st, const char** msg);
+cudaError_t tree_workspace(long long n, size_t* bytes);
+cudaError_t run_tree_induce(const float* pos, const float* str, long long n, float sigma, float theta, int order,
+                            float* u, float* grad_u, char* ws, cudaStream_t st);
 size_t aic_workspace(int n);
 vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, double tol, int max_iter, int* iters,
                          double* berr, char* ws, cudaStream_t st, const char** msg);

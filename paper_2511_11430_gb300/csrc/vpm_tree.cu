@@ -1,0 +1,694 @@
+// Treecode evaluation of the particle velocity and velocity gradient (Eq. 2-4) of n
+// particles on themselves, in O(n log n) work: the fast summation that Sec. II.B
+// calls for in place of the direct sum (the paper uses a Cartesian FMM; this is
+// the Cartesian Taylor treecode, the FMM without local expansions).
+//
+// Tree.  The particles are sorted along a Morton (Z-order) curve of their positions
+// (21 bits per axis) and the sorted array is halved recursively: node (l, k) of
+// level l holds the particles [floor(k n / 2^l), floor((k + 1) n / 2^l)), so every
+// node is one contiguous run of the sorted array, node i has children 2i + 1 and
+// 2i + 2, and the leaves (level D) hold 33 to 64 particles.  A node carries the
+// centre c of its bounding box, the radius r of a sphere about c that holds its
+// particles, and its scaled moments M_k = sum_j Gamma_j (x_j - c)^k / k! for the
+// multi-indices |k| <= p (k! = k1! k2! k3!, d^k = d1^k1 d2^k2 d3^k3).
+//
+// Expansion.  Beyond 7 sigma the blob kernel is the point-vortex kernel to FP32
+// precision, and u = curl Psi / (4 pi) with Psi(x) = sum_j Gamma_j / |x - x_j|.
+// With R = x - c and d_j = x_j - c, Taylor expansion in d_j gives
+//   Psi^l(x) = sum_k M_k^l b_k(R),  b_k = (-1)^|k| d^k(1/|R|)/dR^k,  |k| <= p,
+// and d b_k / dx_j = -b_{k + e_j}, so
+//   4 pi u_a = -eps_ajl sum_k M_k^l b_{k + e_j},   4 pi (grad u)_ab = eps_ajl sum_k M_k^l b_{k + e_j + e_b}.
+// The b_k follow from b_0 = 1/|R| by the recurrence of the derivatives of 1/|R|,
+//   |k| |R|^2 b_k = (2|k| - 1) sum_i k_i R_i b_{k - e_i} - (|k| - 1) sum_i k_i (k_i - 1) b_{k - 2 e_i},
+// (the Taylor-coefficient recurrence of 1/|x - y| with the factorials moved into
+// b_k).  Moving a node's moments from a child centre c' to the parent centre c is
+// the product of two truncated series: M_k = sum_{i <= k} M'_i s^(k - i) / (k - i)!,
+// s = c' - c.
+//
+// Traversal.  One warp per target leaf (its targets two per thread, in the lanes of
+// packed float2 registers, as in the direct sweep) walks the tree depth first from
+// the root with its stack spread over the warp's lanes.  A node is far from the
+// leaf when r_node + r_leaf < theta |c_node - c_leaf| and every pair is at least
+// 7 sigma apart; a far node with at least m2p_min particles enters by its expansion,
+// a smaller far node by the point-vortex sum over its particles (cheaper than the
+// expansion, and exact); a leaf that is not far enters by the direct sum with the
+// regularised kernel; any other node is opened.  theta = 0 opens every node, which
+// gives the direct sum.
+#include <math.h>
+
+#include <algorithm>
+
+#include <cub/device/device_radix_sort.cuh>
+
+#include "vpm_common.cuh"
+#include "vpm_internal.h"
+#include "vpm_kernel.cuh"
+
+namespace vpm {
+namespace {
+
+constexpr int TREE_LEAF = 64;        // particles per leaf at most: one warp's targets
+constexpr int TREE_WARPS = 8;        // warps per traversal block
+constexpr int TREE_MAX_P = 4;        // highest expansion order
+constexpr int BOUNDS_BLOCKS = 1024;  // partial boxes of the bounding-box pass
+constexpr int MORTON_BITS = 21;      // per axis
+
+__host__ __device__ constexpr int nterms(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// Position of the multi-index (a, b, c) in the graded order: by |k|, then a
+// descending, then b descending.
+__host__ __device__ constexpr int midx(int a, int b, int c)
+{
+    return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+
+int tree_depth(long long n)
+{
+    int D = 0;
+    while (((n + (1LL << D) - 1) >> D) > TREE_LEAF) ++D;
+    return D;
+}
+
+// Smallest particle count of a far node that enters by its expansion: below it the
+// point-vortex sum over the node's particles costs less (about 16 lane operations
+// per pair and target against roughly 570, 1,000 and 1,700 for p = 2, 3, 4).
+int m2p_min(int p) { return p == 2 ? 40 : p == 3 ? 64 : 112; }
+
+struct TreeWs {
+    size_t part, keys0, keys1, idx0, idx1, cub, cub_bytes, psrc, geo, box, mom, counter, bytes;
+    int D;
+    long long nodes;
+};
+
+// The layout of the workspace; fails only if the sort's scratch query does.
+cudaError_t tree_layout(long long n, TreeWs& w)
+{
+    Carve cv;
+    w = TreeWs{};
+    w.D = tree_depth(n);
+    w.nodes = (2LL << w.D) - 1;
+    w.part = cv.take((size_t)(BOUNDS_BLOCKS + 1) * 6 * sizeof(float));
+    w.keys0 = cv.take((size_t)n * 8);
+    w.keys1 = cv.take((size_t)n * 8);
+    w.idx0 = cv.take((size_t)n * 4);
+    w.idx1 = cv.take((size_t)n * 4);
+    size_t cb = 0;
+    const cudaError_t e = cub::DeviceRadixSort::SortPairs(
+        nullptr, cb, (const unsigned long long*)nullptr, (unsigned long long*)nullptr, (const int*)nullptr,
+        (int*)nullptr, (int)n, 0, 3 * MORTON_BITS);
+    if (e != cudaSuccess) return e;
+    w.cub_bytes = cb;
+    w.cub = cv.take(cb);
+    w.psrc = cv.take((size_t)n * P_F4 * 16);
+    w.geo = cv.take((size_t)w.nodes * 16);
+    w.box = cv.take((size_t)w.nodes * 32);
+    w.mom = cv.take((size_t)w.nodes * 3 * nterms(TREE_MAX_P) * sizeof(float));
+    w.counter = cv.take(sizeof(int));
+    w.bytes = cv.off;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Build: bounding box, Morton keys, sort, packed sorted sources.
+// ---------------------------------------------------------------------------
+__global__ void tree_bounds_kernel(const float4* __restrict__ pos, int n, float* __restrict__ part)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = pos[i];
+        lo[0] = fminf(lo[0], p.x), lo[1] = fminf(lo[1], p.y), lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x), hi[1] = fmaxf(hi[1], p.y), hi[2] = fmaxf(hi[2], p.z);
+    }
+    __shared__ float red[6][32];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) red[c][w] = lo[c], red[3 + c][w] = hi[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float v = red[threadIdx.x][0];
+        for (int k = 1; k < nw; ++k) v = threadIdx.x < 3 ? fminf(v, red[threadIdx.x][k]) : fmaxf(v, red[threadIdx.x][k]);
+        part[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
+// One block: the partial boxes into one, written after them at part[6 nparts].
+__global__ void tree_box_kernel(float* __restrict__ part, int nparts)
+{
+    __shared__ float red[6][32];
+    float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = c < 3 ? fminf(v[c], part[k * 6 + c]) : fmaxf(v[c], part[k * 6 + c]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float t = __shfl_xor_sync(0xffffffffu, v[c], o);
+            v[c] = c < 3 ? fminf(v[c], t) : fmaxf(v[c], t);
+        }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 6; ++c) red[c][w] = v[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float r = red[threadIdx.x][0];
+        for (int k = 1; k < nw; ++k) r = threadIdx.x < 3 ? fminf(r, red[threadIdx.x][k]) : fmaxf(r, red[threadIdx.x][k]);
+        part[nparts * 6 + threadIdx.x] = r;
+    }
+}
+
+// Spreads the low 21 bits of v to every third bit of a 64-bit word.
+__device__ __forceinline__ unsigned long long spread3(unsigned int v)
+{
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+__global__ void tree_keys_kernel(const float4* __restrict__ pos, int n, const float* __restrict__ boxg,
+                                 unsigned long long* __restrict__ keys, int* __restrict__ idx)
+{
+    __shared__ float box[6];
+    if (threadIdx.x < 6) box[threadIdx.x] = boxg[threadIdx.x];
+    __syncthreads();
+    const float ext = fmaxf(fmaxf(box[3] - box[0], box[4] - box[1]), box[5] - box[2]);
+    const float top = (float)((1u << MORTON_BITS) - 1);
+    const float scale = ext > 0.f ? top / ext : 0.f;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = pos[i];
+    const float q[3] = {(p.x - box[0]) * scale, (p.y - box[1]) * scale, (p.z - box[2]) * scale};
+    unsigned int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = (unsigned int)fminf(fmaxf(q[a], 0.f), top);  // NaN -> 0
+    keys[i] = (spread3(c[0]) << 2) | (spread3(c[1]) << 1) | spread3(c[2]);
+    idx[i] = i;
+}
+
+// Sorted position k <- particle idx[k], packed like the direct sweep's sources:
+//   (-x,-x,-y,-y) (-z,-z,gx,gx) (gy,gy,gz,gz) (-gx,-gx,-gy,-gy) (-gz,-gz,0,0).
+__global__ void tree_gather_kernel(const float4* __restrict__ pos, const float4* __restrict__ str,
+                                   const int* __restrict__ idx, int n, float4* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int j = idx[k];
+    const float4 p = pos[j], g = str[j];
+    float4* o = out + (size_t)k * P_F4;
+    o[0] = make_float4(-p.x, -p.x, -p.y, -p.y);
+    o[1] = make_float4(-p.z, -p.z, g.x, g.x);
+    o[2] = make_float4(g.y, g.y, g.z, g.z);
+    o[3] = make_float4(-g.x, -g.x, -g.y, -g.y);
+    o[4] = make_float4(-g.z, -g.z, 0.f, 0.f);
+}
+
+__device__ __forceinline__ long long run_begin(long long k, long long n, int level) { return (k * n) >> level; }
+
+// ---------------------------------------------------------------------------
+// Leaves: box, radius and moments of every leaf, one warp per leaf.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void tree_leaf_kernel(const float4* __restrict__ psrc, long long n, int D, float4* __restrict__ geo,
+                                 float4* __restrict__ box, float* __restrict__ mom)
+{
+    constexpr int NM = nterms(P);
+    const long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (leaf >= (1LL << D)) return;
+    const long long s = run_begin(leaf, n, D), e = run_begin(leaf + 1, n, D);
+    float px[2], py[2], pz[2], gx[2], gy[2], gz[2];
+    bool ok[2];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long i = s + lane + 32 * h;
+        ok[h] = i < e;
+        px[h] = py[h] = pz[h] = gx[h] = gy[h] = gz[h] = 0.f;
+        if (ok[h]) {
+            const float4* q = psrc + i * P_F4;
+            const float4 q0 = q[0], q1 = q[1], q2 = q[2];
+            px[h] = -q0.x, py[h] = -q0.z, pz[h] = -q1.x;
+            gx[h] = q1.z, gy[h] = q2.x, gz[h] = q2.z;
+            lo[0] = fminf(lo[0], px[h]), lo[1] = fminf(lo[1], py[h]), lo[2] = fminf(lo[2], pz[h]);
+            hi[0] = fmaxf(hi[0], px[h]), hi[1] = fmaxf(hi[1], py[h]), hi[2] = fmaxf(hi[2], pz[h]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    const float cx = 0.5f * (lo[0] + hi[0]), cy = 0.5f * (lo[1] + hi[1]), cz = 0.5f * (lo[2] + hi[2]);
+    float r2 = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (ok[h]) {
+            const float dx = px[h] - cx, dy = py[h] - cy, dz = pz[h] - cz;
+            r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    const long long id = (1LL << D) - 1 + leaf;
+    if (lane == 0) {
+        // the radius is rounded up by a relative 1e-6 so that it bounds the FP32 distances
+        geo[id] = make_float4(cx, cy, cz, sqrtf(r2) * 1.000001f);
+        box[2 * id] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        box[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        float acc[NM];
+#pragma unroll
+        for (int q = 0; q < NM; ++q) acc[q] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!ok[h]) continue;
+            const float g = l == 0 ? gx[h] : (l == 1 ? gy[h] : gz[h]);
+            float tx[P + 1], ty[P + 1], tz[P + 1];  // d^a / a! per axis
+            tx[0] = ty[0] = tz[0] = 1.f;
+#pragma unroll
+            for (int a = 1; a <= P; ++a) {
+                tx[a] = tx[a - 1] * (px[h] - cx) * (1.f / a);
+                ty[a] = ty[a - 1] * (py[h] - cy) * (1.f / a);
+                tz[a] = tz[a - 1] * (pz[h] - cz) * (1.f / a);
+            }
+#pragma unroll
+            for (int m = 0; m <= P; ++m)
+#pragma unroll
+                for (int a = m; a >= 0; --a)
+#pragma unroll
+                    for (int b = m - a; b >= 0; --b) {
+                        const int c = m - a - b;
+                        acc[midx(a, b, c)] = fmaf(g, tx[a] * ty[b] * tz[c], acc[midx(a, b, c)]);
+                    }
+        }
+#pragma unroll
+        for (int q = 0; q < NM; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (lane == (q & 31)) mom[(size_t)id * 3 * NM + l * NM + q] = acc[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Upward pass: one level, one thread per (node, component).
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void tree_up_kernel(int level, float4* __restrict__ geo, float4* __restrict__ box, float* __restrict__ mom)
+{
+    constexpr int NM = nterms(P);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * (1LL << level)) return;
+    const long long k = t / 3;
+    const int l = (int)(t - 3 * k);
+    const long long id = (1LL << level) - 1 + k;
+    const long long ch[2] = {2 * id + 1, 2 * id + 2};
+    const float4 l0 = box[2 * ch[0]], h0 = box[2 * ch[0] + 1], l1 = box[2 * ch[1]], h1 = box[2 * ch[1] + 1];
+    const float lo[3] = {fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z)};
+    const float hi[3] = {fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z)};
+    const float c[3] = {0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2])};
+    float out[NM];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) out[q] = 0.f;
+    float rad = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float4 g = geo[ch[h]];
+        const float sx = g.x - c[0], sy = g.y - c[1], sz = g.z - c[2];
+        rad = fmaxf(rad, sqrtf(sx * sx + sy * sy + sz * sz) + g.w);
+        float tx[P + 1], ty[P + 1], tz[P + 1];  // s^a / a! per axis
+        tx[0] = ty[0] = tz[0] = 1.f;
+#pragma unroll
+        for (int a = 1; a <= P; ++a) {
+            tx[a] = tx[a - 1] * sx * (1.f / a);
+            ty[a] = ty[a - 1] * sy * (1.f / a);
+            tz[a] = tz[a - 1] * sz * (1.f / a);
+        }
+        const float* mc = mom + (size_t)ch[h] * 3 * NM + l * NM;
+        float m[NM];
+#pragma unroll
+        for (int q = 0; q < NM; ++q) m[q] = mc[q];
+#pragma unroll
+        for (int n = 0; n <= P; ++n)
+#pragma unroll
+            for (int a = n; a >= 0; --a)
+#pragma unroll
+                for (int b = n - a; b >= 0; --b) {
+                    const int cc = n - a - b;
+                    float v = out[midx(a, b, cc)];
+#pragma unroll
+                    for (int a2 = 0; a2 <= a; ++a2)
+#pragma unroll
+                        for (int b2 = 0; b2 <= b; ++b2)
+#pragma unroll
+                            for (int c2 = 0; c2 <= cc; ++c2)
+                                v = fmaf(m[midx(a2, b2, c2)], tx[a - a2] * ty[b - b2] * tz[cc - c2], v);
+                    out[midx(a, b, cc)] = v;
+                }
+    }
+    float* mp = mom + (size_t)id * 3 * NM + l * NM;
+#pragma unroll
+    for (int q = 0; q < NM; ++q) mp[q] = out[q];
+    if (l == 0) {
+        const float hd = 0.5f * sqrtf((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                      (hi[2] - lo[2]) * (hi[2] - lo[2]));
+        geo[id] = make_float4(c[0], c[1], c[2], fminf(rad, hd) * 1.000001f);
+        box[2 * id] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        box[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Far-field evaluation of one node's expansion at one target, R = x - c:
+// adds 4 pi u to w[0..2] and -4 pi (grad u)_ab / 3 to the eight stored entries of
+// G' (w[3..10] = xx, xy, xz, yx, yy, yz, zx, zy), the direct sweep's accumulator
+// form (the expansion's gradient is trace-free exactly: its three diagonal sums
+// cancel term by term).
+// ---------------------------------------------------------------------------
+template <int P, bool GRAD>
+__device__ __forceinline__ void m2p(float rx, float ry, float rz, const float* __restrict__ M, float* w)
+{
+    constexpr int NM = nterms(P);
+    constexpr int Q = P + (GRAD ? 2 : 1);
+    constexpr int NC = nterms(Q);
+    float b[NC];
+    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    const float ir2 = __frcp_rn(r2);
+    b[0] = rsqrtf(r2);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    float jxx = 0.f, jxy = 0.f, jxz = 0.f, jyx = 0.f, jyy = 0.f, jyz = 0.f, jzx = 0.f, jzy = 0.f;
+    // Order by order: once the b_k of order n exist, the moments of order n - 1 take
+    // their velocity terms and those of order n - 2 their gradient terms, so only two
+    // orders of b are live at a time.
+#pragma unroll
+    for (int n = 1; n <= Q; ++n) {
+        const float c1 = (float)(2 * n - 1) / (float)n, c2 = (float)(n - 1) / (float)n;
+#pragma unroll
+        for (int a = n; a >= 0; --a)
+#pragma unroll
+            for (int bb = n - a; bb >= 0; --bb) {
+                const int c = n - a - bb;
+                float s1 = 0.f, s2 = 0.f;
+                if (a >= 1) s1 = fmaf((float)a * rx, b[midx(a - 1, bb, c)], s1);
+                if (bb >= 1) s1 = fmaf((float)bb * ry, b[midx(a, bb - 1, c)], s1);
+                if (c >= 1) s1 = fmaf((float)c * rz, b[midx(a, bb, c - 1)], s1);
+                if (a >= 2) s2 = fmaf((float)(a * (a - 1)), b[midx(a - 2, bb, c)], s2);
+                if (bb >= 2) s2 = fmaf((float)(bb * (bb - 1)), b[midx(a, bb - 2, c)], s2);
+                if (c >= 2) s2 = fmaf((float)(c * (c - 1)), b[midx(a, bb, c - 2)], s2);
+                b[midx(a, bb, c)] = ir2 * fmaf(c1, s1, -c2 * s2);
+            }
+        if (n - 1 <= P) {
+            // 4 pi u_a = -eps_ajl sum_k M_k^l b_{k+e_j}, |k| = n - 1
+            const int m = n - 1;
+#pragma unroll
+            for (int a = m; a >= 0; --a)
+#pragma unroll
+                for (int bb = m - a; bb >= 0; --bb) {
+                    const int c = m - a - bb;
+                    const int q = midx(a, bb, c);
+                    const float Mx = M[q], My = M[NM + q], Mz = M[2 * NM + q];
+                    const float bx = b[midx(a + 1, bb, c)], by = b[midx(a, bb + 1, c)], bz = b[midx(a, bb, c + 1)];
+                    ux = fmaf(My, bz, fmaf(-Mz, by, ux));
+                    uy = fmaf(Mz, bx, fmaf(-Mx, bz, uy));
+                    uz = fmaf(Mx, by, fmaf(-My, bx, uz));
+                }
+        }
+        if (GRAD && n >= 2 && n - 2 <= P) {
+            // 4 pi J_ab = eps_ajl H_jb^l,  H_jb^l = sum_k M_k^l b_{k+e_j+e_b}, |k| = n - 2
+            const int m = n - 2;
+#pragma unroll
+            for (int a = m; a >= 0; --a)
+#pragma unroll
+                for (int bb = m - a; bb >= 0; --bb) {
+                    const int c = m - a - bb;
+                    const int q = midx(a, bb, c);
+                    const float Mx = M[q], My = M[NM + q], Mz = M[2 * NM + q];
+                    const float bxx = b[midx(a + 2, bb, c)], byy = b[midx(a, bb + 2, c)], bzz = b[midx(a, bb, c + 2)];
+                    const float bxy = b[midx(a + 1, bb + 1, c)], bxz = b[midx(a + 1, bb, c + 1)],
+                                byz = b[midx(a, bb + 1, c + 1)];
+                    jxx = fmaf(Mz, bxy, fmaf(-My, bxz, jxx));
+                    jxy = fmaf(Mz, byy, fmaf(-My, byz, jxy));
+                    jxz = fmaf(Mz, byz, fmaf(-My, bzz, jxz));
+                    jyx = fmaf(Mx, bxz, fmaf(-Mz, bxx, jyx));
+                    jyy = fmaf(Mx, byz, fmaf(-Mz, bxy, jyy));
+                    jyz = fmaf(Mx, bzz, fmaf(-Mz, bxz, jyz));
+                    jzx = fmaf(My, bxx, fmaf(-Mx, bxy, jzx));
+                    jzy = fmaf(My, bxy, fmaf(-Mx, byy, jzy));
+                }
+        }
+    }
+    w[0] += ux, w[1] += uy, w[2] += uz;
+    if constexpr (GRAD) {
+        constexpr float k = -1.f / 3.f;
+        w[3] = fmaf(k, jxx, w[3]), w[4] = fmaf(k, jxy, w[4]), w[5] = fmaf(k, jxz, w[5]);
+        w[6] = fmaf(k, jyx, w[6]), w[7] = fmaf(k, jyy, w[7]), w[8] = fmaf(k, jyz, w[8]);
+        w[9] = fmaf(k, jzx, w[9]), w[10] = fmaf(k, jzy, w[10]);
+    }
+}
+
+struct TreeArgs {
+    const float4* psrc;  // sorted packed sources [n][5]
+    const float4* geo;   // per node (cx, cy, cz, r)
+    const float* mom;    // per node [3][NM] scaled moments
+    const int* idx;      // sorted position -> particle index
+    long long n;
+    int D;
+    float theta, sep;    // opening angle, 7 sigma
+    int m2p_min;
+    NearConst nc;
+    int* counter;
+    float* u;
+    float* grad;
+};
+
+// The direct sum over the sorted run [s, e) staged through the warp's buffer.
+template <bool GRAD, bool NEAR>
+__device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs& A, long long s, long long e,
+                                           float4* buf, int lane, f2 X, f2 Y, f2 Z)
+{
+    const Own own{};
+    for (long long c0 = s; c0 < e; c0 += 32) {
+        const int cnt = (int)min(32LL, e - c0);
+        __syncwarp();
+        if (lane < cnt) {
+            const float4* src = A.psrc + (c0 + lane) * P_F4;
+#pragma unroll
+            for (int f = 0; f < P_F4; ++f) buf[lane * P_F4 + f] = src[f];
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) particle_source<GRAD, false, NEAR>(acc, buf + j * P_F4, X, Y, Z, A.nc, own);
+    }
+}
+
+template <int P, bool GRAD>
+__global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
+{
+    constexpr int NM = nterms(P);
+    static_assert(3 * NM * 4 <= 32 * P_F4 * 16, "moments fit the warp's source buffer");
+    __shared__ float4 sbuf[TREE_WARPS][32 * P_F4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* buf = sbuf[warp];
+    float* mbuf = reinterpret_cast<float*>(buf);
+    const long long nleaves = 1LL << A.D;
+    for (;;) {
+        long long leaf = 0;
+        if (lane == 0) leaf = atomicAdd(A.counter, 1);
+        leaf = __shfl_sync(0xffffffffu, leaf, 0);
+        if (leaf >= nleaves) break;
+        const long long s = run_begin(leaf, A.n, A.D), e = run_begin(leaf + 1, A.n, A.D);
+        const long long i0 = s + lane, i1 = s + 32 + lane;
+        const bool v0 = i0 < e, v1 = i1 < e;
+        const float4 p0 = A.psrc[(v0 ? i0 : s) * P_F4], p0z = A.psrc[(v0 ? i0 : s) * P_F4 + 1];
+        const float4 p1 = A.psrc[(v1 ? i1 : s) * P_F4], p1z = A.psrc[(v1 ? i1 : s) * P_F4 + 1];
+        const f2 X = make_float2(-p0.x, -p1.x), Y = make_float2(-p0.z, -p1.z), Z = make_float2(-p0z.x, -p1z.x);
+        const float4 tg = A.geo[nleaves - 1 + leaf];
+        Acc<GRAD, false> acc;
+        acc.zero();
+        // depth-first walk; entry t of the stack lives in lane t
+        int st = 0, sp = 1;  // the root
+        while (sp > 0) {
+            const int id = __shfl_sync(0xffffffffu, st, sp - 1);
+            --sp;
+            const int level = 31 - __clz(id + 1);
+            const long long k = (long long)id + 1 - (1LL << level);
+            const long long ns = run_begin(k, A.n, level), ne = run_begin(k + 1, A.n, level);
+            const float4 g = A.geo[id];
+            const float dx = g.x - tg.x, dy = g.y - tg.y, dz = g.z - tg.z;
+            const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            const float rs = g.w + tg.w;
+            const bool far = rs < A.theta * d && d - rs >= A.sep;
+            if (far && ne - ns >= A.m2p_min) {
+                __syncwarp();
+                const float* src = A.mom + (size_t)id * 3 * NM;
+                for (int t = lane; t < 3 * NM; t += 32) mbuf[t] = src[t];
+                __syncwarp();
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    float w[11];
+#pragma unroll
+                    for (int q = 0; q < 11; ++q) w[q] = 0.f;
+                    const float rx = (h ? X.y : X.x) - g.x, ry = (h ? Y.y : Y.x) - g.y, rz = (h ? Z.y : Z.x) - g.z;
+                    m2p<P, GRAD>(rx, ry, rz, mbuf, w);
+                    if (h == 0) {
+                        acc.v[0].x += w[0], acc.v[1].x += w[1], acc.v[2].x += w[2];
+                        if constexpr (GRAD) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) acc.v[6 + q].x += w[3 + q];
+                        }
+                    } else {
+                        acc.v[0].y += w[0], acc.v[1].y += w[1], acc.v[2].y += w[2];
+                        if constexpr (GRAD) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) acc.v[6 + q].y += w[3 + q];
+                        }
+                    }
+                }
+            } else if (far) {
+                direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z);
+            } else if (level == A.D) {
+                if (d - rs >= A.sep)
+                    direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z);
+                else
+                    direct_run<GRAD, true>(acc, A, ns, ne, buf, lane, X, Y, Z);
+            } else {
+                // push the right child first so the left one is walked first
+                if (lane == sp) st = 2 * id + 2;
+                if (lane == sp + 1) st = 2 * id + 1;
+                sp += 2;
+            }
+        }
+        // epilogue: u = u / (4 pi), J = ([S x] - 3 G') / (4 pi), G'_zz = -G'_xx - G'_yy
+        const float f = 0.079577471545947668f;
+        const long long n = A.n;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!(h ? v1 : v0)) continue;
+            const long long o = A.idx[h ? i1 : i0];
+            float v[14];
+#pragma unroll
+            for (int q = 0; q < Acc<GRAD, false>::N; ++q) v[q] = h ? acc.v[q].y : acc.v[q].x;
+            A.u[o] = v[0] * f, A.u[n + o] = v[1] * f, A.u[2 * n + o] = v[2] * f;
+            if constexpr (GRAD) {
+                const float Sx = v[3], Sy = v[4], Sz = v[5], Gzz = -v[6] - v[10];
+                float* J = A.grad;
+                J[o] = (-3.f * v[6]) * f;
+                J[n + o] = (-Sz - 3.f * v[7]) * f;
+                J[2 * n + o] = (Sy - 3.f * v[8]) * f;
+                J[3 * n + o] = (Sz - 3.f * v[9]) * f;
+                J[4 * n + o] = (-3.f * v[10]) * f;
+                J[5 * n + o] = (-Sx - 3.f * v[11]) * f;
+                J[6 * n + o] = (-Sy - 3.f * v[12]) * f;
+                J[7 * n + o] = (Sx - 3.f * v[13]) * f;
+                J[8 * n + o] = (-3.f * Gzz) * f;
+            }
+        }
+    }
+}
+
+template <int P>
+cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, float theta, bool grad, float* u,
+                        float* grad_u, cudaStream_t st)
+{
+    float4* psrc = reinterpret_cast<float4*>(ws + w.psrc);
+    float4* geo = reinterpret_cast<float4*>(ws + w.geo);
+    float4* box = reinterpret_cast<float4*>(ws + w.box);
+    float* mom = reinterpret_cast<float*>(ws + w.mom);
+    const long long leaves = 1LL << w.D;
+    trace_launch();
+    tree_leaf_kernel<P><<<(unsigned)((leaves * 32 + 255) / 256), 256, 0, st>>>(psrc, n, w.D, geo, box, mom);
+    for (int l = w.D - 1; l >= 0; --l) {
+        const long long t = 3 * (1LL << l);
+        trace_launch();
+        tree_up_kernel<P><<<(unsigned)((t + 127) / 128), 128, 0, st>>>(l, geo, box, mom);
+    }
+    TreeArgs A{};
+    A.psrc = psrc;
+    A.geo = geo;
+    A.mom = mom;
+    A.idx = reinterpret_cast<const int*>(ws + w.idx1);
+    A.n = n;
+    A.D = w.D;
+    A.theta = theta;
+    A.sep = (float)(RHO_FAR * (double)sigma);
+    A.m2p_min = m2p_min(P);
+    const double s = sigma;
+    A.nc.inv_s2 = (float)(1.0 / (s * s));
+    A.nc.inv_s3 = (float)(1.0 / (s * s * s));
+    A.nc.inv_s5 = (float)(1.0 / (s * s * s * s * s));
+    A.nc.far2 = (float)((double)RHO_FAR * RHO_FAR * s * s);
+    A.counter = reinterpret_cast<int*>(ws + w.counter);
+    A.u = u;
+    A.grad = grad_u;
+    cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    auto kern = grad ? tree_eval_kernel<P, true> : tree_eval_kernel<P, false>;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TREE_WARPS * 32, 0);
+    if (e != cudaSuccess) return e;
+    const long long want = (leaves + TREE_WARPS - 1) / TREE_WARPS;
+    const long long blocks = std::min<long long>(want, (long long)std::max(per_sm, 1) * sm_count());
+    trace_launch();
+    kern<<<(unsigned)blocks, TREE_WARPS * 32, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tree_workspace(long long n, size_t* bytes)
+{
+    TreeWs w;
+    const cudaError_t e = tree_layout(n, w);
+    *bytes = e == cudaSuccess ? w.bytes : 0;
+    return e;
+}
+
+cudaError_t run_tree_induce(const float* pos, const float* str, long long n, float sigma, float theta, int order,
+                            float* u, float* grad_u, char* ws, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    TreeWs w;
+    cudaError_t e = tree_layout(n, w);
+    if (e != cudaSuccess) return e;
+    float* part = reinterpret_cast<float*>(ws + w.part);
+    auto* k0 = reinterpret_cast<unsigned long long*>(ws + w.keys0);
+    auto* k1 = reinterpret_cast<unsigned long long*>(ws + w.keys1);
+    int* i0 = reinterpret_cast<int*>(ws + w.idx0);
+    int* i1 = reinterpret_cast<int*>(ws + w.idx1);
+    const float4* p4 = reinterpret_cast<const float4*>(pos);
+    const int nparts = (int)std::min<long long>(BOUNDS_BLOCKS, (n + 255) / 256);
+    trace_launch();
+    tree_bounds_kernel<<<nparts, 256, 0, st>>>(p4, (int)n, part);
+    trace_launch();
+    tree_box_kernel<<<1, 1024, 0, st>>>(part, nparts);
+    trace_launch();
+    tree_keys_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p4, (int)n, part + 6 * nparts, k0, i0);
+    size_t cb = w.cub_bytes;
+    e = cub::DeviceRadixSort::SortPairs(ws + w.cub, cb, k0, k1, i0, i1, (int)n, 0, 3 * MORTON_BITS, st);
+    if (e != cudaSuccess) return e;
+    trace_launch();
+    tree_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p4, reinterpret_cast<const float4*>(str), i1,
+                                                                     (int)n, reinterpret_cast<float4*>(ws + w.psrc));
+    const bool grad = grad_u != nullptr;
+    switch (order) {
+        case 2: return launch_tree<2>(w, ws, n, sigma, theta, grad, u, grad_u, st);
+        case 3: return launch_tree<3>(w, ws, n, sigma, theta, grad, u, grad_u, st);
+        default: return launch_tree<4>(w, ws, n, sigma, theta, grad, u, grad_u, st);
+    }
+}
+
+}  // namespace vpm

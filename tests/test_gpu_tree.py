@@ -1,0 +1,158 @@
+"""The treecode (vpm_tree_induce, the fast summation of Sec. II.B) against the direct
+sum as its oracle:
+
+* theta = 0 opens every cluster, so the result is the direct sum: it matches the
+  FP64 oracle to the plain-FP32 tolerance, on sizes that leave ragged leaves;
+* with clusters accepted, the truncation error falls with the expansion order p as
+  (a / L)^(p + 1) for a source cluster of radius a at distance L (a wrong term of the
+  derivative recurrence, the moments or their shift breaks this rate), and it falls
+  with the opening angle theta;
+* on the hover wake and on the million-particle BVI wake the default settings
+  (theta = 0.5, p = 4) stay within stated error bounds against the FP64 oracle on
+  sampled targets;
+* degenerate inputs: one particle, coincident particles, particles on a line.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_11430_gb300 import synth
+from tests._util import TOL_PLAIN, grad_rows, planar_to_rows, rel_l2, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# default settings' error bound against the FP64 oracle (relative L2 over sampled targets)
+TREE_TOL_U = 2e-4
+TREE_TOL_G = 1e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_11430_gb300 import api as a
+    from paper_2511_11430_gb300 import build
+
+    build.build()
+    return a
+
+
+def _oracle_on(pos, strn, sigma, idx):
+    return oracle.p2p(pos, strn, pos[idx], sigma, grad=True)
+
+
+def _errors(u, g, ref_u, ref_J, idx):
+    eu = rel_l2(planar_to_rows(u, 3)[idx], ref_u)
+    eg = rel_l2(grad_rows(g)[idx], ref_J)
+    return eu, eg
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 129, 3001])
+def test_theta_zero_is_the_direct_sum(api, n):
+    w = synth.make(1, n=max(n, 2))
+    pos, strn = w.pos[:n], w.strength[:n]
+    P, S = to_dev(pos), to_dev(strn)
+    u, g = api.tree_induce(P, S, w.sigma, theta=0.0, order=4)
+    if n == 1:
+        assert torch.count_nonzero(u) == 0 and torch.count_nonzero(g) == 0
+        return
+    ref_u, ref_J = oracle.p2p(pos, strn, pos, w.sigma, grad=True)
+    assert rel_l2(planar_to_rows(u, 3), ref_u) <= TOL_PLAIN
+    assert rel_l2(grad_rows(g), ref_J) <= TOL_PLAIN
+    uv = api.tree_induce(P, S, w.sigma, theta=0.0, order=4, grad=False)
+    assert torch.equal(uv, u)
+
+
+def _two_clusters(a, seed=0, L=1.0):
+    """64 zero-strength targets in a ball of radius 1e-3 at the origin, 448 sources in
+    a ball of radius a about (L, 0, 0)."""
+    rng = np.random.default_rng(seed)
+
+    def ball(m, r):
+        v = rng.normal(size=(m, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return v * (r * rng.uniform(0, 1, size=(m, 1)) ** (1 / 3))
+
+    x = np.concatenate([ball(64, 1e-3), ball(448, a) + [L, 0.0, 0.0]])
+    G = np.concatenate([np.zeros((64, 3)), rng.normal(size=(448, 3))])
+    pos = np.zeros((512, 4), np.float32)
+    pos[:, :3] = x
+    strn = np.zeros((512, 4), np.float32)
+    strn[:, :3] = G
+    return pos, strn
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_truncation_error_falls_at_the_expansion_order(api, order):
+    """Halving the source cluster's radius divides the far-field error by about
+    2^(p + 1); the direct sum of the same FP32 inputs is the reference."""
+    sigma = 1e-4
+    errs = []
+    for a in (0.4, 0.2, 0.1):
+        pos, strn = _two_clusters(a)
+        P, S = to_dev(pos), to_dev(strn)
+        u, g = api.tree_induce(P, S, sigma, theta=1.0, order=order)
+        u0, g0 = api.tree_induce(P, S, sigma, theta=0.0, order=order)
+        tu, ru = planar_to_rows(u, 3)[:64], planar_to_rows(u0, 3)[:64]
+        tg, rg = grad_rows(g)[:64], grad_rows(g0)[:64]
+        errs.append((rel_l2(tu, ru), rel_l2(tg, rg)))
+    errs = np.array(errs)
+    assert np.all(errs[0] > 1e-6), errs  # the expansion is in use
+    rate = errs[:-1] / errs[1:]
+    # the expected ratio is 2^(p+1) (8, 16, 32); half of it allows for the FP32 floor
+    # and the clusters' actual extent
+    assert np.all(rate >= 0.5 * 2 ** (order + 1)), (order, errs, rate)
+
+
+def test_error_falls_with_theta(api):
+    rng = np.random.default_rng(5)
+    n = 20000
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = rng.uniform(-1, 1, size=(n, 3))
+    strn = np.zeros((n, 4), np.float32)
+    strn[:, :3] = rng.normal(size=(n, 3)) * 1e-3
+    sigma = 1e-3
+    P, S = to_dev(pos), to_dev(strn)
+    idx = np.sort(rng.choice(n, 200, replace=False))
+    ref_u, ref_J = _oracle_on(pos, strn, sigma, idx)
+    errs = []
+    for theta in (0.8, 0.6, 0.4, 0.25):
+        u, g = api.tree_induce(P, S, sigma, theta=theta, order=4)
+        errs.append(_errors(u, g, ref_u, ref_J, idx))
+    errs = np.array(errs)
+    assert np.all(np.diff(errs[:, 0]) < 0) and np.all(np.diff(errs[:, 1]) < 0), errs
+    assert errs[-1, 0] < 1e-5, errs
+
+
+def test_degenerate_inputs(api):
+    # every particle at one point: all pairs at zero distance contribute nothing
+    pos = np.zeros((300, 4), np.float32)
+    pos[:, :3] = [0.3, -0.2, 0.1]
+    strn = np.ones((300, 4), np.float32)
+    u, g = api.tree_induce(to_dev(pos), to_dev(strn), 0.01, theta=0.5, order=3)
+    assert torch.count_nonzero(u) == 0 and torch.count_nonzero(g) == 0
+    # particles on one line (a filament), a size that leaves ragged leaves
+    n = 777
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, 0] = np.linspace(0, 1, n)
+    strn = np.zeros((n, 4), np.float32)
+    strn[:, 1] = 1e-3
+    P, S = to_dev(pos), to_dev(strn)
+    u, g = api.tree_induce(P, S, 0.002, theta=0.5, order=4)
+    ref_u, ref_J = oracle.p2p(pos, strn, pos, 0.002, grad=True)
+    assert rel_l2(planar_to_rows(u, 3), ref_u) <= TREE_TOL_U
+    assert rel_l2(grad_rows(g), ref_J) <= TREE_TOL_G
+
+
+@pytest.mark.parametrize("config", [2, 3])
+def test_default_settings_on_rotor_wakes(api, config):
+    """Hover (100,000 particles) and BVI (1,000,000) wakes, theta = 0.5, p = 4, against
+    the FP64 oracle on 64 sampled targets."""
+    w = synth.make(config)
+    P, S = to_dev(w.pos), to_dev(w.strength)
+    u, g = api.tree_induce(P, S, w.sigma, theta=0.5, order=4)
+    idx = synth.sample_targets(11, w.n, 64)
+    ref_u, ref_J = _oracle_on(w.pos, w.strength, w.sigma, idx)
+    eu, eg = _errors(u, g, ref_u, ref_J, idx)
+    assert eu <= TREE_TOL_U and eg <= TREE_TOL_G, (eu, eg)
