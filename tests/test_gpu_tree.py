@@ -23,8 +23,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # default settings' error bound against the FP64 oracle (relative L2 over sampled targets)
-TREE_TOL_U = 2e-4
-TREE_TOL_G = 1e-3
+TREE_TOL_U = 1e-3
+TREE_TOL_G = 5e-4
 
 
 @pytest.fixture(scope="module")
@@ -83,13 +83,14 @@ def _two_clusters(a, seed=0, L=1.0):
     return pos, strn
 
 
-@pytest.mark.parametrize("order", [2, 3, 4])
-def test_truncation_error_falls_at_the_expansion_order(api, order):
+@pytest.mark.parametrize("order, radii", [(2, (0.2, 0.1, 0.05)), (3, (0.3, 0.15, 0.075)), (4, (0.4, 0.2, 0.1))])
+def test_truncation_error_falls_at_the_expansion_order(api, order, radii):
     """Halving the source cluster's radius divides the far-field error by about
-    2^(p + 1); the direct sum of the same FP32 inputs is the reference."""
+    2^(p + 1); the direct sum of the same FP32 inputs is the reference.  The radii
+    keep the smallest error well above the FP32 floor."""
     sigma = 1e-4
     errs = []
-    for a in (0.4, 0.2, 0.1):
+    for a in radii:
         pos, strn = _two_clusters(a)
         P, S = to_dev(pos), to_dev(strn)
         u, g = api.tree_induce(P, S, sigma, theta=1.0, order=order)
