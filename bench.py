@@ -72,14 +72,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=None,
                     help="seconds of oracle work per CPU-baseline sample (default 12; reference arm: 60 s over all steps)")
-    ap.add_argument("--part", choices=["aic", "wake"], default=None,
+    ap.add_argument("--part", choices=["aic", "wake", "tree"], default=None,
                     help="time one component alone (for profiling; prints a text line, not the JSON contract)")
     return ap.parse_args()
 
 
 def run_part(args):
-    """One component of the step, repeated --steps times after --warmup: the AIC build +
-    solve of the hover blade lattice, or the conversion of 2,000 hover wake rows."""
+    """One component, repeated --steps times after --warmup: the AIC build + solve of the
+    hover blade lattice, the conversion of 2,000 hover wake rows, or the treecode
+    (theta 0.5, order 4) on the 1,000,000-particle BVI wake (--particles to shrink it)."""
     import torch
 
     from paper_2511_11430_gb300 import api, build, synth
@@ -97,6 +98,14 @@ def run_part(args):
             A, b = api.aic_build(rings, colloc, normal, w.seg_core, 2, v_rel=vrel)
             return api.aic_solve(A, b, tol=1e-12, max_iter=30, ws=wsb)
         what = f"aic_build + aic_solve, n = {w.n_ctrl}"
+    elif args.part == "tree":
+        w = synth.make(3, n=args.particles)
+        P, S = T(w.pos), T(w.strength)
+        wsb = api.Workspace()
+
+        def once():
+            return api.tree_induce(P, S, w.sigma, theta=0.5, order=4, ws=wsb)
+        what = f"tree_induce (theta 0.5, order 4), {w.n:,} particles"
     else:
         ea, eb, eg, egn, ehn, etr, ds_tip = synth.rotor_wake_edges(5, 2000)
         wa, wb, wg, wgn = (T(q, torch.float64) for q in (ea, eb, eg, egn))
