@@ -118,12 +118,14 @@ def test_error_falls_with_theta(api):
     idx = np.sort(rng.choice(n, 200, replace=False))
     ref_u, ref_J = _oracle_on(pos, strn, sigma, idx)
     errs = []
-    for theta in (0.8, 0.6, 0.4, 0.25):
+    for theta in (1.0, 0.8, 0.6, 0.4):
         u, g = api.tree_induce(P, S, sigma, theta=theta, order=4)
         errs.append(_errors(u, g, ref_u, ref_J, idx))
     errs = np.array(errs)
-    assert np.all(np.diff(errs[:, 0]) < 0) and np.all(np.diff(errs[:, 1]) < 0), errs
-    assert errs[-1, 0] < 1e-5, errs
+    # strictly falling while above the plain FP32 floor of a 20,000-term sum (about 2e-6
+    # here), then at that floor
+    assert np.all(np.diff(errs[:3, 0]) < 0) and np.all(np.diff(errs[:3, 1]) < 0), errs
+    assert errs[-1, 0] < 1e-5 and errs[-1, 1] < 1e-5, errs
 
 
 def test_degenerate_inputs(api):
