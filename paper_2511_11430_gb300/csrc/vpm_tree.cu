@@ -1,7 +1,8 @@
 // Treecode evaluation of the particle velocity and velocity gradient (Eq. 2-4) of n
 // particles on themselves, in O(n log n) work: the fast summation that Sec. II.B
-// calls for in place of the direct sum (the paper uses a Cartesian FMM; this is
-// the Cartesian Taylor treecode, the FMM without local expansions).
+// calls for in place of the direct sum (the paper uses a Cartesian FMM; this is a
+// Cartesian Taylor treecode with cluster-to-leaf local expansions: the FMM's
+// expansions without their translations between tree levels).
 //
 // Tree.  The particles are sorted along a Morton (Z-order) curve of their positions
 // (21 bits per axis) and the sorted array is halved recursively: node (l, k) of
@@ -16,24 +17,28 @@
 // precision, and u = curl Psi / (4 pi) with Psi(x) = sum_j Gamma_j / |x - x_j|.
 // With R = x - c and d_j = x_j - c, Taylor expansion in d_j gives
 //   Psi^l(x) = sum_k M_k^l b_k(R),  b_k = (-1)^|k| d^k(1/|R|)/dR^k,  |k| <= p,
-// and d b_k / dx_j = -b_{k + e_j}, so
-//   4 pi u_a = -eps_ajl sum_k M_k^l b_{k + e_j},   4 pi (grad u)_ab = eps_ajl sum_k M_k^l b_{k + e_j + e_b}.
-// The b_k follow from b_0 = 1/|R| by the recurrence of the derivatives of 1/|R|,
-//   |k| |R|^2 b_k = (2|k| - 1) sum_i k_i R_i b_{k - e_i} - (|k| - 1) sum_i k_i (k_i - 1) b_{k - 2 e_i},
-// (the Taylor-coefficient recurrence of 1/|x - y| with the factorials moved into
-// b_k).  Moving a node's moments from a child centre c' to the parent centre c is
-// the product of two truncated series: M_k = sum_{i <= k} M'_i s^(k - i) / (k - i)!,
-// s = c' - c.
+// and d b_k / dR_j = -b_{k + e_j}.  The b_k follow from b_0 = 1/|R| by the
+// recurrence of the derivatives of 1/|R|,
+//   |k| |R|^2 b_k = (2|k| - 1) sum_i k_i R_i b_{k - e_i} - (|k| - 1) sum_i k_i (k_i - 1) b_{k - 2 e_i}
+// (the Taylor-coefficient recurrence of 1/|x - y| with the factorials moved into b_k).
+// Moving a node's moments from a child centre c' to the parent centre c is the
+// product of two truncated series: M_k = sum_{i <= k} M'_i s^(k - i) / (k - i)!,
+// s = c' - c.  A far cluster s acts on a target leaf t (centre c_t, x = c_t + y,
+// R0 = c_t - c_s) through the leaf's local expansion of order q = p + 2,
+//   Psi^l(c_t + y) = sum_{|m| <= q} L_m^l y^m / m!,  L_m^l = (-1)^|m| sum_k M_k^l b_{k + m}(R0),
+// summed over every far cluster of the leaf, and at each target
+//   4 pi u_a = eps_ajl sum_m L^l_{m + e_j} y^m / m!,   4 pi (grad u)_ab = eps_ajl sum_m L^l_{m + e_j + e_b} y^m / m!.
 //
 // Traversal.  One warp per target leaf (its targets two per thread, in the lanes of
 // packed float2 registers, as in the direct sweep) walks the tree depth first from
 // the root with its stack spread over the warp's lanes.  A node is far from the
 // leaf when r_node + r_leaf < theta |c_node - c_leaf| and every pair is at least
-// 7 sigma apart; a far node with at least m2p_min particles enters by its expansion,
-// a smaller far node by the point-vortex sum over its particles (cheaper than the
-// expansion, and exact); a leaf that is not far enters by the direct sum with the
-// regularised kernel; any other node is opened.  theta = 0 opens every node, which
-// gives the direct sum.
+// 7 sigma apart; a far node enters the leaf's local expansion (the warp computes
+// the b_k(R0) together, order by order, into a dense table in shared memory, and
+// each lane accumulates its share of the L_m), a leaf that is not far enters by the
+// direct sum with the regularised kernel, and any other node is opened.  After the
+// walk every target evaluates the local expansion once.  theta = 0 opens every
+// node, which gives the direct sum.
 #include <math.h>
 
 #include <algorithm>
@@ -69,10 +74,10 @@ int tree_depth(long long n)
     return D;
 }
 
-// Smallest particle count of a far node that enters by its expansion: below it the
-// point-vortex sum over the node's particles costs less (about 16 lane operations
-// per pair and target against roughly 570, 1,000 and 1,700 for p = 2, 3, 4).
-int m2p_min(int p) { return p == 2 ? 40 : p == 3 ? 64 : 112; }
+// Smallest particle count of a far node that enters the leaf's local expansion:
+// below it the point-vortex sum over its particles is cheaper (about 16 lane
+// operations per pair and target against about 1,000 per lane for the expansion).
+constexpr int M2L_MIN = 32;
 
 struct TreeWs {
     size_t part, keys0, keys1, idx0, idx1, cub, cub_bytes, psrc, geo, box, mom, counter, bytes;
@@ -373,83 +378,153 @@ __global__ void tree_up_kernel(int level, float4* __restrict__ geo, float4* __re
 }
 
 // ---------------------------------------------------------------------------
-// Far-field evaluation of one node's expansion at one target, R = x - c:
-// adds 4 pi u to w[0..2] and -4 pi (grad u)_ab / 3 to the eight stored entries of
-// G' (w[3..10] = xx, xy, xz, yx, yy, yz, zx, zy), the direct sweep's accumulator
-// form (the expansion's gradient is trace-free exactly: its three diagonal sums
-// cancel term by term).
+// Far field through the target leaf's local expansion.
 // ---------------------------------------------------------------------------
-template <int P, bool GRAD>
-__device__ __forceinline__ void m2p(float rx, float ry, float rz, const float* __restrict__ M, float* w)
+template <int P>
+struct Local {
+    static constexpr int Q = P + 2;              // local expansion order
+    static constexpr int NQ = P + Q;             // highest order of b_k needed
+    static constexpr int DIM = NQ + 1;           // dense table b[a][b][c], a, b, c <= NQ
+    static constexpr int DL = Q + 1;             // dense table L[l][a][b][c], a, b, c <= Q
+    static constexpr int SL = DL * DL * DL;
+    static constexpr int NM = nterms(P);         // moments per component
+    static constexpr int NL = nterms(Q);         // local coefficients per component
+    static constexpr int RL = (NL + 31) / 32;    // local coefficients owned per lane
+    static constexpr int TABLE = DIM * DIM * DIM > 3 * SL ? DIM * DIM * DIM : 3 * SL;
+};
+
+// The multi-indices of order <= 10 in the graded order, (a, b, c) packed 4 bits each,
+// and the reciprocals 1/j.
+constexpr int MI_MAX = 10;
+struct MiTable {
+    unsigned short abc[nterms(MI_MAX)];
+    float recip[16];
+};
+
+constexpr MiTable make_mi_table()
 {
-    constexpr int NM = nterms(P);
-    constexpr int Q = P + (GRAD ? 2 : 1);
-    constexpr int NC = nterms(Q);
-    float b[NC];
+    MiTable t{};
+    int q = 0;
+    for (int n = 0; n <= MI_MAX; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) t.abc[q++] = (unsigned short)(a | (b << 4) | ((n - a - b) << 8));
+    t.recip[0] = 0.f;
+    for (int j = 1; j < 16; ++j) t.recip[j] = 1.0f / (float)j;
+    return t;
+}
+
+static __constant__ MiTable kMi = make_mi_table();
+
+// b_k(R0) for |k| <= NQ into the warp's dense table, order by order (each order reads
+// the two before it); the lanes share every order's entries.
+template <int P>
+__device__ __forceinline__ void local_table(float* __restrict__ B, float rx, float ry, float rz, int lane)
+{
+    using L = Local<P>;
+    static_assert(L::NQ <= MI_MAX, "multi-index table too short");
+    constexpr int D1 = L::DIM, D2 = L::DIM * L::DIM;
     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
     const float ir2 = __frcp_rn(r2);
-    b[0] = rsqrtf(r2);
+    if (lane == 0) B[0] = rsqrtf(r2);
+    __syncwarp();
+#pragma unroll 1
+    for (int n = 1; n <= L::NQ; ++n) {
+        const float c1 = (float)(2 * n - 1) * kMi.recip[n], c2 = (float)(n - 1) * kMi.recip[n];
+        const int q1 = nterms(n);
+#pragma unroll 1
+        for (int q = nterms(n - 1) + lane; q < q1; q += 32) {
+            const unsigned v = kMi.abc[q];
+            const int a = v & 15, b = (v >> 4) & 15, c = v >> 8;
+            const int i = a * D2 + b * D1 + c;
+            float s1 = 0.f, s2 = 0.f;
+            if (a >= 1) s1 = fmaf((float)a * rx, B[i - D2], s1);
+            if (b >= 1) s1 = fmaf((float)b * ry, B[i - D1], s1);
+            if (c >= 1) s1 = fmaf((float)c * rz, B[i - 1], s1);
+            if (a >= 2) s2 = fmaf((float)(a * (a - 1)), B[i - 2 * D2], s2);
+            if (b >= 2) s2 = fmaf((float)(b * (b - 1)), B[i - 2 * D1], s2);
+            if (c >= 2) s2 = fmaf((float)(c * (c - 1)), B[i - 2], s2);
+            B[i] = ir2 * fmaf(c1, s1, -c2 * s2);
+        }
+        __syncwarp();
+    }
+}
+
+// The local coefficients owned by a lane: m = lane + 32 r.
+template <int P>
+struct LocalAcc {
+    float x[Local<P>::RL], y[Local<P>::RL], z[Local<P>::RL];
+    int base[Local<P>::RL];  // offset of m in the b table
+};
+
+// L_m^l += sum_k M_k^l b_{k+m}(R0) for the lane's m (the sign (-1)^|m| comes later).
+template <int P>
+__device__ __forceinline__ void local_accumulate(LocalAcc<P>& acc, const float* __restrict__ B,
+                                                 const float* __restrict__ M)
+{
+    using L = Local<P>;
+    constexpr int D1 = L::DIM, D2 = L::DIM * L::DIM;
+#pragma unroll 5
+    for (int q = 0; q < L::NM; ++q) {
+        const unsigned v = kMi.abc[q];
+        const int off = (int)(v & 15) * D2 + (int)((v >> 4) & 15) * D1 + (int)(v >> 8);
+        const float Mx = M[q], My = M[L::NM + q], Mz = M[2 * L::NM + q];
+#pragma unroll
+        for (int r = 0; r < L::RL; ++r) {
+            const float bv = B[acc.base[r] + off];
+            acc.x[r] = fmaf(Mx, bv, acc.x[r]);
+            acc.y[r] = fmaf(My, bv, acc.y[r]);
+            acc.z[r] = fmaf(Mz, bv, acc.z[r]);
+        }
+    }
+}
+
+// The local expansion at one target, y = x - c_t: adds 4 pi u to w[0..2] and
+// -4 pi (grad u)_ab / 3 to the eight stored entries of G' (w[3..10] = xx, xy, xz,
+// yx, yy, yz, zx, zy), the direct sweep's accumulator form (the expansion's gradient
+// is trace-free exactly: its three diagonal sums cancel term by term).
+// Ld[l SL + (a DL + b) DL + c] = L_m^l, m = (a, b, c).
+template <int P, bool GRAD>
+__device__ __forceinline__ void local_eval(float yx, float yy, float yz, const float* __restrict__ Ld, float* w)
+{
+    using L = Local<P>;
+    constexpr int Q = L::Q, DL = L::DL, SL = L::SL, D2 = DL * DL;
+    const float* Lx = Ld;
+    const float* Ly = Ld + SL;
+    const float* Lz = Ld + 2 * SL;
     float ux = 0.f, uy = 0.f, uz = 0.f;
     float jxx = 0.f, jxy = 0.f, jxz = 0.f, jyx = 0.f, jyy = 0.f, jyz = 0.f, jzx = 0.f, jzy = 0.f;
-    // Order by order: once the b_k of order n exist, the moments of order n - 1 take
-    // their velocity terms and those of order n - 2 their gradient terms, so only two
-    // orders of b are live at a time.
-#pragma unroll
-    for (int n = 1; n <= Q; ++n) {
-        const float c1 = (float)(2 * n - 1) / (float)n, c2 = (float)(n - 1) / (float)n;
-#pragma unroll
-        for (int a = n; a >= 0; --a)
-#pragma unroll
-            for (int bb = n - a; bb >= 0; --bb) {
-                const int c = n - a - bb;
-                float s1 = 0.f, s2 = 0.f;
-                if (a >= 1) s1 = fmaf((float)a * rx, b[midx(a - 1, bb, c)], s1);
-                if (bb >= 1) s1 = fmaf((float)bb * ry, b[midx(a, bb - 1, c)], s1);
-                if (c >= 1) s1 = fmaf((float)c * rz, b[midx(a, bb, c - 1)], s1);
-                if (a >= 2) s2 = fmaf((float)(a * (a - 1)), b[midx(a - 2, bb, c)], s2);
-                if (bb >= 2) s2 = fmaf((float)(bb * (bb - 1)), b[midx(a, bb - 2, c)], s2);
-                if (c >= 2) s2 = fmaf((float)(c * (c - 1)), b[midx(a, bb, c - 2)], s2);
-                b[midx(a, bb, c)] = ir2 * fmaf(c1, s1, -c2 * s2);
+    float wa = 1.f;  // y^m / m!, built incrementally
+#pragma unroll 1
+    for (int a = 0; a < Q; ++a) {
+        float wb = wa;
+#pragma unroll 1
+        for (int b = 0; a + b < Q; ++b) {
+            float wm = wb;
+            int i = (a * DL + b) * DL;
+#pragma unroll 1
+            for (int c = 0; a + b + c < Q; ++c, ++i) {
+                // 4 pi u_a = eps_ajl d_j Psi^l
+                ux = fmaf(wm, Lz[i + DL] - Ly[i + 1], ux);
+                uy = fmaf(wm, Lx[i + 1] - Lz[i + D2], uy);
+                uz = fmaf(wm, Ly[i + D2] - Lx[i + DL], uz);
+                if (GRAD && a + b + c < Q - 1) {
+                    // 4 pi J_ab = eps_ajl d_b d_j Psi^l
+                    const int ixx = i + 2 * D2, iyy = i + 2 * DL, izz = i + 2;
+                    const int ixy = i + D2 + DL, ixz = i + D2 + 1, iyz = i + DL + 1;
+                    jxx = fmaf(wm, Lz[ixy] - Ly[ixz], jxx);
+                    jxy = fmaf(wm, Lz[iyy] - Ly[iyz], jxy);
+                    jxz = fmaf(wm, Lz[iyz] - Ly[izz], jxz);
+                    jyx = fmaf(wm, Lx[ixz] - Lz[ixx], jyx);
+                    jyy = fmaf(wm, Lx[iyz] - Lz[ixy], jyy);
+                    jyz = fmaf(wm, Lx[izz] - Lz[ixz], jyz);
+                    jzx = fmaf(wm, Ly[ixx] - Lx[ixy], jzx);
+                    jzy = fmaf(wm, Ly[ixy] - Lx[iyy], jzy);
+                }
+                wm *= yz * kMi.recip[c + 1];
             }
-        if (n - 1 <= P) {
-            // 4 pi u_a = -eps_ajl sum_k M_k^l b_{k+e_j}, |k| = n - 1
-            const int m = n - 1;
-#pragma unroll
-            for (int a = m; a >= 0; --a)
-#pragma unroll
-                for (int bb = m - a; bb >= 0; --bb) {
-                    const int c = m - a - bb;
-                    const int q = midx(a, bb, c);
-                    const float Mx = M[q], My = M[NM + q], Mz = M[2 * NM + q];
-                    const float bx = b[midx(a + 1, bb, c)], by = b[midx(a, bb + 1, c)], bz = b[midx(a, bb, c + 1)];
-                    ux = fmaf(My, bz, fmaf(-Mz, by, ux));
-                    uy = fmaf(Mz, bx, fmaf(-Mx, bz, uy));
-                    uz = fmaf(Mx, by, fmaf(-My, bx, uz));
-                }
+            wb *= yy * kMi.recip[b + 1];
         }
-        if (GRAD && n >= 2 && n - 2 <= P) {
-            // 4 pi J_ab = eps_ajl H_jb^l,  H_jb^l = sum_k M_k^l b_{k+e_j+e_b}, |k| = n - 2
-            const int m = n - 2;
-#pragma unroll
-            for (int a = m; a >= 0; --a)
-#pragma unroll
-                for (int bb = m - a; bb >= 0; --bb) {
-                    const int c = m - a - bb;
-                    const int q = midx(a, bb, c);
-                    const float Mx = M[q], My = M[NM + q], Mz = M[2 * NM + q];
-                    const float bxx = b[midx(a + 2, bb, c)], byy = b[midx(a, bb + 2, c)], bzz = b[midx(a, bb, c + 2)];
-                    const float bxy = b[midx(a + 1, bb + 1, c)], bxz = b[midx(a + 1, bb, c + 1)],
-                                byz = b[midx(a, bb + 1, c + 1)];
-                    jxx = fmaf(Mz, bxy, fmaf(-My, bxz, jxx));
-                    jxy = fmaf(Mz, byy, fmaf(-My, byz, jxy));
-                    jxz = fmaf(Mz, byz, fmaf(-My, bzz, jxz));
-                    jyx = fmaf(Mx, bxz, fmaf(-Mz, bxx, jyx));
-                    jyy = fmaf(Mx, byz, fmaf(-Mz, bxy, jyy));
-                    jyz = fmaf(Mx, bzz, fmaf(-Mz, bxz, jyz));
-                    jzx = fmaf(My, bxx, fmaf(-Mx, bxy, jzx));
-                    jzy = fmaf(My, bxy, fmaf(-Mx, byy, jzy));
-                }
-        }
+        wa *= yx * kMi.recip[a + 1];
     }
     w[0] += ux, w[1] += uy, w[2] += uz;
     if constexpr (GRAD) {
@@ -468,7 +543,6 @@ struct TreeArgs {
     long long n;
     int D;
     float theta, sep;    // opening angle, 7 sigma
-    int m2p_min;
     NearConst nc;
     int* counter;
     float* u;
@@ -495,16 +569,35 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
     }
 }
 
+// Shared memory of one traversal warp: the source staging buffer (also the node's
+// moments) and the dense b_k table (also the finished local coefficients), rounded
+// up to 16 bytes so that every warp's float4 staging buffer stays aligned.
+template <int P>
+__host__ __device__ constexpr size_t tree_warp_smem()
+{
+    return (32 * P_F4 * 16 + (size_t)Local<P>::TABLE * 4 + 15) / 16 * 16;
+}
+
 template <int P, bool GRAD>
 __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
 {
-    constexpr int NM = nterms(P);
-    static_assert(3 * NM * 4 <= 32 * P_F4 * 16, "moments fit the warp's source buffer");
-    __shared__ float4 sbuf[TREE_WARPS][32 * P_F4];
+    using L = Local<P>;
+    static_assert(3 * L::NM <= 32 * P_F4 * 4, "moments fit the warp's source buffer");
+    static_assert(3 * L::SL <= L::TABLE, "local coefficients fit the table");
+    static_assert(tree_warp_smem<P>() % 16 == 0 && (32 * P_F4 * 16) % 16 == 0, "16-byte aligned warp slices");
+    extern __shared__ __align__(16) unsigned char tree_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* buf = sbuf[warp];
+    float4* buf = reinterpret_cast<float4*>(tree_smem + warp * tree_warp_smem<P>());
     float* mbuf = reinterpret_cast<float*>(buf);
+    float* B = reinterpret_cast<float*>(tree_smem + warp * tree_warp_smem<P>() + 32 * P_F4 * 16);
     const long long nleaves = 1LL << A.D;
+    // the lane's local coefficients m = lane + 32 r, (a, b, c) packed 4 bits each
+    unsigned mabc[L::RL];
+#pragma unroll
+    for (int r = 0; r < L::RL; ++r) {
+        const int q = lane + 32 * r;
+        mabc[r] = q < L::NL ? kMi.abc[q] : 0u;
+    }
     for (;;) {
         long long leaf = 0;
         if (lane == 0) leaf = atomicAdd(A.counter, 1);
@@ -519,6 +612,14 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         const float4 tg = A.geo[nleaves - 1 + leaf];
         Acc<GRAD, false> acc;
         acc.zero();
+        LocalAcc<P> la;
+#pragma unroll
+        for (int r = 0; r < L::RL; ++r) {
+            la.x[r] = la.y[r] = la.z[r] = 0.f;
+            const int a = mabc[r] & 15, b = (mabc[r] >> 4) & 15, c = mabc[r] >> 8;
+            la.base[r] = (a * L::DIM + b) * L::DIM + c;
+        }
+        bool any_far = false;
         // depth-first walk; entry t of the stack lives in lane t
         int st = 0, sp = 1;  // the root
         while (sp > 0) {
@@ -532,32 +633,13 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
             const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
             const float rs = g.w + tg.w;
             const bool far = rs < A.theta * d && d - rs >= A.sep;
-            if (far && ne - ns >= A.m2p_min) {
+            if (far && ne - ns >= M2L_MIN) {
                 __syncwarp();
-                const float* src = A.mom + (size_t)id * 3 * NM;
-                for (int t = lane; t < 3 * NM; t += 32) mbuf[t] = src[t];
-                __syncwarp();
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    float w[11];
-#pragma unroll
-                    for (int q = 0; q < 11; ++q) w[q] = 0.f;
-                    const float rx = (h ? X.y : X.x) - g.x, ry = (h ? Y.y : Y.x) - g.y, rz = (h ? Z.y : Z.x) - g.z;
-                    m2p<P, GRAD>(rx, ry, rz, mbuf, w);
-                    if (h == 0) {
-                        acc.v[0].x += w[0], acc.v[1].x += w[1], acc.v[2].x += w[2];
-                        if constexpr (GRAD) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) acc.v[6 + q].x += w[3 + q];
-                        }
-                    } else {
-                        acc.v[0].y += w[0], acc.v[1].y += w[1], acc.v[2].y += w[2];
-                        if constexpr (GRAD) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) acc.v[6 + q].y += w[3 + q];
-                        }
-                    }
-                }
+                const float* src = A.mom + (size_t)id * 3 * L::NM;
+                for (int t = lane; t < 3 * L::NM; t += 32) mbuf[t] = src[t];
+                local_table<P>(B, -dx, -dy, -dz, lane);  // R0 = c_t - c_s; ends with a warp sync
+                local_accumulate<P>(la, B, mbuf);
+                any_far = true;
             } else if (far) {
                 direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z);
             } else if (level == A.D) {
@@ -570,6 +652,40 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 if (lane == sp) st = 2 * id + 2;
                 if (lane == sp + 1) st = 2 * id + 1;
                 sp += 2;
+            }
+        }
+        if (any_far) {
+            // the finished local coefficients, signed, into the table's storage
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < L::RL; ++r)
+                if (lane + 32 * r < L::NL) {
+                    const int a = mabc[r] & 15, b = (mabc[r] >> 4) & 15, c = mabc[r] >> 8;
+                    const int i = (a * L::DL + b) * L::DL + c;
+                    const float sg = ((a + b + c) & 1) ? -1.f : 1.f;
+                    B[i] = sg * la.x[r], B[L::SL + i] = sg * la.y[r], B[2 * L::SL + i] = sg * la.z[r];
+                }
+            __syncwarp();
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                float w[11];
+#pragma unroll
+                for (int q = 0; q < 11; ++q) w[q] = 0.f;
+                const float yx = (h ? X.y : X.x) - tg.x, yy = (h ? Y.y : Y.x) - tg.y, yz = (h ? Z.y : Z.x) - tg.z;
+                local_eval<P, GRAD>(yx, yy, yz, B, w);
+                if (h == 0) {
+                    acc.v[0].x += w[0], acc.v[1].x += w[1], acc.v[2].x += w[2];
+                    if constexpr (GRAD) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc.v[6 + q].x += w[3 + q];
+                    }
+                } else {
+                    acc.v[0].y += w[0], acc.v[1].y += w[1], acc.v[2].y += w[2];
+                    if constexpr (GRAD) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) acc.v[6 + q].y += w[3 + q];
+                    }
+                }
             }
         }
         // epilogue: u = u / (4 pi), J = ([S x] - 3 G') / (4 pi), G'_zz = -G'_xx - G'_yy
@@ -597,6 +713,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 J[8 * n + o] = (-3.f * Gzz) * f;
             }
         }
+        __syncwarp();  // the table is read by every lane before the next leaf overwrites it
     }
 }
 
@@ -625,7 +742,6 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     A.D = w.D;
     A.theta = theta;
     A.sep = (float)(RHO_FAR * (double)sigma);
-    A.m2p_min = m2p_min(P);
     const double s = sigma;
     A.nc.inv_s2 = (float)(1.0 / (s * s));
     A.nc.inv_s3 = (float)(1.0 / (s * s * s));
@@ -638,12 +754,15 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     auto kern = grad ? tree_eval_kernel<P, true> : tree_eval_kernel<P, false>;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TREE_WARPS * 32, 0);
+    const size_t smem = TREE_WARPS * tree_warp_smem<P>();
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TREE_WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     const long long want = (leaves + TREE_WARPS - 1) / TREE_WARPS;
     const long long blocks = std::min<long long>(want, (long long)std::max(per_sm, 1) * sm_count());
     trace_launch();
-    kern<<<(unsigned)blocks, TREE_WARPS * 32, 0, st>>>(A);
+    kern<<<(unsigned)blocks, TREE_WARPS * 32, smem, st>>>(A);
     return cudaGetLastError();
 }
 
