@@ -538,6 +538,7 @@ __device__ __forceinline__ void local_eval(float yx, float yy, float yz, const f
 struct TreeArgs {
     const float4* psrc;  // sorted packed sources [n][5]
     const float4* geo;   // per node (cx, cy, cz, r)
+    const float4* box;   // per node (lo, hi)
     const float* mom;    // per node [3][NM] scaled moments
     const int* idx;      // sorted position -> particle index
     long long n;
@@ -549,10 +550,13 @@ struct TreeArgs {
     float* grad;
 };
 
-// The direct sum over the sorted run [s, e) staged through the warp's buffer.
+// The direct sum over the sorted run [s, e) staged through the warp's buffer.  With
+// NEAR, a source at least 7 sigma from the target leaf's box takes the point-vortex
+// form for the whole warp (a warp-uniform test on the broadcast source), and only
+// the others evaluate the regularised kernel pair by pair.
 template <bool GRAD, bool NEAR>
 __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs& A, long long s, long long e,
-                                           float4* buf, int lane, f2 X, f2 Y, f2 Z)
+                                           float4* buf, int lane, f2 X, f2 Y, f2 Z, float4 blo, float4 bhi)
 {
     const Own own{};
     for (long long c0 = s; c0 < e; c0 += 32) {
@@ -565,7 +569,22 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
         }
         __syncwarp();
 #pragma unroll 1
-        for (int j = 0; j < cnt; ++j) particle_source<GRAD, false, NEAR>(acc, buf + j * P_F4, X, Y, Z, A.nc, own);
+        for (int j = 0; j < cnt; ++j) {
+            const float4* q = buf + j * P_F4;
+            if constexpr (NEAR) {
+                const float4 q0 = q[0], q1 = q[1];
+                const float sx = -q0.x, sy = -q0.z, sz = -q1.x;
+                const float ex = fmaxf(fmaxf(blo.x - sx, sx - bhi.x), 0.f);
+                const float ey = fmaxf(fmaxf(blo.y - sy, sy - bhi.y), 0.f);
+                const float ez = fmaxf(fmaxf(blo.z - sz, sz - bhi.z), 0.f);
+                if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) >= A.nc.far2)
+                    particle_source<GRAD, false, false>(acc, q, X, Y, Z, A.nc, own);
+                else
+                    particle_source<GRAD, false, true>(acc, q, X, Y, Z, A.nc, own);
+            } else {
+                particle_source<GRAD, false, false>(acc, q, X, Y, Z, A.nc, own);
+            }
+        }
     }
 }
 
@@ -610,6 +629,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         const float4 p1 = A.psrc[(v1 ? i1 : s) * P_F4], p1z = A.psrc[(v1 ? i1 : s) * P_F4 + 1];
         const f2 X = make_float2(-p0.x, -p1.x), Y = make_float2(-p0.z, -p1.z), Z = make_float2(-p0z.x, -p1z.x);
         const float4 tg = A.geo[nleaves - 1 + leaf];
+        const float4 blo = A.box[2 * (nleaves - 1 + leaf)], bhi = A.box[2 * (nleaves - 1 + leaf) + 1];
         Acc<GRAD, false> acc;
         acc.zero();
         LocalAcc<P> la;
@@ -641,12 +661,12 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 local_accumulate<P>(la, B, mbuf);
                 any_far = true;
             } else if (far) {
-                direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z);
+                direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi);
             } else if (level == A.D) {
                 if (d - rs >= A.sep)
-                    direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z);
+                    direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi);
                 else
-                    direct_run<GRAD, true>(acc, A, ns, ne, buf, lane, X, Y, Z);
+                    direct_run<GRAD, true>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi);
             } else {
                 // push the right child first so the left one is walked first
                 if (lane == sp) st = 2 * id + 2;
@@ -736,6 +756,7 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     TreeArgs A{};
     A.psrc = psrc;
     A.geo = geo;
+    A.box = box;
     A.mom = mom;
     A.idx = reinterpret_cast<const int*>(ws + w.idx1);
     A.n = n;
