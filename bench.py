@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=None,
                     help="seconds of oracle work per CPU-baseline sample (default 12; reference arm: 60 s over all steps)")
+    ap.add_argument("--no-tree", action="store_true", help="skip the informative treecode timing")
     ap.add_argument("--part", choices=["aic", "wake", "tree", "rotor"], default=None,
                     help="time one component alone (for profiling; prints a text line, not the JSON contract)")
     return ap.parse_args()
@@ -247,6 +248,13 @@ def oracle_rate(w, seconds, cores):
             rate = k * (n - 1) / dt
             return rate, k, dt
         k = min(n, int(k * max(2.0, seconds / max(dt, 1e-3) * 0.6)))
+
+
+def oracle_values(w, idx):
+    """The FP64 oracle's u and grad u at the sampled particles idx (cpu_baseline leg)."""
+    import oracle
+
+    return oracle.p2p(w.pos, w.strength, w.pos[idx], w.sigma)
 
 
 def oracle_threads_default(cores):
@@ -468,25 +476,20 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e2e_ms / ksteps}
 
-    # error at the stated tolerance, on a sample (outside every timed region)
-    err = None
+    # error at the stated tolerance, on a sample (outside every timed region): the GPU
+    # side here, the FP64 reference values in the cpu_baseline leg below
+    err_gpu = None
+    err_idx = synth.sample_targets(11, n, 96)
     if rank == 0:
         try:
-            import oracle
-
-            idx = synth.sample_targets(11, n, 96)
             pos, strn = api.pack_state(*make_state(), vol)
             u, gr = api.induce(pos, strn, pos, w.sigma, compensated=True)
             up, gp = api.induce(pos, strn, pos, w.sigma, compensated=False)
-            ru, rJ = oracle.p2p(w.pos, w.strength, w.pos[idx], w.sigma)
-            rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-            U = lambda t: t[:, idx].double().cpu().numpy().T
-            Jm = lambda t: t[:, idx].double().cpu().numpy().T.reshape(-1, 3, 3)
-            err = {"sample_targets": len(idx), "compensated": {"u": rel(U(u), ru), "grad_u": rel(Jm(gr), rJ)},
-                   "plain": {"u": rel(U(up), ru), "grad_u": rel(Jm(gp), rJ)}, "tolerance": {"compensated": 2e-6,
-                                                                                              "plain": 1e-4}}
+            U = lambda t: t[:, err_idx].double().cpu().numpy().T
+            Jm = lambda t: t[:, err_idx].double().cpu().numpy().T.reshape(-1, 3, 3)
+            err_gpu = (U(u), Jm(gr), U(up), Jm(gp))
         except Exception as ex:  # the error report is informative, never fatal
-            err = {"unavailable": str(ex)[:200]}
+            err_gpu = str(ex)[:200]
 
     # the wake panel -> particle conversion (Eq. 6-8), outside the timed step: the edges of
     # 2,000 wake panel rows of the 4-blade hover rotor, n_tip = 4 (informative)
@@ -519,7 +522,49 @@ def run_ours(args):
         except Exception as ex:  # informative, never fatal
             wake = {"unavailable": str(ex)[:200]}
 
+    # the treecode (the O(n log n) variant, outside the timed step) on the 1,000,000-particle
+    # BVI wake against the direct plain sum of the same wake (informative)
+    tree = None
+    wt = tree_idx = tree_gpu = None
+    if rank == 0 and not args.no_tree:
+        try:
+            wt = synth.make(3)
+            Pt = torch.from_numpy(wt.pos).to(dev)
+            St = torch.from_numpy(wt.strength).to(dev)
+            tws = api.Workspace(dev)
+            st = torch.cuda.current_stream()
+
+            def timed(fn, reps):
+                fn()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(reps):
+                    fn()
+                e1.record(st)
+                e1.synchronize()
+                return e0.elapsed_time(e1) / reps
+
+            out = {}
+            tms = timed(lambda: out.__setitem__("t", api.tree_induce(Pt, St, wt.sigma, theta=0.5, order=4, ws=tws)), 3)
+            dms = timed(lambda: api.induce(Pt, St, Pt, wt.sigma, compensated=False, ws=tws), 1)
+            ut, gt = out["t"]
+            tree_idx = synth.sample_targets(11, wt.n, 32)
+            tree_gpu = (ut.cpu().numpy().T[tree_idx].astype(np.float64),
+                        gt.cpu().numpy().T[tree_idx].reshape(-1, 3, 3).astype(np.float64))
+            tree = {"particles": wt.n, "theta": 0.5, "order": 4, "ms": tms, "direct_plain_ms": dms,
+                    "speedup": dms / tms}
+            del Pt, St, tws, out, ut, gt
+        except Exception as ex:  # informative, never fatal
+            tree = {"unavailable": str(ex)[:200]}
+
+    # the cpu_baseline leg: the FP64 oracle on the host cores, timed, and the same oracle's
+    # values at the sampled targets of the error reports (the only place the main arm
+    # runs it)
     cpu = None
+    err = {"unavailable": "the FP64 reference values come from the cpu_baseline leg (skipped)"}
+    rel = lambda a_, b_: float(np.linalg.norm(a_ - b_) / np.linalg.norm(b_))
     if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
         cores = host_cores()
         rate, k, dt = oracle_rate(w, 12.0 if args.cpu_seconds is None else args.cpu_seconds, cores)
@@ -529,6 +574,21 @@ def run_ours(args):
                "sample": f"{k} sampled targets x all {n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)",
                "single_thread": {"value": rate1, "unit": UNIT,
                                  "sample": f"{k1} sampled targets x all {n:,} sources ({dt1:.1f} s)"}}
+        try:
+            ru, rJ = oracle_values(w, err_idx)
+            if isinstance(err_gpu, tuple):
+                cu, cg, pu, pg = err_gpu
+                err = {"sample_targets": len(err_idx), "compensated": {"u": rel(cu, ru), "grad_u": rel(cg, rJ)},
+                       "plain": {"u": rel(pu, ru), "grad_u": rel(pg, rJ)},
+                       "tolerance": {"compensated": 2e-6, "plain": 1e-4}}
+            else:
+                err = {"unavailable": str(err_gpu)}
+            if tree_gpu is not None and "unavailable" not in tree:
+                tu, tJ = oracle_values(wt, tree_idx)
+                tree["error_vs_oracle"] = {"sample_targets": len(tree_idx), "u": rel(tree_gpu[0], tu),
+                                           "grad_u": rel(tree_gpu[1], tJ)}
+        except Exception as ex:  # informative, never fatal
+            err = {"unavailable": str(ex)[:200]}
 
     if dist is not None:
         dist.barrier()
@@ -544,7 +604,7 @@ def run_ours(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                        "parallelism": "replicas" if ws_n > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_total),
-            "clocks": clk, "plain": plain, "error": err, "wake_convert": wake,
+            "clocks": clk, "plain": plain, "error": err, "wake_convert": wake, "treecode": tree,
             "kernel_ms": {"sweep_grad": [nl, sms_ms], "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
                           "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL])},
         }
