@@ -54,6 +54,7 @@ namespace {
 
 constexpr int TREE_LEAF = 64;        // particles per leaf at most: one warp's targets
 constexpr int TREE_WARPS = 8;        // warps per traversal block
+constexpr int TREE_STAGE = 64;       // sources staged in shared memory at a time: a whole leaf
 constexpr int TREE_MAX_P = 4;        // highest expansion order
 constexpr int BOUNDS_BLOCKS = 1024;  // partial boxes of the bounding-box pass
 constexpr int MORTON_BITS = 21;      // per axis
@@ -559,13 +560,17 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
                                            float4* buf, int lane, f2 X, f2 Y, f2 Z, float4 blo, float4 bhi)
 {
     const Own own{};
-    for (long long c0 = s; c0 < e; c0 += 32) {
-        const int cnt = (int)min(32LL, e - c0);
+    for (long long c0 = s; c0 < e; c0 += TREE_STAGE) {
+        const int cnt = (int)min((long long)TREE_STAGE, e - c0);
         __syncwarp();
-        if (lane < cnt) {
-            const float4* src = A.psrc + (c0 + lane) * P_F4;
 #pragma unroll
-            for (int f = 0; f < P_F4; ++f) buf[lane * P_F4 + f] = src[f];
+        for (int h = 0; h < TREE_STAGE / 32; ++h) {
+            const int t = lane + 32 * h;
+            if (t < cnt) {
+                const float4* src = A.psrc + (c0 + t) * P_F4;
+#pragma unroll
+                for (int f = 0; f < P_F4; ++f) buf[t * P_F4 + f] = src[f];
+            }
         }
         __syncwarp();
 #pragma unroll 1
@@ -594,21 +599,21 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
 template <int P>
 __host__ __device__ constexpr size_t tree_warp_smem()
 {
-    return (32 * P_F4 * 16 + (size_t)Local<P>::TABLE * 4 + 15) / 16 * 16;
+    return (TREE_STAGE * P_F4 * 16 + (size_t)Local<P>::TABLE * 4 + 15) / 16 * 16;
 }
 
 template <int P, bool GRAD>
 __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
 {
     using L = Local<P>;
-    static_assert(3 * L::NM <= 32 * P_F4 * 4, "moments fit the warp's source buffer");
+    static_assert(3 * L::NM <= TREE_STAGE * P_F4 * 4, "moments fit the warp's source buffer");
     static_assert(3 * L::SL <= L::TABLE, "local coefficients fit the table");
-    static_assert(tree_warp_smem<P>() % 16 == 0 && (32 * P_F4 * 16) % 16 == 0, "16-byte aligned warp slices");
+    static_assert(tree_warp_smem<P>() % 16 == 0 && (TREE_STAGE * P_F4 * 16) % 16 == 0, "16-byte aligned warp slices");
     extern __shared__ __align__(16) unsigned char tree_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* buf = reinterpret_cast<float4*>(tree_smem + warp * tree_warp_smem<P>());
     float* mbuf = reinterpret_cast<float*>(buf);
-    float* B = reinterpret_cast<float*>(tree_smem + warp * tree_warp_smem<P>() + 32 * P_F4 * 16);
+    float* B = reinterpret_cast<float*>(tree_smem + warp * tree_warp_smem<P>() + TREE_STAGE * P_F4 * 16);
     const long long nleaves = 1LL << A.D;
     // the lane's local coefficients m = lane + 32 r, (a, b, c) packed 4 bits each
     unsigned mabc[L::RL];
