@@ -71,6 +71,8 @@ typedef enum vpm_status {
 #define VPM_OP_WAKE_ROW 8
 #define VPM_OP_LOADS 9
 #define VPM_OP_TREE 10
+#define VPM_OP_RHS_TREE 11
+#define VPM_OP_STEP_TREE 12
 
 /* Largest particle / target / segment count accepted (int32 indexing). */
 #define VPM_MAX_ITEMS (1 << 30)
@@ -108,6 +110,7 @@ vpm_status vpm_device_error(int* code);
  *   VPM_OP_WAKE_CONVERT: n_src edges;  VPM_OP_WAKE_ROW: n_src panels of the row
  *   VPM_OP_LOADS:     m_seg bound segments, n_tgt panels
  *   VPM_OP_TREE:      n_src particles (vpm_tree_induce)
+ *   VPM_OP_RHS_TREE, VPM_OP_STEP_TREE: n_src particles, m_seg segments
  * `flags` as passed to the operation.  Host-only; does not launch. */
 vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_seg, int flags, size_t* bytes);
 
@@ -141,6 +144,22 @@ vpm_status vpm_induce(const float* src_pos_d, const float* src_str_d, int64_t n_
  *   0 <= theta <= 1; order in {2, 3, 4}.  Workspace: VPM_OP_TREE (n_src = n). */
 vpm_status vpm_tree_induce(const float* pos_d, const float* str_d, int64_t n, float sigma, float theta, int order,
                            float* u_d, float* grad_u_d, void* ws_d, size_t ws_bytes, void* stream);
+
+/* The right-hand side of Eq. 4-5 (as vpm_rhs) and one RK3 step (as vpm_step) with the
+ * particle-particle u and grad u from the treecode of vpm_tree_induce (theta, order as
+ * there) instead of the direct sweep; the segments' u and grad u still come from the
+ * direct segment sweep (flags: VPM_COMPENSATED applies to it), Vreman's eddy viscosity
+ * and the stretching are formed in FP64 from the summed u and grad u (the transposed
+ * stretching from J^T Gamma, not pair by pair), and the PSE term is summed over the
+ * pairs within 7 sigma found by a walk of the same tree.  theta = 0 gives the direct
+ * sums.  For particle counts where the direct sweep's O(n^2) cost dominates (1e6 and
+ * more).  Workspace: VPM_OP_RHS_TREE / VPM_OP_STEP_TREE (n_src = n, m_seg = m). */
+vpm_status vpm_rhs_tree(const float* pos_d, const float* str_d, int64_t n, const float* seg_a_d, const float* seg_b_d,
+                        int64_t m, const vpm_params* prm, float theta, int order, float* dxdt_d, float* dGdt_d,
+                        float* nu_t_d, void* ws_d, size_t ws_bytes, void* stream);
+vpm_status vpm_step_tree(double* x_d, double* G_d, const float* vol_d, int64_t n, const float* seg_a_d,
+                         const float* seg_b_d, int64_t m, const vpm_params* prm, float theta, int order, double dt,
+                         void* ws_d, size_t ws_bytes, void* stream);
 
 /* ---- Sec. II.A: straight vortex segments with a Vatistas core ------------
  * The finite-segment Biot-Savart law with |r1 x r2|^2 replaced by

@@ -34,6 +34,8 @@ VPM_OP_WAKE_CONVERT = 7
 VPM_OP_WAKE_ROW = 8
 VPM_OP_LOADS = 9
 VPM_OP_TREE = 10
+VPM_OP_RHS_TREE = 11
+VPM_OP_STEP_TREE = 12
 
 VPM_TRACE_ALL = 0
 VPM_TRACE_SWEEP = 1
@@ -87,6 +89,9 @@ SIGNATURES = {
     "vpm_rhs": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _P, _P, _P, _P, _SZ, _P]),
     "vpm_pack_state": (_INT, [_P, _P, _P, _I64, _P, _P, _P]),
     "vpm_step": (_INT, [_P, _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _D, _P, _SZ, _P]),
+    "vpm_rhs_tree": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _F, _INT, _P, _P, _P, _P, _SZ,
+                            _P]),
+    "vpm_step_tree": (_INT, [_P, _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _F, _INT, _D, _P, _SZ, _P]),
     "aic_build": (_INT, [_P, _P, _P, _INT, _F, _INT, _P, _P, _P, _P, _P]),
     "aic_solve": (_INT, [_P, _P, _P, _INT, _D, _INT, ctypes.POINTER(_INT), ctypes.POINTER(_D), _P, _SZ, _P]),
     "vpm_induce_backward": (_INT, [_P, _P, _I64, _P, _I64, _F, _INT, _P, _P, _P, _P, _SZ, _P]),

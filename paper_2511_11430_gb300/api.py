@@ -184,6 +184,24 @@ def rhs(pos, strength, seg_a, seg_b, params: Params, ws=None):
     return dxdt, dGdt, nut
 
 
+def rhs_tree(pos, strength, seg_a, seg_b, params: Params, theta: float = 0.5, order: int = 4, ws=None):
+    """As rhs, with the particle-particle u and grad u from the treecode (vpm_rhs_tree)."""
+    _need(pos, "pos", torch.float32, (4,))
+    _need(strength, "strength", torch.float32, (4,))
+    sa, sb, m = _segs(seg_a, seg_b)
+    n = pos.shape[0]
+    dev = pos.device
+    dxdt = torch.empty((3, n), dtype=torch.float32, device=dev)
+    dGdt = torch.empty((3, n), dtype=torch.float32, device=dev)
+    nut = torch.empty((n,), dtype=torch.float32, device=dev)
+    cp = params.to_c()
+    w = _ws(ws, workspace_size(_lib.VPM_OP_RHS_TREE, n, 0, m, cp.flags), dev)
+    check(_lib.load().vpm_rhs_tree(_void(pos), _void(strength), n, _void(sa), _void(sb), m, ctypes.byref(cp),
+                                   float(theta), int(order), _void(dxdt), _void(dGdt), _void(nut), _void(w),
+                                   w.numel(), _stream()))
+    return dxdt, dGdt, nut
+
+
 def pack_state(x, G, vol, pos=None, strength=None):
     """FP32 packed particles pos [n, 4], strength [n, 4] from the FP64 state x, G [3, n] and vol [n]."""
     _need(x, "x", torch.float64)
@@ -212,6 +230,22 @@ def step(x, G, vol, seg_a, seg_b, params: Params, dt: float, ws=None):
     w = _ws(ws, nb, x.device)
     check(_lib.load().vpm_step(_void(x), _void(G), _void(vol), n, _void(sa), _void(sb), m, ctypes.byref(cp),
                                float(dt), _void(w), w.numel(), _stream()))
+    return x, G
+
+
+def step_tree(x, G, vol, seg_a, seg_b, params: Params, dt: float, theta: float = 0.5, order: int = 4, ws=None):
+    """As step, with the treecode right-hand side (vpm_step_tree)."""
+    _need(x, "x", torch.float64)
+    _need(G, "G", torch.float64)
+    _need(vol, "vol", torch.float32)
+    if x.dim() != 2 or x.shape[0] != 3 or G.shape != x.shape or vol.shape != (x.shape[1],):
+        raise ValueError("x and G must be [3, n] and vol [n]")
+    sa, sb, m = _segs(seg_a, seg_b)
+    n = x.shape[1]
+    cp = params.to_c()
+    w = _ws(ws, workspace_size(_lib.VPM_OP_STEP_TREE, n, 0, m, cp.flags), x.device)
+    check(_lib.load().vpm_step_tree(_void(x), _void(G), _void(vol), n, _void(sa), _void(sb), m, ctypes.byref(cp),
+                                    float(theta), int(order), float(dt), _void(w), w.numel(), _stream()))
     return x, G
 
 

@@ -77,6 +77,19 @@ StepWs step_layout(int64_t n, int64_t m, bool comp, bool classic)
     return s;
 }
 
+// The buffers vpm_step_tree adds after the treecode right-hand side's workspace.
+size_t tree_step_extra(int64_t n)
+{
+    Carve cv;
+    cv.take((size_t)n * 16);
+    cv.take((size_t)n * 16);
+    cv.take((size_t)n * 3 * sizeof(float));
+    cv.take((size_t)n * 3 * sizeof(float));
+    cv.take((size_t)n * 3 * sizeof(double));
+    cv.take((size_t)n * 3 * sizeof(double));
+    return cv.off + 256;  // room for aligning the first buffer after the right-hand side's
+}
+
 bool overflow_guard(const SweepPlan& p)
 {
     // keep tot * B < 2^62 for the 64-bit stream-K arithmetic
@@ -168,6 +181,14 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
         REQUIRE(n_src >= 1, "a wake row needs at least one panel");
         *bytes = wake_workspace(3 * n_src + 1, true);
         break;
+    case VPM_OP_RHS_TREE:
+    case VPM_OP_STEP_TREE: {
+        TreeRhsWs r;
+        const cudaError_t e = tree_rhs_layout(n_src, m_seg, comp, r);
+        if (e != cudaSuccess) return cuda_fail(e, "vpm_workspace_size: sort scratch query");
+        *bytes = r.bytes + (op == VPM_OP_STEP_TREE ? tree_step_extra(n_src) : 0);
+        break;
+    }
     case VPM_OP_TREE: {
         const cudaError_t e = tree_workspace(n_src, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "vpm_workspace_size(VPM_OP_TREE): sort scratch query");
@@ -374,6 +395,80 @@ vpm_status vpm_step(double* x_d, double* G_d, const float* vol_d, int64_t n, con
         e = run_rk3_stage(k, dt, x_d, G_d, qx, qG, dxdt, dGdt, vol_d, (int)n, k < 2 ? pos : nullptr,
                           k < 2 ? str : nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "vpm_step");
+    }
+    return ok();
+}
+
+vpm_status vpm_rhs_tree(const float* pos_d, const float* str_d, int64_t n, const float* seg_a_d, const float* seg_b_d,
+                        int64_t m, const vpm_params* prm, float theta, int order, float* dxdt_d, float* dGdt_d,
+                        float* nu_t_d, void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_params(prm)) != VPM_OK) return s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    if ((s = check_count(m, "m")) != VPM_OK) return s;
+    REQUIRE(theta >= 0.f && theta <= 1.f, "theta must lie in [0, 1] (got %g)", (double)theta);
+    REQUIRE(order >= 2 && order <= 4, "order must be 2, 3 or 4 (got %d)", order);
+    if (n == 0) return ok();
+    REQUIRE(pos_d && str_d && aligned16(pos_d) && aligned16(str_d), "pos/str must be 16-byte aligned device pointers");
+    REQUIRE(dxdt_d && dGdt_d && aligned4(dxdt_d) && aligned4(dGdt_d), "dxdt/dGdt must be device pointers");
+    REQUIRE(m == 0 || (seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d)),
+            "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
+    TreeRhsWs r;
+    cudaError_t e = tree_rhs_layout(n, m, prm->flags & VPM_COMPENSATED, r);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_rhs_tree: sort scratch query");
+    if (!overflow_guard(r.seg_plan)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
+    if (!ws_d || ws_bytes < r.bytes || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", r.bytes, ws_bytes);
+    if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
+    e = run_tree_rhs(r, static_cast<char*>(ws_d), pos_d, str_d, n, seg_a_d, seg_b_d, m, prm, theta, order, dxdt_d,
+                     dGdt_d, nu_t_d, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_rhs_tree");
+}
+
+vpm_status vpm_step_tree(double* x_d, double* G_d, const float* vol_d, int64_t n, const float* seg_a_d,
+                         const float* seg_b_d, int64_t m, const vpm_params* prm, float theta, int order, double dt,
+                         void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_params(prm)) != VPM_OK) return s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    if ((s = check_count(m, "m")) != VPM_OK) return s;
+    REQUIRE(isfinite(dt), "dt must be finite");
+    REQUIRE(theta >= 0.f && theta <= 1.f, "theta must lie in [0, 1] (got %g)", (double)theta);
+    REQUIRE(order >= 2 && order <= 4, "order must be 2, 3 or 4 (got %d)", order);
+    if (n == 0) return ok();
+    REQUIRE(x_d && G_d && vol_d && aligned8(x_d) && aligned8(G_d) && aligned4(vol_d),
+            "x/G/vol must be aligned device pointers");
+    REQUIRE(m == 0 || (seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d)),
+            "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
+    TreeRhsWs r;
+    cudaError_t e = tree_rhs_layout(n, m, prm->flags & VPM_COMPENSATED, r);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_step_tree: sort scratch query");
+    if (!overflow_guard(r.seg_plan)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
+    const size_t need = r.bytes + tree_step_extra(n);
+    if (!ws_d || ws_bytes < need || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", need, ws_bytes);
+    if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
+    char* ws = static_cast<char*>(ws_d);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the step's own buffers after the right-hand side's
+    Carve cv;
+    cv.off = r.bytes;
+    float* pos = reinterpret_cast<float*>(ws + cv.take((size_t)n * 16));
+    float* str = reinterpret_cast<float*>(ws + cv.take((size_t)n * 16));
+    float* dxdt = reinterpret_cast<float*>(ws + cv.take((size_t)n * 3 * sizeof(float)));
+    float* dGdt = reinterpret_cast<float*>(ws + cv.take((size_t)n * 3 * sizeof(float)));
+    double* qx = reinterpret_cast<double*>(ws + cv.take((size_t)n * 3 * sizeof(double)));
+    double* qG = reinterpret_cast<double*>(ws + cv.take((size_t)n * 3 * sizeof(double)));
+    e = run_cast_state(x_d, G_d, vol_d, (int)n, pos, str, st);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_step_tree");
+    for (int k = 0; k < 3; ++k) {
+        e = run_tree_rhs(r, ws, pos, str, n, seg_a_d, seg_b_d, m, prm, theta, order, dxdt, dGdt, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "vpm_step_tree");
+        e = run_rk3_stage(k, dt, x_d, G_d, qx, qG, dxdt, dGdt, vol_d, (int)n, k < 2 ? pos : nullptr,
+                          k < 2 ? str : nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "vpm_step_tree");
     }
     return ok();
 }

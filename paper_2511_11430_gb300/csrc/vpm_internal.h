@@ -115,6 +115,14 @@ vpm_status run_wake_convert_row(const double* U, const double* D, const double* 
                                 int n_tip, int n_shed, double* x, double* G, long long ld, long long* n_out, char* ws,
                                 cudaStream_t st, const char** msg);
 cudaError_t tree_workspace(long long n, size_t* bytes);
+struct TreeRhsWs {
+    size_t tree, up, Jp, us, Js, sp, sg, nut, counter, seg, bytes;
+    SweepPlan seg_plan;
+};
+cudaError_t tree_rhs_layout(long long n, long long m, bool comp, TreeRhsWs& r);
+cudaError_t run_tree_rhs(const TreeRhsWs& r, char* ws, const float* pos, const float* str, long long n,
+                         const float* seg_a, const float* seg_b, long long m, const vpm_params* prm, float theta,
+                         int order, float* dxdt, float* dGdt, float* nu_t, cudaStream_t st);
 cudaError_t run_tree_induce(const float* pos, const float* str, long long n, float sigma, float theta, int order,
                             float* u, float* grad_u, char* ws, cudaStream_t st);
 size_t aic_workspace(int n);

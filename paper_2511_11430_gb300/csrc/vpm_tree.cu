@@ -792,6 +792,159 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Right-hand side of Eq. 4-5 with the treecode for the particle-particle sums.
+// ---------------------------------------------------------------------------
+
+// Per particle (original order): u, J from the tree (up, Jp) plus the segments (us,
+// Js, or none), then Vreman's eddy viscosity, the stretching and dx/dt in FP64, as
+// the direct sweep's epilogue forms them.
+__global__ void tree_rhs_epilogue_kernel(int n, const float* __restrict__ up, const float* __restrict__ Jp,
+                                         const float* __restrict__ us, const float* __restrict__ Js,
+                                         const float4* __restrict__ str, float sigma, float c_v, float ux_inf,
+                                         float uy_inf, float uz_inf, int classic, int check, int* dev_err,
+                                         float* __restrict__ dxdt, float* __restrict__ dGdt, float* __restrict__ nu_t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double u[3], J[9];
+    for (int a = 0; a < 3; ++a) u[a] = (double)up[(size_t)a * n + i] + (us ? (double)us[(size_t)a * n + i] : 0.0);
+    for (int c = 0; c < 9; ++c) J[c] = (double)Jp[(size_t)c * n + i] + (Js ? (double)Js[(size_t)c * n + i] : 0.0);
+    const float4 G4 = str[i];
+    const double G[3] = {G4.x, G4.y, G4.z};
+    // Vreman: alpha = J^T, beta = Delta^2 J J^T, Delta = sigma
+    double bt[3][3], aa = 0.0;
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            double v = 0.0;
+            for (int m = 0; m < 3; ++m) v += J[3 * p + m] * J[3 * q + m];
+            bt[p][q] = v * (double)sigma * (double)sigma;
+        }
+    for (int c = 0; c < 9; ++c) aa += J[c] * J[c];
+    const double B = bt[0][0] * bt[1][1] - bt[0][1] * bt[0][1] + bt[0][0] * bt[2][2] - bt[0][2] * bt[0][2] +
+                     bt[1][1] * bt[2][2] - bt[1][2] * bt[1][2];
+    const double nut = (aa > 0.0 && B > 0.0) ? (double)c_v * sqrt(B / aa) : 0.0;
+    double st[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        for (int c = 0; c < 3; ++c) v += classic ? J[3 * a + c] * G[c] : J[3 * c + a] * G[c];
+        st[a] = v;
+    }
+    dxdt[i] = (float)(u[0] + ux_inf);
+    dxdt[(size_t)n + i] = (float)(u[1] + uy_inf);
+    dxdt[2 * (size_t)n + i] = (float)(u[2] + uz_inf);
+    for (int a = 0; a < 3; ++a) dGdt[(size_t)a * n + i] = (float)st[a];
+    nu_t[i] = (float)nut;
+    if (check && !isfinite(u[0] + u[1] + u[2] + st[0] + st[1] + st[2] + nut)) atomicOr(dev_err, DEV_ERR_NONFINITE);
+}
+
+// Sorted copies for the PSE walk: (x, y, z, volume) and (Gamma, nu_t).
+__global__ void tree_pse_gather_kernel(const float4* __restrict__ pos, const float4* __restrict__ str,
+                                       const float* __restrict__ nu_t, const int* __restrict__ idx, int n,
+                                       float4* __restrict__ sp, float4* __restrict__ sg)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int j = idx[k];
+    sp[k] = pos[j];
+    const float4 g = str[j];
+    sg[k] = make_float4(g.x, g.y, g.z, nu_t[j]);
+}
+
+struct PseArgs {
+    const float4* sp;   // sorted (x, y, z, v)
+    const float4* sg;   // sorted (Gamma, nu_t)
+    const float4* geo;  // the tree of the same positions
+    const int* idx;
+    long long n;
+    int D;
+    float sep, cut2, inv2s2, nu, pref;
+    int* counter;
+    float* dGdt;        // [3][n], original order: the PSE term is added
+};
+
+// Particle strength exchange (Eq. 5) by a walk of the same tree: one warp per target
+// leaf visits the nodes whose sphere comes within 7 sigma of the leaf's and sums the
+// Degond-Mas-Gallic pairs of the leaves it reaches (the pairs beyond 7 sigma, whose
+// Gaussian is below 3e-11 of its peak, are skipped, as the direct PSE does).
+__global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
+{
+    __shared__ float4 sbuf[TREE_WARPS][2 * TREE_STAGE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* bp = sbuf[warp];
+    float4* bg = sbuf[warp] + TREE_STAGE;
+    const long long nleaves = 1LL << A.D;
+    for (;;) {
+        long long leaf = 0;
+        if (lane == 0) leaf = atomicAdd(A.counter, 1);
+        leaf = __shfl_sync(0xffffffffu, leaf, 0);
+        if (leaf >= nleaves) break;
+        const long long s = run_begin(leaf, A.n, A.D), e = run_begin(leaf + 1, A.n, A.D);
+        const long long i0 = s + lane, i1 = s + 32 + lane;
+        const bool v0 = i0 < e, v1 = i1 < e;
+        const float4 p0 = A.sp[v0 ? i0 : s], g0 = A.sg[v0 ? i0 : s];
+        const float4 p1 = A.sp[v1 ? i1 : s], g1 = A.sg[v1 ? i1 : s];
+        const float base0 = A.nu + 0.5f * g0.w, base1 = A.nu + 0.5f * g1.w;
+        const float4 tg = A.geo[nleaves - 1 + leaf];
+        float a0x = 0.f, a0y = 0.f, a0z = 0.f, a1x = 0.f, a1y = 0.f, a1z = 0.f;
+        int st = 0, sp = 1;  // the stack, one entry per lane
+        while (sp > 0) {
+            const int id = __shfl_sync(0xffffffffu, st, sp - 1);
+            --sp;
+            const int level = 31 - __clz(id + 1);
+            const float4 g = A.geo[id];
+            const float dx = g.x - tg.x, dy = g.y - tg.y, dz = g.z - tg.z;
+            const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            if (d - (g.w + tg.w) >= A.sep) continue;  // every pair beyond 7 sigma
+            if (level < A.D) {
+                if (lane == sp) st = 2 * id + 2;
+                if (lane == sp + 1) st = 2 * id + 1;
+                sp += 2;
+                continue;
+            }
+            const long long k = (long long)id + 1 - (1LL << level);
+            const long long ns = run_begin(k, A.n, level), ne = run_begin(k + 1, A.n, level);
+            const int cnt = (int)(ne - ns);  // a leaf: at most TREE_STAGE
+            __syncwarp();
+#pragma unroll
+            for (int h = 0; h < TREE_STAGE / 32; ++h) {
+                const int t = lane + 32 * h;
+                if (t < cnt) bp[t] = A.sp[ns + t], bg[t] = A.sg[ns + t];
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int j = 0; j < cnt; ++j) {
+                const float4 pj = bp[j], gj = bg[j];
+                const float ntj = gj.w;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float4 pi = h ? p1 : p0, gi = h ? g1 : g0;
+                    const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
+                    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                    if (r2 < A.cut2) {
+                        const float w = fmaf(0.5f, ntj, h ? base1 : base0) * expf(-r2 * A.inv2s2);
+                        const float vi = pi.w, vj = pj.w;
+                        const float tx = __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x));
+                        const float ty = __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y));
+                        const float tz = __fsub_rn(__fmul_rn(vi, gj.z), __fmul_rn(vj, gi.z));
+                        if (h) a1x = fmaf(w, tx, a1x), a1y = fmaf(w, ty, a1y), a1z = fmaf(w, tz, a1z);
+                        else a0x = fmaf(w, tx, a0x), a0y = fmaf(w, ty, a0y), a0z = fmaf(w, tz, a0z);
+                    }
+                }
+            }
+        }
+        const long long n = A.n;
+        if (v0) {
+            const long long o = A.idx[i0];
+            A.dGdt[o] += A.pref * a0x, A.dGdt[n + o] += A.pref * a0y, A.dGdt[2 * n + o] += A.pref * a0z;
+        }
+        if (v1) {
+            const long long o = A.idx[i1];
+            A.dGdt[o] += A.pref * a1x, A.dGdt[n + o] += A.pref * a1y, A.dGdt[2 * n + o] += A.pref * a1z;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t tree_workspace(long long n, size_t* bytes)
@@ -834,6 +987,100 @@ cudaError_t run_tree_induce(const float* pos, const float* str, long long n, flo
         case 3: return launch_tree<3>(w, ws, n, sigma, theta, grad, u, grad_u, st);
         default: return launch_tree<4>(w, ws, n, sigma, theta, grad, u, grad_u, st);
     }
+}
+
+}  // namespace vpm
+
+namespace vpm {
+
+// Workspace of the treecode right-hand side: the tree, the tree's u and J, the
+// segment sweep and its u and J, the sorted PSE copies and nu_t.
+cudaError_t tree_rhs_layout(long long n, long long m, bool comp, TreeRhsWs& r)
+{
+    r = TreeRhsWs{};
+    size_t tb = 0;
+    cudaError_t e = tree_workspace(n, &tb);
+    if (e != cudaSuccess) return e;
+    Carve cv;
+    r.tree = cv.take(tb);
+    r.up = cv.take((size_t)n * 3 * sizeof(float));
+    r.Jp = cv.take((size_t)n * 9 * sizeof(float));
+    r.us = cv.take((size_t)n * 3 * sizeof(float));
+    r.Js = cv.take((size_t)n * 9 * sizeof(float));
+    r.sp = cv.take((size_t)n * 16);
+    r.sg = cv.take((size_t)n * 16);
+    r.nut = cv.take((size_t)n * sizeof(float));
+    r.counter = cv.take(sizeof(int));
+    Carve c2;
+    r.seg_plan = plan_sweep(n, 0, m, true, comp, c2);
+    r.seg = cv.take(c2.off);
+    r.bytes = cv.off;
+    return cudaSuccess;
+}
+
+cudaError_t run_tree_rhs(const TreeRhsWs& r, char* ws, const float* pos, const float* str, long long n,
+                         const float* seg_a, const float* seg_b, long long m, const vpm_params* prm, float theta,
+                         int order, float* dxdt, float* dGdt, float* nu_t, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    float* up = reinterpret_cast<float*>(ws + r.up);
+    float* Jp = reinterpret_cast<float*>(ws + r.Jp);
+    float* us = reinterpret_cast<float*>(ws + r.us);
+    float* Js = reinterpret_cast<float*>(ws + r.Js);
+    float* nut = nu_t ? nu_t : reinterpret_cast<float*>(ws + r.nut);
+    char* tws = ws + r.tree;
+    cudaError_t e = run_tree_induce(pos, str, n, prm->sigma, theta, order, up, Jp, tws, st);
+    if (e != cudaSuccess) return e;
+    if (m > 0) {
+        EpilogueOut o;
+        o.mode = 0;
+        o.u = us;
+        o.grad_u = Js;
+        e = run_sweep(r.seg_plan, ws + r.seg, pos, nullptr, nullptr, seg_a, seg_b, prm->sigma, prm->seg_core,
+                      prm->vatistas_n, o, st);
+        if (e != cudaSuccess) return e;
+    }
+    trace_launch();
+    tree_rhs_epilogue_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (int)n, up, Jp, m > 0 ? us : nullptr, m > 0 ? Js : nullptr, reinterpret_cast<const float4*>(str), prm->sigma,
+        prm->c_v, prm->u_inf[0], prm->u_inf[1], prm->u_inf[2], (prm->flags & VPM_STRETCH_CLASSIC) ? 1 : 0,
+        (prm->flags & VPM_CHECK_FINITE) ? 1 : 0, dev_err_ptr(), dxdt, dGdt, nut);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // PSE over the tree built for these positions (still in the tree's workspace)
+    TreeWs w;
+    if ((e = tree_layout(n, w)) != cudaSuccess) return e;
+    float4* sp = reinterpret_cast<float4*>(ws + r.sp);
+    float4* sg = reinterpret_cast<float4*>(ws + r.sg);
+    const int* idx = reinterpret_cast<const int*>(tws + w.idx1);
+    trace_launch();
+    tree_pse_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const float4*>(pos), reinterpret_cast<const float4*>(str), nut, idx, (int)n, sp, sg);
+    PseArgs A{};
+    A.sp = sp;
+    A.sg = sg;
+    A.geo = reinterpret_cast<const float4*>(tws + w.geo);
+    A.idx = idx;
+    A.n = n;
+    A.D = w.D;
+    const double sg2 = (double)prm->sigma * prm->sigma;
+    A.sep = (float)(RHO_FAR * (double)prm->sigma);
+    A.cut2 = (float)((double)RHO_FAR * RHO_FAR * sg2);
+    A.inv2s2 = (float)(0.5 / sg2);
+    A.nu = prm->nu;
+    A.pref = (float)(2.0 / sg2 * pow(2.0 * 3.14159265358979323846 * sg2, -1.5));  // (2/sigma^2) zeta's norm
+    A.counter = reinterpret_cast<int*>(ws + r.counter);
+    A.dGdt = dGdt;
+    if ((e = cudaMemsetAsync(A.counter, 0, sizeof(int), st)) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_pse_kernel, TREE_WARPS * 32, 0)) !=
+        cudaSuccess)
+        return e;
+    const long long leaves = 1LL << w.D;
+    const long long blocks =
+        std::min<long long>((leaves + TREE_WARPS - 1) / TREE_WARPS, (long long)std::max(per_sm, 1) * sm_count());
+    trace_launch();
+    tree_pse_kernel<<<(unsigned)blocks, TREE_WARPS * 32, 0, st>>>(A);
+    return cudaGetLastError();
 }
 
 }  // namespace vpm

@@ -159,3 +159,62 @@ def test_default_settings_on_rotor_wakes(api, config):
     ref_u, ref_J = _oracle_on(w.pos, w.strength, w.sigma, idx)
     eu, eg = _errors(u, g, ref_u, ref_J, idx)
     assert eu <= TREE_TOL_U and eg <= TREE_TOL_G, (eu, eg)
+
+
+@pytest.mark.parametrize("classic", [False, True])
+def test_rhs_tree_theta_zero_matches_the_oracle(api, classic):
+    """The treecode right-hand side with every cluster opened is the direct right-hand
+    side: u and grad u of the particles, the segments, Vreman, the stretching (here from
+    J^T Gamma of the summed gradient) and PSE over the tree's near pairs."""
+    w = synth.make(1)
+    rdx, rdG, rnut = oracle.rhs(w.pos, w.strength, w.seg_a, w.seg_b, w.sigma, nu=w.nu, c_v=w.c_v,
+                                seg_core=w.seg_core, u_inf=w.u_inf, classic=classic)
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=False,
+                     classic=classic)
+    dx, dG, nut = api.rhs_tree(to_dev(w.pos), to_dev(w.strength), to_dev(w.seg_a), to_dev(w.seg_b), prm, theta=0.0)
+    torch.cuda.synchronize()
+    assert rel_l2(planar_to_rows(dx, 3), rdx) <= TOL_PLAIN
+    assert rel_l2(planar_to_rows(dG, 3), rdG) <= TOL_PLAIN
+    assert rel_l2(nut.cpu().numpy(), rnut) <= 1e-3
+
+
+def test_rhs_tree_with_strong_diffusion(api):
+    """A viscosity large enough that the PSE term is a large part of dGamma/dt, no
+    segments, no eddy viscosity: the tree's PSE walk against the oracle's sum."""
+    w = synth.make(1)
+    rdx, rdG, rnut = oracle.rhs(w.pos, w.strength, None, None, w.sigma, nu=5e-2, c_v=0.0)
+    dx, dG, nut = api.rhs_tree(to_dev(w.pos), to_dev(w.strength), None, None,
+                               api.Params(sigma=w.sigma, nu=5e-2, c_v=0.0), theta=0.0)
+    torch.cuda.synchronize()
+    assert rel_l2(planar_to_rows(dG, 3), rdG) <= TOL_PLAIN
+
+
+def test_rhs_tree_default_against_the_direct_rhs(api):
+    """Hover wake, 100,000 particles: theta = 0.5, order 4 against the direct right-hand
+    side of the library (itself within 1e-4 of the oracle)."""
+    w = synth.make(2)
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=False)
+    P, S, A, B = to_dev(w.pos), to_dev(w.strength), to_dev(w.seg_a), to_dev(w.seg_b)
+    dx0, dG0, nt0 = api.rhs(P, S, A, B, prm)
+    dx, dG, nt = api.rhs_tree(P, S, A, B, prm, theta=0.5, order=4)
+    torch.cuda.synchronize()
+    ex = rel_l2(planar_to_rows(dx, 3), planar_to_rows(dx0, 3))
+    eG = rel_l2(planar_to_rows(dG, 3), planar_to_rows(dG0, 3))
+    en = rel_l2(nt.cpu().numpy(), nt0.cpu().numpy())
+    assert ex <= TREE_TOL_U and eG <= 1e-2 and en <= 1e-2, (ex, eG, en)
+
+
+def test_step_tree_theta_zero_matches_the_direct_step(api):
+    w = synth.make(1)
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=False)
+    x0 = torch.from_numpy(w.pos[:, :3].T.astype(np.float64).copy()).cuda()
+    G0 = torch.from_numpy(w.strength[:, :3].T.astype(np.float64).copy()).cuda()
+    vol = torch.from_numpy(w.pos[:, 3].copy()).cuda()
+    A, B = to_dev(w.seg_a), to_dev(w.seg_b)
+    x1, G1 = api.step(x0.clone(), G0.clone(), vol, A, B, prm, w.dt)
+    x2, G2 = api.step_tree(x0.clone(), G0.clone(), vol, A, B, prm, w.dt, theta=0.0)
+    torch.cuda.synchronize()
+    dx_ref = (x1 - x0).cpu().numpy()
+    dG_ref = (G1 - G0).cpu().numpy()
+    assert rel_l2((x2 - x0).cpu().numpy(), dx_ref) <= TOL_PLAIN
+    assert rel_l2((G2 - G0).cpu().numpy(), dG_ref) <= TOL_PLAIN
