@@ -66,7 +66,24 @@ def test_version_and_invalid_arguments_without_gpu(lib):
     assert st == _lib.VPM_ERR_INVALID_ARG
     st = lib.aic_solve(None, None, None, VPM_MAX_AIC_PLUS_ONE, ctypes.c_double(1e-12), 5, None, None, None, 0, None)
     assert st == _lib.VPM_ERR_INVALID_ARG
+    # the treecode entries check theta, order and sigma before any CUDA call
+    F = ctypes.c_float
+    st = lib.vpm_tree_induce(None, None, 10, F(0.1), F(1.5), 4, None, None, None, 0, None)
+    assert st == _lib.VPM_ERR_INVALID_ARG and b"theta" in lib.vpm_last_error()
+    st = lib.vpm_tree_induce(None, None, 10, F(0.1), F(0.5), 5, None, None, None, 0, None)
+    assert st == _lib.VPM_ERR_INVALID_ARG and b"order" in lib.vpm_last_error()
+    st = lib.vpm_tree_induce(None, None, 10, F(0.0), F(0.5), 4, None, None, None, 0, None)
+    assert st == _lib.VPM_ERR_INVALID_ARG and b"sigma" in lib.vpm_last_error()
+    p.sigma = 0.1
+    p.vatistas_n = 2
+    st = lib.vpm_rhs_tree(None, None, 10, None, None, 0, ctypes.byref(p), F(-0.1), 4, None, None, None, None, 0,
+                          None)
+    assert st == _lib.VPM_ERR_INVALID_ARG and b"theta" in lib.vpm_last_error()
+    st = lib.vpm_step_tree(None, None, None, 10, None, None, 0, ctypes.byref(p), F(0.5), 1, ctypes.c_double(1e-3),
+                           None, 0, None)
+    assert st == _lib.VPM_ERR_INVALID_ARG and b"order" in lib.vpm_last_error()
     # zero-size calls are no-ops that succeed
+    assert lib.vpm_tree_induce(None, None, 0, F(0.1), F(0.5), 4, None, None, None, 0, None) == 0
     assert lib.vpm_induce(None, None, 5, None, 0, ctypes.c_float(1.0), 0, None, None, None, 0, None) == 0
     assert lib.aic_solve(None, None, None, 0, ctypes.c_double(1e-12), 5, None, None, None, 0, None) == 0
 
