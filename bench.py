@@ -549,13 +549,21 @@ def run_ours(args):
             out = {}
             tms = timed(lambda: out.__setitem__("t", api.tree_induce(Pt, St, wt.sigma, theta=0.5, order=4, ws=tws)), 3)
             dms = timed(lambda: api.induce(Pt, St, Pt, wt.sigma, compensated=False, ws=tws), 1)
+            # the whole right-hand side (segments, Vreman, stretching, PSE) with the treecode
+            # against the direct one
+            prm_t = api.Params(sigma=wt.sigma, nu=wt.nu, c_v=wt.c_v, seg_core=wt.seg_core, u_inf=wt.u_inf,
+                               compensated=False)
+            At = torch.from_numpy(wt.seg_a).to(dev)
+            Bt = torch.from_numpy(wt.seg_b).to(dev)
+            rms = timed(lambda: api.rhs_tree(Pt, St, At, Bt, prm_t, theta=0.5, order=4, ws=tws), 2)
+            rdms = timed(lambda: api.rhs(Pt, St, At, Bt, prm_t, ws=tws), 1)
             ut, gt = out["t"]
             tree_idx = synth.sample_targets(11, wt.n, 32)
             tree_gpu = (ut.cpu().numpy().T[tree_idx].astype(np.float64),
                         gt.cpu().numpy().T[tree_idx].reshape(-1, 3, 3).astype(np.float64))
             tree = {"particles": wt.n, "theta": 0.5, "order": 4, "ms": tms, "direct_plain_ms": dms,
-                    "speedup": dms / tms}
-            del Pt, St, tws, out, ut, gt
+                    "speedup": dms / tms, "rhs_ms": rms, "rhs_direct_plain_ms": rdms}
+            del Pt, St, At, Bt, tws, out, ut, gt
         except Exception as ex:  # informative, never fatal
             tree = {"unavailable": str(ex)[:200]}
 
