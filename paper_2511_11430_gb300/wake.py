@@ -46,9 +46,12 @@ def _dev(a, dtype, device):
 class RotorWake:
     def __init__(self, n_blades=2, n_span=20, n_chord=4, sigma=None, dt=None, max_rows=2, n_tip=2,
                  n_shed=1, adaptive=True, compensated=True, seg_core=None, nu=synth.NU_AIR, c_v=synth.C_V,
-                 kin=None, device="cuda"):
+                 kin=None, tree=None, device="cuda"):
         """sigma defaults to 0.02 R, dt to 5 deg of azimuth; kin to the hover rotor
-        (synth.Kinematics(): 8 deg collective, no flapping, no free stream)."""
+        (synth.Kinematics(): 8 deg collective, no flapping, no free stream).  tree =
+        (theta, order) advances the particles with the treecode right-hand side
+        (vpm_step_tree) instead of the direct sums, for wakes of a million particles."""
+        self.tree = tree
         self.kin = synth.Kinematics() if kin is None else kin
         self.nb, self.S, self.nc = n_blades, n_span, n_chord
         sigma = 0.02 * self.kin.radius if sigma is None else sigma
@@ -142,7 +145,11 @@ class RotorWake:
         check(lib.vpm_points_advect(api._void(pts), api._void(u_n), npts, ctypes.c_double(self.dt),
                                     (ctypes.c_float * 3)(*self.u_inf), api._stream()))
         if self.n > 0:
-            api.step(self.x, self.G, self.vol, seg_a, seg_b, self.prm, self.dt, ws=self.ws)
+            if self.tree is None:
+                api.step(self.x, self.G, self.vol, seg_a, seg_b, self.prm, self.dt, ws=self.ws)
+            else:
+                api.step_tree(self.x, self.G, self.vol, seg_a, seg_b, self.prm, self.dt, theta=self.tree[0],
+                              order=self.tree[1], ws=self.ws)
         # 4. shed a row behind the trailing edge of t + dt
         te_next = self._geometry_host(self.t + self.dt)[4]
         line0 = _dev(te_next, torch.float64, self.dev).reshape(1, self.nb, self.S + 1, 3)

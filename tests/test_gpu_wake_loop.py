@@ -55,3 +55,19 @@ def test_adaptive_conversion_creates_fewer_particles(wake_mod):
         a.step()
         c.step()
     assert 0 < a.n < c.n
+
+
+def test_rotor_wake_with_the_treecode_step(wake_mod):
+    """The driver with the treecode step at theta = 0 (every cluster opened: the direct
+    sums in plain FP32) follows the driver with the direct compensated step."""
+    kw = dict(n_blades=2, n_span=12, n_chord=3, max_rows=2, n_tip=3, n_shed=1)
+    a = wake_mod.RotorWake(**kw)
+    b = wake_mod.RotorWake(tree=(0.0, 4), **kw)
+    for _ in range(6):
+        ga = a.step().cpu().numpy()
+        gb = b.step().cpu().numpy()
+        assert rel_l2(gb, ga) <= 1e-4
+    torch.cuda.synchronize()
+    assert a.n == b.n > 0
+    assert rel_l2(b.x.cpu().numpy(), a.x.cpu().numpy()) <= 1e-6
+    assert rel_l2(b.G.cpu().numpy(), a.G.cpu().numpy()) <= 1e-4
