@@ -573,7 +573,7 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
             }
         }
         __syncwarp();
-#pragma unroll 1
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const float4* q = buf + j * P_F4;
             if constexpr (NEAR) {
