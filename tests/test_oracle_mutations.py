@@ -1,7 +1,8 @@
 """The oracle's pins are strong enough to catch plausible mistakes: each mutation
 below plants one (a dropped factor, a wrong sign, an index swapped, a wrong
 coefficient) in a copy of oracle/vpm_oracle.c, builds it, and runs the pin tests
-against it in a subprocess; every mutant must make at least one pin fail."""
+against it in a subprocess; every mutant must make at least one pin fail.  The same
+is done for the oracle's near-wake time loop (oracle/wake_loop.py)."""
 import os
 import subprocess
 import sys
@@ -64,4 +65,56 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     res = _run_pins(src.replace(old, new), tmp_path)
+    assert res.returncode != 0, f"no pin caught mutation {name}:\n{res.stdout[-2000:]}"
+
+
+# Mistakes planted in the oracle's near-wake time loop (oracle/wake_loop.py): the copy of
+# the oracle package with the mutated loop is put first on the import path of a
+# subprocess that runs the loop's pins (the C routines are the unmutated library).
+LOOP_SRC = os.path.join(ROOT, "oracle", "wake_loop.py")
+LOOP_PINS = ["tests/test_oracle_wake_loop.py"]
+LOOP_MUTATIONS = {
+    "nodes_drop_free_stream": ("self.nodes = (pts + self.dt * (_f32(u_n) + self.u_inf)).reshape(self.nodes.shape)",
+                               "self.nodes = (pts + self.dt * _f32(u_n)).reshape(self.nodes.shape)"),
+    "particles_drop_free_stream": ("seg_core=self.core, u_inf=self.u_inf, cast_f32=True)",
+                                   "seg_core=self.core, cast_f32=True)"),
+    "kutta_sign": ("shed = -gam[te_idx.ravel()].reshape(1, self.nb, self.S)",
+                   "shed = gam[te_idx.ravel()].reshape(1, self.nb, self.S)"),
+}
+
+
+def _run_loop_pins(loop_text, tmp_path):
+    import shutil
+
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), pkg / "__init__.py")
+    (pkg / "wake_loop.py").write_text(loop_text)
+    os.symlink(os.path.join(ROOT, "paper_2511_11430_gb300"), tmp_path / "paper_2511_11430_gb300")
+    os.symlink(os.path.join(ROOT, "tests"), tmp_path / "tests")
+    lib = os.path.join(ROOT, "oracle", "liboracle.so")
+    env = dict(os.environ, VPM_ORACLE_LIB=lib, OMP_NUM_THREADS="4")
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *LOOP_PINS],
+                          cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=900)
+
+
+@pytest.mark.slow
+def test_unmutated_loop_passes_its_pins(tmp_path):
+    import oracle
+
+    oracle.build()
+    res = _run_loop_pins(open(LOOP_SRC).read(), tmp_path)
+    assert res.returncode == 0, res.stdout[-2000:]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(LOOP_MUTATIONS))
+def test_loop_pins_catch_planted_mistake(name, tmp_path):
+    import oracle
+
+    oracle.build()
+    old, new = LOOP_MUTATIONS[name]
+    src = open(LOOP_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    res = _run_loop_pins(src.replace(old, new), tmp_path)
     assert res.returncode != 0, f"no pin caught mutation {name}:\n{res.stdout[-2000:]}"
