@@ -39,6 +39,11 @@
 // direct sum with the regularised kernel, and any other node is opened.  After the
 // walk every target evaluates the local expansion once.  theta = 0 opens every
 // node, which gives the direct sum.
+//
+// Right-hand side (vpm_rhs_tree).  The tree's u and grad u plus the segments' (the
+// direct segment sweep) give Vreman's eddy viscosity, the stretching and dx/dt per
+// particle; the PSE term of Eq. 5 is then summed by a second walk of the same tree
+// that visits only the nodes within 7 sigma of each target leaf.
 #include <math.h>
 
 #include <algorithm>
