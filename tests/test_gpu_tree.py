@@ -218,3 +218,25 @@ def test_step_tree_theta_zero_matches_the_direct_step(api):
     dG_ref = (G1 - G0).cpu().numpy()
     assert rel_l2((x2 - x0).cpu().numpy(), dx_ref) <= TOL_PLAIN
     assert rel_l2((G2 - G0).cpu().numpy(), dG_ref) <= TOL_PLAIN
+
+
+def test_tree_is_independent_of_the_input_order(api):
+    """The Morton sort makes the tree canonical: a permuted particle list gives the same
+    u and grad u bit for bit once un-permuted (distinct positions, so no key ties)."""
+    w = synth.make(2, n=20000)
+    perm = np.random.default_rng(3).permutation(w.n)
+    u, g = api.tree_induce(to_dev(w.pos), to_dev(w.strength), w.sigma, theta=0.5, order=4)
+    up, gp = api.tree_induce(to_dev(w.pos[perm]), to_dev(w.strength[perm]), w.sigma, theta=0.5, order=4)
+    torch.cuda.synchronize()
+    inv = np.argsort(perm)
+    assert np.array_equal(up.cpu().numpy()[:, inv], u.cpu().numpy())
+    assert np.array_equal(gp.cpu().numpy()[:, inv], g.cpu().numpy())
+
+
+def test_velocity_only_tree_matches_the_gradient_tree(api):
+    w = synth.make(2, n=30000)
+    P, S = to_dev(w.pos), to_dev(w.strength)
+    u, g = api.tree_induce(P, S, w.sigma, theta=0.5, order=4)
+    uv = api.tree_induce(P, S, w.sigma, theta=0.5, order=4, grad=False)
+    torch.cuda.synchronize()
+    assert rel_l2(uv.cpu().numpy(), u.cpu().numpy()) <= 1e-6
