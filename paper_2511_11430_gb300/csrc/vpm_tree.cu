@@ -60,6 +60,7 @@ namespace {
 constexpr int TREE_LEAF = 64;        // particles per leaf at most: one warp's targets
 constexpr int TREE_WARPS = 8;        // warps per traversal block
 constexpr int TREE_STAGE = 64;       // sources staged in shared memory at a time: a whole leaf
+static_assert(TREE_STAGE == 32 || TREE_STAGE == 64, "one or two warp-wide masks per staged run");
 constexpr int TREE_MAX_P = 4;        // highest expansion order
 constexpr int BOUNDS_BLOCKS = 1024;  // partial boxes of the bounding-box pass
 constexpr int MORTON_BITS = 21;      // per axis
@@ -568,32 +569,37 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
     for (long long c0 = s; c0 < e; c0 += TREE_STAGE) {
         const int cnt = (int)min((long long)TREE_STAGE, e - c0);
         __syncwarp();
+        // each lane stages two sources and, for a near run, tests them against the
+        // target leaf's box; the warp-wide masks then steer every source uniformly
+        unsigned far_mask[TREE_STAGE / 32];
 #pragma unroll
         for (int h = 0; h < TREE_STAGE / 32; ++h) {
             const int t = lane + 32 * h;
+            bool far = true;
             if (t < cnt) {
                 const float4* src = A.psrc + (c0 + t) * P_F4;
+                float4 v[P_F4];
 #pragma unroll
-                for (int f = 0; f < P_F4; ++f) buf[t * P_F4 + f] = src[f];
+                for (int f = 0; f < P_F4; ++f) v[f] = src[f], buf[t * P_F4 + f] = v[f];
+                if constexpr (NEAR) {
+                    const float sx = -v[0].x, sy = -v[0].z, sz = -v[1].x;
+                    const float ex = fmaxf(fmaxf(blo.x - sx, sx - bhi.x), 0.f);
+                    const float ey = fmaxf(fmaxf(blo.y - sy, sy - bhi.y), 0.f);
+                    const float ez = fmaxf(fmaxf(blo.z - sz, sz - bhi.z), 0.f);
+                    far = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) >= A.nc.far2;
+                }
             }
+            far_mask[h] = __ballot_sync(0xffffffffu, far);
         }
         __syncwarp();
 #pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const float4* q = buf + j * P_F4;
-            if constexpr (NEAR) {
-                const float4 q0 = q[0], q1 = q[1];
-                const float sx = -q0.x, sy = -q0.z, sz = -q1.x;
-                const float ex = fmaxf(fmaxf(blo.x - sx, sx - bhi.x), 0.f);
-                const float ey = fmaxf(fmaxf(blo.y - sy, sy - bhi.y), 0.f);
-                const float ez = fmaxf(fmaxf(blo.z - sz, sz - bhi.z), 0.f);
-                if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) >= A.nc.far2)
-                    particle_source<GRAD, false, false>(acc, q, X, Y, Z, A.nc, own);
-                else
-                    particle_source<GRAD, false, true>(acc, q, X, Y, Z, A.nc, own);
-            } else {
+            const unsigned m = (TREE_STAGE > 32 && j >= 32) ? far_mask[TREE_STAGE / 32 - 1] : far_mask[0];
+            if (NEAR && !((m >> (j & 31)) & 1u))
+                particle_source<GRAD, false, true>(acc, q, X, Y, Z, A.nc, own);
+            else
                 particle_source<GRAD, false, false>(acc, q, X, Y, Z, A.nc, own);
-            }
         }
     }
 }
