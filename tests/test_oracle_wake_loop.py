@@ -111,4 +111,6 @@ def test_forward_flight_thrust_of_the_ah1g_case():
         o.step()
     ct = np.array([h[1] for h in o.history])
     assert np.all(ct[3:] > 0)
-    assert abs(ct[6:].mean() / 0.00478 - 1.0) < 0.25
+    from tests.test_synth_kinematics import golden_ah1g
+
+    assert abs(ct[6:].mean() / golden_ah1g()["C_T_NL_UVLM_VPM"] - 1.0) < 0.25

@@ -2,9 +2,9 @@
 the blade lattice of ``synth.rotor_lattice`` against the closed forms it must meet.
 
 * hover kinematics reproduce ``synth.blade_lattice`` bit for bit;
-* the pitch and flap angles read back from the lattice equal the Eq. 12 schedules of
-  the AH-1G case at psi = 0 and 90 deg (values printed with Eq. 12), with the -10 deg
-  linear twist of the rotor's property table;
+* the AH-1G preset carries the values printed in Sec. IV.B (tests/golden), and the pitch
+  and flap angles read back from the lattice equal the Eq. 12 schedules at psi = 0, 90,
+  180 and 270 deg, with the -10 deg linear twist of the rotor's property table;
 * every ring corner and control point moves with omega_b x (x - hub): central finite
   differences of the lattice in time against the stated angular velocity, and v_rel is
   the free stream minus that motion;
@@ -13,11 +13,35 @@ the blade lattice of ``synth.rotor_lattice`` against the closed forms it must me
 * the free stream is mu Omega R along +x (psi = 0 downstream).
 """
 import dataclasses
+import os
 
 import numpy as np
 import pytest
 
 from paper_2511_11430_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ah1g_forward_flight.txt")
+
+
+def golden_ah1g():
+    """The AH-1G values printed in Sec. IV.B (Eq. 12, Tables 3 and 4)."""
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].split()
+        if len(line) == 2:
+            out[line[0]] = float(line[1])
+    return out
+
+
+def test_ah1g_preset_is_the_printed_case():
+    g = golden_ah1g()
+    k = synth.AH1G
+    assert k.theta == (g["theta_0"], g["theta_1c"], g["theta_1s"])
+    assert k.beta == (0.0, g["beta_1c"], g["beta_1s"])
+    assert (k.radius, k.chord, k.twist) == (g["radius"], g["chord"], g["twist"])
+    assert k.root == pytest.approx(g["root_cutout"] * g["radius"], rel=1e-15)
+    assert k.mu == g["advance_ratio"]
+    assert k.omega * k.radius == pytest.approx(g["tip_mach"] * 340.3, rel=1e-15)
 
 
 def test_hover_kinematics_reduce_to_blade_lattice():
@@ -47,9 +71,12 @@ def _pitch(L, b, S, nc, i, psi, beta_deg):
     return np.degrees(np.arcsin(-chord @ nf))  # trailing edge below the flapped disk plane
 
 
-@pytest.mark.parametrize("psi_deg, theta, beta", [(0.0, 6.0 + 1.7, 2.13), (90.0, 6.0 - 5.5, -0.15),
-                                                  (180.0, 6.0 - 1.7, -2.13), (270.0, 6.0 + 5.5, 0.15)])
-def test_eq12_schedules_read_back(psi_deg, theta, beta):
+@pytest.mark.parametrize("psi_deg", [0.0, 90.0, 180.0, 270.0])
+def test_eq12_schedules_read_back(psi_deg):
+    g = golden_ah1g()
+    c, sn = np.cos(np.radians(psi_deg)), np.sin(np.radians(psi_deg))
+    theta = g["theta_0"] + g["theta_1c"] * c + g["theta_1s"] * sn
+    beta = g["beta_1c"] * c + g["beta_1s"] * sn
     S, nc = 16, 3
     kin = synth.AH1G
     t = np.radians(psi_deg) / kin.omega
@@ -66,7 +93,7 @@ def test_eq12_schedules_read_back(psi_deg, theta, beta):
     # blade 1 sits half a turn later: the schedules at psi + 180 deg
     flap1, _ = _flap(flat, 1, S, nc, 3)
     assert flap1 == pytest.approx(-beta, abs=1e-9)
-    th1 = 6.0 - (theta - 6.0) + kin.twist * (r_nodes[3] / kin.radius - kin.twist_ref)
+    th1 = g["theta_0"] - (theta - g["theta_0"]) + kin.twist * (r_nodes[3] / kin.radius - kin.twist_ref)
     assert _pitch(L, 1, S, nc, 3, psi + np.pi, -beta) == pytest.approx(th1, abs=1e-9)
 
 
