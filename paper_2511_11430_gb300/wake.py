@@ -81,11 +81,16 @@ class RotorWake:
 
     # ---- geometry (prescribed motion: synthetic input) ---------------------------
     def _geometry_host(self, t):
+        # each step asks for the lattice at t and at t + dt: keep the last one
+        if getattr(self, "_geo_t", None) == t:
+            return self._geo
         L = synth.rotor_lattice(self.kin, t, self.nb, self.S, self.nc)
         r4 = np.zeros(L.rings.shape[:2] + (4,))
         r4[..., :3] = L.rings
         pad = lambda a: np.concatenate([a, np.zeros((a.shape[0], 1))], 1)
-        return r4, pad(L.colloc), pad(L.normal), pad(L.v_rel), L.te, L.te_idx, L.omega_b
+        self._geo_t = t
+        self._geo = (r4, pad(L.colloc), pad(L.normal), pad(L.v_rel), L.te, L.te_idx, L.omega_b)
+        return self._geo
 
     @property
     def rows(self) -> int:
