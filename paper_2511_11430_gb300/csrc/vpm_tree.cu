@@ -613,6 +613,43 @@ __host__ __device__ constexpr size_t tree_warp_smem()
     return (TREE_STAGE * P_F4 * 16 + (size_t)Local<P>::TABLE * 4 + 15) / 16 * 16;
 }
 
+// A target leaf that straddles a jump of the Morton curve (two compact clusters far
+// apart) has a sphere so large that no node is ever far from it, and its warp would sum
+// most of the wake directly.  Such a leaf is split at the largest gap between
+// index-consecutive targets, [s, g) and [g, e), and each part walks the tree with its
+// own box and sphere (the warp computes every target in both walks and keeps each
+// target's own part).  Split when both parts' spheres are below half the leaf's.
+struct TargetGroup {
+    float4 sph, lo, hi;  // sphere (centre, radius) and box of the group
+    long long g0, g1;    // the group's index range
+};
+
+__device__ __forceinline__ void group_box(float3 p0, bool in0, float3 p1, bool in1, float4& lo, float4& hi,
+                                          float4& sph)
+{
+    float l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const float a0[3] = {p0.x, p0.y, p0.z}, a1[3] = {p1.x, p1.y, p1.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (in0) l[c] = fminf(l[c], a0[c]), h[c] = fmaxf(h[c], a0[c]);
+        if (in1) l[c] = fminf(l[c], a1[c]), h[c] = fmaxf(h[c], a1[c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            l[c] = fminf(l[c], __shfl_xor_sync(0xffffffffu, l[c], o));
+            h[c] = fmaxf(h[c], __shfl_xor_sync(0xffffffffu, h[c], o));
+        }
+    }
+    const float cx = 0.5f * (l[0] + h[0]), cy = 0.5f * (l[1] + h[1]), cz = 0.5f * (l[2] + h[2]);
+    float r2 = 0.f;
+    if (in0) r2 = fmaxf(r2, (p0.x - cx) * (p0.x - cx) + (p0.y - cy) * (p0.y - cy) + (p0.z - cz) * (p0.z - cz));
+    if (in1) r2 = fmaxf(r2, (p1.x - cx) * (p1.x - cx) + (p1.y - cy) * (p1.y - cy) + (p1.z - cz) * (p1.z - cz));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    lo = make_float4(l[0], l[1], l[2], 0.f);
+    hi = make_float4(h[0], h[1], h[2], 0.f);
+    sph = make_float4(cx, cy, cz, sqrtf(r2) * 1.000001f);
+}
+
 template <int P, bool GRAD>
 __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
 {
@@ -644,8 +681,50 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         const float4 p0 = A.psrc[(v0 ? i0 : s) * P_F4], p0z = A.psrc[(v0 ? i0 : s) * P_F4 + 1];
         const float4 p1 = A.psrc[(v1 ? i1 : s) * P_F4], p1z = A.psrc[(v1 ? i1 : s) * P_F4 + 1];
         const f2 X = make_float2(-p0.x, -p1.x), Y = make_float2(-p0.z, -p1.z), Z = make_float2(-p0z.x, -p1z.x);
-        const float4 tg = A.geo[nleaves - 1 + leaf];
-        const float4 blo = A.box[2 * (nleaves - 1 + leaf)], bhi = A.box[2 * (nleaves - 1 + leaf) + 1];
+        // the leaf's targets in one group, or two if the leaf straddles a gap
+        TargetGroup grp[2];
+        int ngroups = 1;
+        grp[0].sph = A.geo[nleaves - 1 + leaf];
+        grp[0].lo = A.box[2 * (nleaves - 1 + leaf)];
+        grp[0].hi = A.box[2 * (nleaves - 1 + leaf) + 1];
+        grp[0].g0 = s, grp[0].g1 = e;
+        {
+            const float3 q0 = make_float3(X.x, Y.x, Z.x), q1 = make_float3(X.y, Y.y, Z.y);
+            // the gap after target s + lane (next: s + lane + 1) and after s + 32 + lane
+            const float3 n0 = make_float3(__shfl_down_sync(0xffffffffu, q0.x, 1), __shfl_down_sync(0xffffffffu, q0.y, 1),
+                                          __shfl_down_sync(0xffffffffu, q0.z, 1));
+            const float3 f1 = make_float3(__shfl_sync(0xffffffffu, q1.x, 0), __shfl_sync(0xffffffffu, q1.y, 0),
+                                          __shfl_sync(0xffffffffu, q1.z, 0));
+            const float3 n1 = make_float3(__shfl_down_sync(0xffffffffu, q1.x, 1), __shfl_down_sync(0xffffffffu, q1.y, 1),
+                                          __shfl_down_sync(0xffffffffu, q1.z, 1));
+            const float3 nx0 = lane < 31 ? n0 : f1;
+            auto dist2 = [](float3 a, float3 b) {
+                return (a.x - b.x) * (a.x - b.x) + (a.y - b.y) * (a.y - b.y) + (a.z - b.z) * (a.z - b.z);
+            };
+            const float gap0 = i0 + 1 < e ? dist2(q0, nx0) : -1.f;
+            const float gap1 = (lane < 31 && i1 + 1 < e) ? dist2(q1, n1) : -1.f;
+            float best = fmaxf(gap0, gap1);
+            long long bi = gap0 >= gap1 ? i0 + 1 : i1 + 1;  // the first index after the gap
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) best = ob, bi = oi;
+            }
+            if (best > 0.f) {
+                TargetGroup a, b;
+                group_box(q0, v0 && i0 < bi, q1, v1 && i1 < bi, a.lo, a.hi, a.sph);
+                group_box(q0, v0 && i0 >= bi, q1, v1 && i1 >= bi, b.lo, b.hi, b.sph);
+                if (fmaxf(a.sph.w, b.sph.w) < 0.5f * grp[0].sph.w) {
+                    a.g0 = s, a.g1 = bi, b.g0 = bi, b.g1 = e;
+                    grp[0] = a, grp[1] = b, ngroups = 2;
+                }
+            }
+        }
+#pragma unroll 1
+        for (int gi = 0; gi < ngroups; ++gi) {
+        const float4 tg = grp[gi].sph, blo = grp[gi].lo, bhi = grp[gi].hi;
+        const long long gs = grp[gi].g0, ge = grp[gi].g1;
         Acc<GRAD, false> acc;
         acc.zero();
         LocalAcc<P> la;
@@ -729,8 +808,9 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         const long long n = A.n;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (!(h ? v1 : v0)) continue;
-            const long long o = A.idx[h ? i1 : i0];
+            const long long it = h ? i1 : i0;
+            if (!(h ? v1 : v0) || it < gs || it >= ge) continue;
+            const long long o = A.idx[it];
             float v[14];
 #pragma unroll
             for (int q = 0; q < Acc<GRAD, false>::N; ++q) v[q] = h ? acc.v[q].y : acc.v[q].x;
@@ -749,7 +829,8 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 J[8 * n + o] = (-3.f * Gzz) * f;
             }
         }
-        __syncwarp();  // the table is read by every lane before the next leaf overwrites it
+        __syncwarp();  // the table is read by every lane before the next walk overwrites it
+        }
     }
 }
 
