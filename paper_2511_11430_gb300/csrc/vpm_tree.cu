@@ -650,6 +650,41 @@ __device__ __forceinline__ void group_box(float3 p0, bool in0, float3 p1, bool i
     sph = make_float4(cx, cy, cz, sqrtf(r2) * 1.000001f);
 }
 
+// grp[0] holds the whole leaf; returns 2 (and both parts in grp) if it is split.
+__device__ __forceinline__ int split_leaf(float3 q0, float3 q1, bool v0, bool v1, long long i0, long long i1,
+                                          long long s, long long e, int lane, TargetGroup* grp)
+{
+    // the gap after target s + lane (next: s + lane + 1) and after s + 32 + lane
+    const float3 n0 = make_float3(__shfl_down_sync(0xffffffffu, q0.x, 1), __shfl_down_sync(0xffffffffu, q0.y, 1),
+                                  __shfl_down_sync(0xffffffffu, q0.z, 1));
+    const float3 f1 = make_float3(__shfl_sync(0xffffffffu, q1.x, 0), __shfl_sync(0xffffffffu, q1.y, 0),
+                                  __shfl_sync(0xffffffffu, q1.z, 0));
+    const float3 n1 = make_float3(__shfl_down_sync(0xffffffffu, q1.x, 1), __shfl_down_sync(0xffffffffu, q1.y, 1),
+                                  __shfl_down_sync(0xffffffffu, q1.z, 1));
+    const float3 nx0 = lane < 31 ? n0 : f1;
+    auto dist2 = [](float3 a, float3 b) {
+        return (a.x - b.x) * (a.x - b.x) + (a.y - b.y) * (a.y - b.y) + (a.z - b.z) * (a.z - b.z);
+    };
+    const float gap0 = i0 + 1 < e ? dist2(q0, nx0) : -1.f;
+    const float gap1 = (lane < 31 && i1 + 1 < e) ? dist2(q1, n1) : -1.f;
+    float best = fmaxf(gap0, gap1);
+    long long bi = gap0 >= gap1 ? i0 + 1 : i1 + 1;  // the first index after the gap
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) best = ob, bi = oi;
+    }
+    if (!(best > 0.f)) return 1;
+    TargetGroup a, b;
+    group_box(q0, v0 && i0 < bi, q1, v1 && i1 < bi, a.lo, a.hi, a.sph);
+    group_box(q0, v0 && i0 >= bi, q1, v1 && i1 >= bi, b.lo, b.hi, b.sph);
+    if (!(fmaxf(a.sph.w, b.sph.w) < 0.5f * grp[0].sph.w)) return 1;
+    a.g0 = s, a.g1 = bi, b.g0 = bi, b.g1 = e;
+    grp[0] = a, grp[1] = b;
+    return 2;
+}
+
 template <int P, bool GRAD>
 __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
 {
@@ -688,39 +723,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         grp[0].lo = A.box[2 * (nleaves - 1 + leaf)];
         grp[0].hi = A.box[2 * (nleaves - 1 + leaf) + 1];
         grp[0].g0 = s, grp[0].g1 = e;
-        {
-            const float3 q0 = make_float3(X.x, Y.x, Z.x), q1 = make_float3(X.y, Y.y, Z.y);
-            // the gap after target s + lane (next: s + lane + 1) and after s + 32 + lane
-            const float3 n0 = make_float3(__shfl_down_sync(0xffffffffu, q0.x, 1), __shfl_down_sync(0xffffffffu, q0.y, 1),
-                                          __shfl_down_sync(0xffffffffu, q0.z, 1));
-            const float3 f1 = make_float3(__shfl_sync(0xffffffffu, q1.x, 0), __shfl_sync(0xffffffffu, q1.y, 0),
-                                          __shfl_sync(0xffffffffu, q1.z, 0));
-            const float3 n1 = make_float3(__shfl_down_sync(0xffffffffu, q1.x, 1), __shfl_down_sync(0xffffffffu, q1.y, 1),
-                                          __shfl_down_sync(0xffffffffu, q1.z, 1));
-            const float3 nx0 = lane < 31 ? n0 : f1;
-            auto dist2 = [](float3 a, float3 b) {
-                return (a.x - b.x) * (a.x - b.x) + (a.y - b.y) * (a.y - b.y) + (a.z - b.z) * (a.z - b.z);
-            };
-            const float gap0 = i0 + 1 < e ? dist2(q0, nx0) : -1.f;
-            const float gap1 = (lane < 31 && i1 + 1 < e) ? dist2(q1, n1) : -1.f;
-            float best = fmaxf(gap0, gap1);
-            long long bi = gap0 >= gap1 ? i0 + 1 : i1 + 1;  // the first index after the gap
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) best = ob, bi = oi;
-            }
-            if (best > 0.f) {
-                TargetGroup a, b;
-                group_box(q0, v0 && i0 < bi, q1, v1 && i1 < bi, a.lo, a.hi, a.sph);
-                group_box(q0, v0 && i0 >= bi, q1, v1 && i1 >= bi, b.lo, b.hi, b.sph);
-                if (fmaxf(a.sph.w, b.sph.w) < 0.5f * grp[0].sph.w) {
-                    a.g0 = s, a.g1 = bi, b.g0 = bi, b.g1 = e;
-                    grp[0] = a, grp[1] = b, ngroups = 2;
-                }
-            }
-        }
+        ngroups = split_leaf(make_float3(X.x, Y.x, Z.x), make_float3(X.y, Y.y, Z.y), v0, v1, i0, i1, s, e, lane, grp);
 #pragma unroll 1
         for (int gi = 0; gi < ngroups; ++gi) {
         const float4 tg = grp[gi].sph, blo = grp[gi].lo, bhi = grp[gi].hi;
@@ -977,7 +980,15 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
         const float4 p0 = A.sp[v0 ? i0 : s], g0 = A.sg[v0 ? i0 : s];
         const float4 p1 = A.sp[v1 ? i1 : s], g1 = A.sg[v1 ? i1 : s];
         const float base0 = A.nu + 0.5f * g0.w, base1 = A.nu + 0.5f * g1.w;
-        const float4 tg = A.geo[nleaves - 1 + leaf];
+        TargetGroup grp[2];
+        grp[0].sph = A.geo[nleaves - 1 + leaf];
+        grp[0].g0 = s, grp[0].g1 = e;
+        const int ngroups = split_leaf(make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z), v0, v1, i0, i1,
+                                       s, e, lane, grp);
+#pragma unroll 1
+        for (int gi = 0; gi < ngroups; ++gi) {
+        const float4 tg = grp[gi].sph;
+        const long long gs = grp[gi].g0, ge = grp[gi].g1;
         float a0x = 0.f, a0y = 0.f, a0z = 0.f, a1x = 0.f, a1y = 0.f, a1z = 0.f;
         int st = 0, sp = 1;  // the stack, one entry per lane
         while (sp > 0) {
@@ -1026,13 +1037,15 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
             }
         }
         const long long n = A.n;
-        if (v0) {
+        if (v0 && i0 >= gs && i0 < ge) {
             const long long o = A.idx[i0];
             A.dGdt[o] += A.pref * a0x, A.dGdt[n + o] += A.pref * a0y, A.dGdt[2 * n + o] += A.pref * a0z;
         }
-        if (v1) {
+        if (v1 && i1 >= gs && i1 < ge) {
             const long long o = A.idx[i1];
             A.dGdt[o] += A.pref * a1x, A.dGdt[n + o] += A.pref * a1y, A.dGdt[2 * n + o] += A.pref * a1z;
+        }
+        __syncwarp();  // the staging buffer is read by every lane before the next walk refills it
         }
     }
 }
