@@ -87,7 +87,8 @@ int tree_depth(long long n)
 constexpr int M2L_MIN = 32;
 
 struct TreeWs {
-    size_t part, keys0, keys1, idx0, idx1, cub, cub_bytes, psrc, geo, box, mom, counter, bytes;
+    size_t part, keys0, keys1, idx0, idx1, cub, cub_bytes, psrc, geo, box, mom, counter, lkey0, lkey1, lord0,
+        lord1, bytes;
     int D;
     long long nodes;
 };
@@ -109,8 +110,19 @@ cudaError_t tree_layout(long long n, TreeWs& w)
         nullptr, cb, (const unsigned long long*)nullptr, (unsigned long long*)nullptr, (const int*)nullptr,
         (int*)nullptr, (int)n, 0, 3 * MORTON_BITS);
     if (e != cudaSuccess) return e;
+    // the leaves' order of processing: by radius, largest first
+    const long long leaves = 1LL << w.D;
+    size_t cbl = 0;
+    const cudaError_t el = cub::DeviceRadixSort::SortPairs(nullptr, cbl, (const unsigned*)nullptr, (unsigned*)nullptr,
+                                                           (const int*)nullptr, (int*)nullptr, (int)leaves, 0, 32);
+    if (el != cudaSuccess) return el;
+    cb = std::max(cb, cbl);
     w.cub_bytes = cb;
     w.cub = cv.take(cb);
+    w.lkey0 = cv.take((size_t)leaves * 4);
+    w.lkey1 = cv.take((size_t)leaves * 4);
+    w.lord0 = cv.take((size_t)leaves * 4);
+    w.lord1 = cv.take((size_t)leaves * 4);
     w.psrc = cv.take((size_t)n * P_F4 * 16);
     w.geo = cv.take((size_t)w.nodes * 16);
     w.box = cv.take((size_t)w.nodes * 32);
@@ -226,6 +238,18 @@ __global__ void tree_gather_kernel(const float4* __restrict__ pos, const float4*
 }
 
 __device__ __forceinline__ long long run_begin(long long k, long long n, int level) { return (k * n) >> level; }
+
+// Sort keys that put the leaves of largest radius first (the likeliest to take the
+// longest): the bit pattern of a non-negative float orders like the float.
+__global__ void tree_leaf_keys_kernel(const float4* __restrict__ geo, int D, unsigned* __restrict__ key,
+                                      int* __restrict__ val)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long leaves = 1LL << D;
+    if (k >= leaves) return;
+    key[k] = ~__float_as_uint(fmaxf(geo[leaves - 1 + k].w, 0.f));
+    val[k] = (int)k;
+}
 
 // ---------------------------------------------------------------------------
 // Leaves: box, radius and moments of every leaf, one warp per leaf.
@@ -548,6 +572,7 @@ struct TreeArgs {
     const float4* box;   // per node (lo, hi)
     const float* mom;    // per node [3][NM] scaled moments
     const int* idx;      // sorted position -> particle index
+    const int* order;    // the leaves in order of processing
     long long n;
     int D;
     float theta, sep;    // opening angle, 7 sigma
@@ -710,6 +735,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         if (lane == 0) leaf = atomicAdd(A.counter, 1);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
         if (leaf >= nleaves) break;
+        leaf = A.order[leaf];
         const long long s = run_begin(leaf, A.n, A.D), e = run_begin(leaf + 1, A.n, A.D);
         const long long i0 = s + lane, i1 = s + 32 + lane;
         const bool v0 = i0 < e, v1 = i1 < e;
@@ -853,7 +879,18 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
         trace_launch();
         tree_up_kernel<P><<<(unsigned)((t + 127) / 128), 128, 0, st>>>(l, geo, box, mom);
     }
+    // the leaves by radius, largest first
+    unsigned* lk0 = reinterpret_cast<unsigned*>(ws + w.lkey0);
+    unsigned* lk1 = reinterpret_cast<unsigned*>(ws + w.lkey1);
+    int* lo0 = reinterpret_cast<int*>(ws + w.lord0);
+    int* lo1 = reinterpret_cast<int*>(ws + w.lord1);
+    trace_launch();
+    tree_leaf_keys_kernel<<<(unsigned)((leaves + 255) / 256), 256, 0, st>>>(geo, w.D, lk0, lo0);
+    size_t cb = w.cub_bytes;
+    cudaError_t e0 = cub::DeviceRadixSort::SortPairs(ws + w.cub, cb, lk0, lk1, lo0, lo1, (int)leaves, 0, 32, st);
+    if (e0 != cudaSuccess) return e0;
     TreeArgs A{};
+    A.order = lo1;
     A.psrc = psrc;
     A.geo = geo;
     A.box = box;
@@ -951,6 +988,7 @@ struct PseArgs {
     const float4* sg;   // sorted (Gamma, nu_t)
     const float4* geo;  // the tree of the same positions
     const int* idx;
+    const int* order;   // the leaves in order of processing
     long long n;
     int D;
     float sep, cut2, inv2s2, nu, pref;
@@ -974,6 +1012,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
         if (lane == 0) leaf = atomicAdd(A.counter, 1);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
         if (leaf >= nleaves) break;
+        leaf = A.order[leaf];
         const long long s = run_begin(leaf, A.n, A.D), e = run_begin(leaf + 1, A.n, A.D);
         const long long i0 = s + lane, i1 = s + 32 + lane;
         const bool v0 = i0 < e, v1 = i1 < e;
@@ -1165,6 +1204,7 @@ cudaError_t run_tree_rhs(const TreeRhsWs& r, char* ws, const float* pos, const f
     A.sg = sg;
     A.geo = reinterpret_cast<const float4*>(tws + w.geo);
     A.idx = idx;
+    A.order = reinterpret_cast<const int*>(tws + w.lord1);
     A.n = n;
     A.D = w.D;
     const double sg2 = (double)prm->sigma * prm->sigma;
