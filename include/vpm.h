@@ -140,6 +140,9 @@ vpm_status vpm_induce(const float* src_pos_d, const float* src_str_d, int64_t n_
  * least 7 sigma apart (where the Gaussian blob equals the point vortex in FP32).
  * theta = 0 opens every cluster: the direct sum (plain FP32 accumulation).  The
  * truncation error falls as theta^(order + 1).
+ * Near pairs take the blob kernel from a 16 KB table (cubic Hermite interpolation in
+ * rho^2, error far below FP32 rounding); the first call on each device copies that
+ * table to the device synchronously, so make it before any stream capture.
  *   pos_d, str_d [n][4] particles; u_d [3][n]; grad_u_d [9][n] or NULL;
  *   0 <= theta <= 1; order in {2, 3, 4}.  Workspace: VPM_OP_TREE (n_src = n). */
 vpm_status vpm_tree_induce(const float* pos_d, const float* str_d, int64_t n, float sigma, float theta, int order,

@@ -47,6 +47,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include <cub/device/device_radix_sort.cuh>
 
@@ -85,6 +86,114 @@ int tree_depth(long long n)
 // below it the point-vortex sum over its particles is cheaper (about 16 lane
 // operations per pair and target against about 1,000 per lane for the expansion).
 constexpr int M2L_MIN = 32;
+
+// ---------------------------------------------------------------------------
+// Near-field blob functions by table.  With x = rho^2 / 2, the direct sweep's kernel
+// functions are q(x) = g / rho^3 = 2^(-3/2) e^(-x) sum_k x^k / Gamma(k + 5/2) and
+// f = dq/dx = -(3/2) 2^(-3/2) e^(-x) sum_k x^k / Gamma(k + 7/2), whose derivative is
+// f' = (15/4) 2^(-3/2) e^(-x) sum_k x^k / Gamma(k + 9/2): the derivative of
+// e^(-x) sum_k x^k / Gamma(k + a) is e^(-x) sum_k x^k ((k + 1) c_{k+1} - c_k) with
+// c_k = 1 / Gamma(k + a), that is -(a - 1) e^(-x) sum_k x^k / Gamma(k + a + 1).  All
+// three series have positive terms, so on the host in FP64 they are exact to rounding
+// for every x up to 24.5 (rho = 7).  The treecode's near pairs interpolate q (with
+// q' = f) and f (with f') by cubic Hermite polynomials on NEAR_NT equal intervals of
+// x: the interpolation error is far below FP32 rounding, and a pair costs two table
+// reads and a few FMAs instead of the series or the erf form with their per-lane
+// branches.
+// ---------------------------------------------------------------------------
+constexpr int NEAR_NT = 1024;
+constexpr float NEAR_XMAX = 0.5f * RHO_FAR * RHO_FAR;
+
+static __device__ float4 g_near_table[NEAR_NT + 1];  // (q, D f, f, D f') at x_i = i D, D = NEAR_XMAX / NEAR_NT
+
+void near_table_host(float4* t)
+{
+    const double D = (double)NEAR_XMAX / NEAR_NT, c = 0.35355339059327376;  // 2^(-3/2)
+    for (int i = 0; i <= NEAR_NT; ++i) {
+        const double x = i * D;
+        double term = 4.0 / (3.0 * sqrt(3.14159265358979323846));  // x^k / Gamma(k + 5/2), k = 0
+        double T = 0.0, U = 0.0, V = 0.0;
+        for (int k = 0; k < 400; ++k) {
+            const double u = term / (k + 2.5), v = u / (k + 3.5);  // x^k / Gamma(k + 7/2), x^k / Gamma(k + 9/2)
+            T += term, U += u, V += v;
+            if (k > 10 && term < 1e-18 * T) break;
+            term *= x / (k + 2.5);
+        }
+        const double e = c * exp(-x);
+        const double q = e * T, f = -1.5 * e * U, fp = 3.75 * e * V;
+        t[i] = make_float4((float)q, (float)(D * f), (float)f, (float)(D * fp));
+    }
+}
+
+std::mutex g_near_mu;
+bool g_near_ready[64];
+
+// Uploads the table to the current device once (a synchronous copy).
+cudaError_t near_table_ready()
+{
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_near_mu);
+    if (g_near_ready[d]) return cudaSuccess;
+    static float4 host[NEAR_NT + 1];
+    static bool built = false;
+    if (!built) near_table_host(host), built = true;
+    e = cudaMemcpyToSymbol(g_near_table, host, sizeof(host));
+    if (e == cudaSuccess) g_near_ready[d] = true;
+    return e;
+}
+
+// K (without 1/(4 pi)) and h = H (-1/3) (without 1/(4 pi)) of one pair, as near_kh,
+// with the regularised part from the table T (in shared memory).
+__device__ __forceinline__ void near_kh_table(float r2, const NearConst& nc, const float4* __restrict__ T, float& K,
+                                              float& h)
+{
+    if (r2 == 0.f) {
+        K = 0.f;
+        h = 0.f;
+        return;
+    }
+    if (r2 >= nc.far2) {
+        const float rs = rsqrt_approx(r2);
+        const float i2 = rs * rs;
+        K = i2 * rs;
+        h = K * i2;
+        return;
+    }
+    const float t = (0.5f * r2 * nc.inv_s2) * ((float)NEAR_NT / NEAR_XMAX);
+    const int i = min((int)t, NEAR_NT - 1);  // x < 24.5 here; NaN converts to 0
+    const float s = t - (float)i;
+    const float4 a = T[i], b = T[i + 1];
+    const float s2 = s * s, s3 = s2 * s;
+    const float h01 = fmaf(-2.f, s3, 3.f * s2);  // cubic Hermite basis
+    const float h00 = 1.f - h01;
+    const float h10 = fmaf(-2.f, s2, s3 + s);
+    const float h11 = s3 - s2;
+    const float q = fmaf(h00, a.x, fmaf(h10, a.y, fmaf(h01, b.x, h11 * b.y)));
+    const float f = fmaf(h00, a.z, fmaf(h10, a.w, fmaf(h01, b.z, h11 * b.w)));
+    K = q * nc.inv_s3;
+    h = f * (-1.0f / 3.0f) * nc.inv_s5;
+}
+
+// One source against the thread's two targets with the tabulated near kernel.
+template <bool GRAD>
+__device__ __forceinline__ void near_source_table(Acc<GRAD, false>& a, const float4* __restrict__ e, f2 X, f2 Y,
+                                                  f2 Z, const NearConst& nc, const float4* __restrict__ T)
+{
+    const float4 q0 = e[0], q1 = e[1], q2 = e[2], q3 = e[3], q4 = e[4];
+    const f2 rx = add2(X, make_float2(q0.x, q0.y));
+    const f2 ry = add2(Y, make_float2(q0.z, q0.w));
+    const f2 rz = add2(Z, make_float2(q1.x, q1.y));
+    const f2 r2 = fma2(rz, rz, fma2(ry, ry, mul2(rx, rx)));
+    f2 K, h;
+    near_kh_table(r2.x, nc, T, K.x, h.x);
+    near_kh_table(r2.y, nc, T, K.y, h.y);
+    accum_particle<GRAD, false, true>(a, K, h, rx, ry, rz, make_float2(q1.z, q1.w), make_float2(q2.x, q2.y),
+                                      make_float2(q2.z, q2.w), make_float2(q3.x, q3.y), make_float2(q3.z, q3.w),
+                                      make_float2(q4.x, q4.y), Own{});
+}
 
 struct TreeWs {
     size_t part, keys0, keys1, idx0, idx1, cub, cub_bytes, psrc, geo, box, mom, counter, lkey0, lkey1, lord0,
@@ -588,7 +697,8 @@ struct TreeArgs {
 // the others evaluate the regularised kernel pair by pair.
 template <bool GRAD, bool NEAR>
 __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs& A, long long s, long long e,
-                                           float4* buf, int lane, f2 X, f2 Y, f2 Z, float4 blo, float4 bhi)
+                                           float4* buf, int lane, f2 X, f2 Y, f2 Z, float4 blo, float4 bhi,
+                                           const float4* __restrict__ T)
 {
     const Own own{};
     for (long long c0 = s; c0 < e; c0 += TREE_STAGE) {
@@ -622,7 +732,7 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
             const float4* q = buf + j * P_F4;
             const unsigned m = (TREE_STAGE > 32 && j >= 32) ? far_mask[TREE_STAGE / 32 - 1] : far_mask[0];
             if (NEAR && !((m >> (j & 31)) & 1u))
-                particle_source<GRAD, false, true>(acc, q, X, Y, Z, A.nc, own);
+                near_source_table<GRAD>(acc, q, X, Y, Z, A.nc, T);
             else
                 particle_source<GRAD, false, false>(acc, q, X, Y, Z, A.nc, own);
         }
@@ -722,6 +832,10 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
     float4* buf = reinterpret_cast<float4*>(tree_smem + warp * tree_warp_smem<P>());
     float* mbuf = reinterpret_cast<float*>(buf);
     float* B = reinterpret_cast<float*>(tree_smem + warp * tree_warp_smem<P>() + TREE_STAGE * P_F4 * 16);
+    // the near-field table, after the warps' slices
+    float4* T = reinterpret_cast<float4*>(tree_smem + TREE_WARPS * tree_warp_smem<P>());
+    for (int t = threadIdx.x; t <= NEAR_NT; t += blockDim.x) T[t] = g_near_table[t];
+    __syncthreads();
     const long long nleaves = 1LL << A.D;
     // the lane's local coefficients m = lane + 32 r, (a, b, c) packed 4 bits each
     unsigned mabc[L::RL];
@@ -785,12 +899,12 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 local_accumulate<P>(la, B, mbuf);
                 any_far = true;
             } else if (far) {
-                direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi);
+                direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi, T);
             } else if (level == A.D) {
                 if (d - rs >= A.sep)
-                    direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi);
+                    direct_run<GRAD, false>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi, T);
                 else
-                    direct_run<GRAD, true>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi);
+                    direct_run<GRAD, true>(acc, A, ns, ne, buf, lane, X, Y, Z, blo, bhi, T);
             } else {
                 // push the right child first so the left one is walked first
                 if (lane == sp) st = 2 * id + 2;
@@ -912,7 +1026,7 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     auto kern = grad ? tree_eval_kernel<P, true> : tree_eval_kernel<P, false>;
-    const size_t smem = TREE_WARPS * tree_warp_smem<P>();
+    const size_t smem = TREE_WARPS * tree_warp_smem<P>() + (NEAR_NT + 1) * sizeof(float4);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TREE_WARPS * 32, smem);
@@ -1106,6 +1220,7 @@ cudaError_t run_tree_induce(const float* pos, const float* str, long long n, flo
     TreeWs w;
     cudaError_t e = tree_layout(n, w);
     if (e != cudaSuccess) return e;
+    if ((e = near_table_ready()) != cudaSuccess) return e;
     float* part = reinterpret_cast<float*>(ws + w.part);
     auto* k0 = reinterpret_cast<unsigned long long*>(ws + w.keys0);
     auto* k1 = reinterpret_cast<unsigned long long*>(ws + w.keys1);
