@@ -24,7 +24,7 @@
 // Moving a node's moments from a child centre c' to the parent centre c is the
 // product of two truncated series: M_k = sum_{i <= k} M'_i s^(k - i) / (k - i)!,
 // s = c' - c.  A far cluster s acts on a target leaf t (centre c_t, x = c_t + y,
-// R0 = c_t - c_s) through the leaf's local expansion of order q = p + 2,
+// R0 = c_t - c_s) through the leaf's local expansion of order q = p + 1,
 //   Psi^l(c_t + y) = sum_{|m| <= q} L_m^l y^m / m!,  L_m^l = (-1)^|m| sum_k M_k^l b_{k + m}(R0),
 // summed over every far cluster of the leaf, and at each target
 //   4 pi u_a = eps_ajl sum_m L^l_{m + e_j} y^m / m!,   4 pi (grad u)_ab = eps_ajl sum_m L^l_{m + e_j + e_b} y^m / m!.
@@ -522,7 +522,8 @@ __global__ void tree_up_kernel(int level, float4* __restrict__ geo, float4* __re
 // ---------------------------------------------------------------------------
 template <int P>
 struct Local {
-    static constexpr int Q = P + 2;              // local expansion order
+    static constexpr int Q = P + 1;              // local expansion order (p + 2 measured 10% slower
+                                                 // for a gradient error 1.1-3 times smaller)
     static constexpr int NQ = P + Q;             // highest order of b_k needed
     static constexpr int DIM = NQ + 1;           // dense table b[a][b][c], a, b, c <= NQ
     static constexpr int DL = Q + 1;             // dense table L[l][a][b][c], a, b, c <= Q
