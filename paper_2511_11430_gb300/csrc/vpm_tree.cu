@@ -559,7 +559,8 @@ static __constant__ MiTable kMi = make_mi_table();
 // b_k(R0) for |k| <= NQ into the warp's dense table, order by order (each order reads
 // the two before it); the lanes share every order's entries.
 template <int P>
-__device__ __forceinline__ void local_table(float* __restrict__ B, float rx, float ry, float rz, int lane)
+__device__ __forceinline__ void local_table(float* __restrict__ B, float rx, float ry, float rz, int lane,
+                                            const unsigned short* __restrict__ abc)
 {
     using L = Local<P>;
     static_assert(L::NQ <= MI_MAX, "multi-index table too short");
@@ -574,7 +575,7 @@ __device__ __forceinline__ void local_table(float* __restrict__ B, float rx, flo
         const int q1 = nterms(n);
 #pragma unroll 1
         for (int q = nterms(n - 1) + lane; q < q1; q += 32) {
-            const unsigned v = kMi.abc[q];
+            const unsigned v = abc[q];  // lanes read different entries: shared memory, not the constant bank
             const int a = v & 15, b = (v >> 4) & 15, c = v >> 8;
             const int i = a * D2 + b * D1 + c;
             float s1 = 0.f, s2 = 0.f;
@@ -836,6 +837,8 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
     // the near-field table, after the warps' slices
     float4* T = reinterpret_cast<float4*>(tree_smem + TREE_WARPS * tree_warp_smem<P>());
     for (int t = threadIdx.x; t <= NEAR_NT; t += blockDim.x) T[t] = g_near_table[t];
+    __shared__ unsigned short s_abc[nterms(MI_MAX)];
+    for (int t = threadIdx.x; t < nterms(MI_MAX); t += blockDim.x) s_abc[t] = kMi.abc[t];
     __syncthreads();
     const long long nleaves = 1LL << A.D;
     // the lane's local coefficients m = lane + 32 r, (a, b, c) packed 4 bits each
@@ -896,7 +899,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 __syncwarp();
                 const float* src = A.mom + (size_t)id * 3 * L::NM;
                 for (int t = lane; t < 3 * L::NM; t += 32) mbuf[t] = src[t];
-                local_table<P>(B, -dx, -dy, -dz, lane);  // R0 = c_t - c_s; ends with a warp sync
+                local_table<P>(B, -dx, -dy, -dz, lane, s_abc);  // R0 = c_t - c_s; ends with a warp sync
                 local_accumulate<P>(la, B, mbuf);
                 any_far = true;
             } else if (far) {
