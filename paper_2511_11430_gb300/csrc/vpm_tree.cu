@@ -684,6 +684,7 @@ struct TreeArgs {
     const float* mom;    // per node [3][NM] scaled moments
     const int* idx;      // sorted position -> particle index
     const int* order;    // the leaves in order of processing
+    long long heavy;     // leaves at the head of the order that are processed as two items
     long long n;
     int D;
     float theta, sep;    // opening angle, 7 sigma
@@ -789,7 +790,7 @@ __device__ __forceinline__ void group_box(float3 p0, bool in0, float3 p1, bool i
 
 // grp[0] holds the whole leaf; returns 2 (and both parts in grp) if it is split.
 __device__ __forceinline__ int split_leaf(float3 q0, float3 q1, bool v0, bool v1, long long i0, long long i1,
-                                          long long s, long long e, int lane, TargetGroup* grp)
+                                          long long s, long long e, int lane, TargetGroup* grp, bool force = false)
 {
     // the gap after target s + lane (next: s + lane + 1) and after s + 32 + lane
     const float3 n0 = make_float3(__shfl_down_sync(0xffffffffu, q0.x, 1), __shfl_down_sync(0xffffffffu, q0.y, 1),
@@ -816,7 +817,7 @@ __device__ __forceinline__ int split_leaf(float3 q0, float3 q1, bool v0, bool v1
     TargetGroup a, b;
     group_box(q0, v0 && i0 < bi, q1, v1 && i1 < bi, a.lo, a.hi, a.sph);
     group_box(q0, v0 && i0 >= bi, q1, v1 && i1 >= bi, b.lo, b.hi, b.sph);
-    if (!(fmaxf(a.sph.w, b.sph.w) < 0.5f * grp[0].sph.w)) return 1;
+    if (!force && !(fmaxf(a.sph.w, b.sph.w) < 0.5f * grp[0].sph.w)) return 1;
     a.g0 = s, a.g1 = bi, b.g0 = bi, b.g1 = e;
     grp[0] = a, grp[1] = b;
     return 2;
@@ -848,12 +849,17 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         const int q = lane + 32 * r;
         mabc[r] = q < L::NL ? kMi.abc[q] : 0u;
     }
+    // work items: the A.heavy largest leaves (the first in A.order) as two items, one per
+    // part of the leaf split at its largest gap, so that their two walks run on two warps;
+    // every other leaf as one item (split or not by split_leaf's own test)
+    const long long nitems = nleaves + A.heavy;
     for (;;) {
-        long long leaf = 0;
-        if (lane == 0) leaf = atomicAdd(A.counter, 1);
-        leaf = __shfl_sync(0xffffffffu, leaf, 0);
-        if (leaf >= nleaves) break;
-        leaf = A.order[leaf];
+        long long item = 0;
+        if (lane == 0) item = atomicAdd(A.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems) break;
+        const int part = item < 2LL * A.heavy ? (int)(item & 1) : -1;
+        const long long leaf = A.order[item < 2LL * A.heavy ? item >> 1 : item - A.heavy];
         const long long s = run_begin(leaf, A.n, A.D), e = run_begin(leaf + 1, A.n, A.D);
         const long long i0 = s + lane, i1 = s + 32 + lane;
         const bool v0 = i0 < e, v1 = i1 < e;
@@ -867,9 +873,15 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
         grp[0].lo = A.box[2 * (nleaves - 1 + leaf)];
         grp[0].hi = A.box[2 * (nleaves - 1 + leaf) + 1];
         grp[0].g0 = s, grp[0].g1 = e;
-        ngroups = split_leaf(make_float3(X.x, Y.x, Z.x), make_float3(X.y, Y.y, Z.y), v0, v1, i0, i1, s, e, lane, grp);
+        ngroups = split_leaf(make_float3(X.x, Y.x, Z.x), make_float3(X.y, Y.y, Z.y), v0, v1, i0, i1, s, e, lane, grp,
+                             part >= 0);
+        int g_first = 0, g_last = ngroups;
+        if (part >= 0) {
+            if (ngroups == 1 && part == 1) continue;  // a leaf of one target: its first item covers it
+            g_first = part, g_last = part + 1;
+        }
 #pragma unroll 1
-        for (int gi = 0; gi < ngroups; ++gi) {
+        for (int gi = g_first; gi < g_last; ++gi) {
         const float4 tg = grp[gi].sph, blo = grp[gi].lo, bhi = grp[gi].hi;
         const long long gs = grp[gi].g0, ge = grp[gi].g1;
         Acc<GRAD, false> acc;
@@ -1009,6 +1021,7 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     if (e0 != cudaSuccess) return e0;
     TreeArgs A{};
     A.order = lo1;
+    A.heavy = std::min<long long>(leaves, std::max<long long>(leaves / 64, 1));
     A.psrc = psrc;
     A.geo = geo;
     A.box = box;
