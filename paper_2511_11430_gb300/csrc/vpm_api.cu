@@ -184,7 +184,7 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
     case VPM_OP_RHS_TREE:
     case VPM_OP_STEP_TREE: {
         TreeRhsWs r;
-        const cudaError_t e = tree_rhs_layout(n_src, m_seg, comp, r);
+        const cudaError_t e = tree_rhs_layout(n_src, m_seg, r);
         if (e != cudaSuccess) return cuda_fail(e, "vpm_workspace_size: sort scratch query");
         *bytes = r.bytes + (op == VPM_OP_STEP_TREE ? tree_step_extra(n_src) : 0);
         break;
@@ -415,9 +415,8 @@ vpm_status vpm_rhs_tree(const float* pos_d, const float* str_d, int64_t n, const
     REQUIRE(m == 0 || (seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d)),
             "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
     TreeRhsWs r;
-    cudaError_t e = tree_rhs_layout(n, m, prm->flags & VPM_COMPENSATED, r);
+    cudaError_t e = tree_rhs_layout(n, m, r);
     if (e != cudaSuccess) return cuda_fail(e, "vpm_rhs_tree: sort scratch query");
-    if (!overflow_guard(r.seg_plan)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
     if (!ws_d || ws_bytes < r.bytes || !aligned16(ws_d))
         return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", r.bytes, ws_bytes);
     if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
@@ -443,9 +442,8 @@ vpm_status vpm_step_tree(double* x_d, double* G_d, const float* vol_d, int64_t n
     REQUIRE(m == 0 || (seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d)),
             "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
     TreeRhsWs r;
-    cudaError_t e = tree_rhs_layout(n, m, prm->flags & VPM_COMPENSATED, r);
+    cudaError_t e = tree_rhs_layout(n, m, r);
     if (e != cudaSuccess) return cuda_fail(e, "vpm_step_tree: sort scratch query");
-    if (!overflow_guard(r.seg_plan)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
     const size_t need = r.bytes + tree_step_extra(n);
     if (!ws_d || ws_bytes < need || !aligned16(ws_d))
         return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", need, ws_bytes);

@@ -116,15 +116,24 @@ vpm_status run_wake_convert_row(const double* U, const double* D, const double* 
                                 cudaStream_t st, const char** msg);
 cudaError_t tree_workspace(long long n, size_t* bytes);
 struct TreeRhsWs {
-    size_t tree, up, Jp, us, Js, sp, sg, nut, counter, seg, bytes;
-    SweepPlan seg_plan;
+    size_t tree, stree, up, Jp, sp, sg, nut, counter, bytes;
 };
-cudaError_t tree_rhs_layout(long long n, long long m, bool comp, TreeRhsWs& r);
+// A built segment tree, as the treecode's traversal reads it.
+struct SegTreeView {
+    const float4* ssrc;  // sorted packed segments [m][S_F4]
+    const float4* geo;   // per node (cx, cy, cz, r)
+    const float* mom;    // per node [3][NM] scaled moments of the line strengths
+    long long m;
+    int D;               // depth
+    float sep;           // least sphere distance of a far node
+    int vn, core_pos;    // Vatistas exponent; the core is > 0
+};
+cudaError_t tree_rhs_layout(long long n, long long m, TreeRhsWs& r);
 cudaError_t run_tree_rhs(const TreeRhsWs& r, char* ws, const float* pos, const float* str, long long n,
                          const float* seg_a, const float* seg_b, long long m, const vpm_params* prm, float theta,
                          int order, float* dxdt, float* dGdt, float* nu_t, cudaStream_t st);
 cudaError_t run_tree_induce(const float* pos, const float* str, long long n, float sigma, float theta, int order,
-                            float* u, float* grad_u, char* ws, cudaStream_t st);
+                            float* u, float* grad_u, char* ws, cudaStream_t st, const SegTreeView* segs = nullptr);
 size_t aic_workspace(int n);
 vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, double tol, int max_iter, int* iters,
                          double* berr, char* ws, cudaStream_t st, const char** msg);

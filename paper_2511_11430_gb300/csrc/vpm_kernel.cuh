@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "vpm_common.cuh"
+#include "vpm_internal.h"
 
 namespace vpm {
 
@@ -215,6 +216,139 @@ __device__ __forceinline__ void particle_source(Acc<GRAD, STRETCH>& a, const flo
     accum_particle<GRAD, STRETCH, NEAR>(a, K, h, rx, ry, rz, make_float2(q1.z, q1.w), make_float2(q2.x, q2.y),
                                         make_float2(q2.z, q2.w), make_float2(q3.x, q3.y),
                                         make_float2(q3.z, q3.w), make_float2(q4.x, q4.y), o);
+}
+
+// ---------------------------------------------------------------------------
+// Vatistas-cored straight segments (Sec. II.A) against two packed targets.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Inverse lengths of one segment pair for one lane, with the end-point and axis
+// guards: a target within 1e-10 |r0| (or 1e-15 m) of an end point, or with
+// D == 0, gets zero (all outputs zero so every later product stays finite).
+__device__ __forceinline__ void seg_lane(float n1, float n2, float c2, float L2, float e, int vn, float& i1,
+                                         float& i2, float& irs, float& invD)
+{
+    const float thr = fmaxf(1e-20f * L2, 1e-30f);  // (1e-10 |r0|)^2, (1e-15 m)^2
+    const bool ok = (n1 > thr) && (n2 > thr);
+    float D;
+    if (vn == 2) {
+        D = fmaf(c2, c2, e);
+        invD = D > 0.f ? rsqrt_approx(D) : 0.f;
+    } else {
+        D = c2 + e;
+        invD = D > 0.f ? __frcp_rn(D) : 0.f;
+    }
+    if (!ok || !(D > 0.f)) {
+        i1 = i2 = irs = invD = 0.f;
+        return;
+    }
+    i1 = rsqrt_approx(n1);
+    i2 = rsqrt_approx(n2);
+    irs = rcp_approx(fmaf(n1, i1, n2 * i2));  // 1 / (|r1| + |r2|)
+}
+
+// Packed segment source (6 float4, both lanes equal):
+//   (-ax,-ax,-ay,-ay) (-az,-az,r0x,r0x) (r0y,r0y,r0z,r0z) (-r0x,-r0x,-r0y,-r0y) (-r0z,-r0z,-L2,-L2) (G,G,e,e)
+// with r0 = b - a, L2 = |r0|^2, e = (core |r0|)^(2n).  With r1 = x - a, r2 = x - b,
+// c = r0 x r1 (= r1 x r2), D = (|c|^(2n) + e)^(1/n):
+//   u = G/(4 pi) c d / D,   d = r0 . (r1/|r1| - r2/|r2|),
+//   J = G/(4 pi D) ( d [r0 x] + c (x) w ),   w = grad d - d grad D / D.
+// Both are written to avoid cancellation in FP32:
+//   d = (r0 . r1) (1/|r1| - 1/|r2|) + L2/|r2|,
+//     1/|r1| - 1/|r2| = (L2 - 2 r0.r1) / (|r1| |r2| (|r1| + |r2|))   (|r2|^2 - |r1|^2 = L2 - 2 r0.r1),
+//   grad d = (r1/|r1|^3 - r2/|r2|^3) x c   (the projections of r0 normal to r1, r2),
+//   grad D / D = 2 |c|^(2n-2) D^(-n) (c x r0),   so  w = (r1/|r1|^3 - r2/|r2|^3 + k3 r0) x c
+//   with k3 = 2 d |c|^(2n-2) D^(-n).
+// SAFE: the warp's targets are at least 1e-3 of the longest segment away from the
+// tile's bounding box and the core is positive, so no guard can trigger and every
+// reciprocal is taken on both lanes at once.
+template <bool GRAD, bool STRETCH, bool SAFE>
+__device__ __forceinline__ void segment_source(Acc<GRAD, STRETCH>& a, const float4* __restrict__ e4, f2 X, f2 Y, f2 Z,
+                                               int vn)
+{
+    {
+        const float4 s0 = e4[0], s1 = e4[1], s2 = e4[2], s3 = e4[3], s4 = e4[4], s5 = e4[5];
+        const f2 r0x = make_float2(s1.z, s1.w), r0y = make_float2(s2.x, s2.y), r0z = make_float2(s2.z, s2.w);
+        const f2 nr0x = make_float2(s3.x, s3.y), nr0y = make_float2(s3.z, s3.w), nr0z = make_float2(s4.x, s4.y);
+        const f2 nL2 = make_float2(s4.z, s4.w), gs = make_float2(s5.x, s5.y);
+        const f2 r1x = add2(X, make_float2(s0.x, s0.y));
+        const f2 r1y = add2(Y, make_float2(s0.z, s0.w));
+        const f2 r1z = add2(Z, make_float2(s1.x, s1.y));
+        const f2 r2x = add2(r1x, nr0x), r2y = add2(r1y, nr0y), r2z = add2(r1z, nr0z);
+        const f2 cx = fma2(r0y, r1z, mul2(nr0z, r1y));
+        const f2 cy = fma2(r0z, r1x, mul2(nr0x, r1z));
+        const f2 cz = fma2(r0x, r1y, mul2(nr0y, r1x));
+        const f2 n1 = fma2(r1z, r1z, fma2(r1y, r1y, mul2(r1x, r1x)));
+        const f2 n2 = fma2(r2z, r2z, fma2(r2y, r2y, mul2(r2x, r2x)));
+        const f2 p1 = fma2(r0z, r1z, fma2(r0y, r1y, mul2(r0x, r1x)));
+        const f2 c2 = fma2(cz, cz, fma2(cy, cy, mul2(cx, cx)));
+        f2 i1, i2, irs, invD;
+        if (SAFE) {
+            i1 = rsqrt2_approx(n1);
+            i2 = rsqrt2_approx(n2);
+            const f2 e = make_float2(s5.z, s5.w);
+            invD = vn == 2 ? rsqrt2_approx(fma2(c2, c2, e)) : rcp2_approx(add2(c2, e));
+            irs = rcp2_approx(fma2(n1, i1, mul2(n2, i2)));
+        } else {
+            seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, irs.x, invD.x);
+            seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, irs.y, invD.y);
+        }
+        const f2 L2 = mul2(nL2, splat(-1.f));
+        const f2 di = mul2(mul2(fma2(splat(-2.f), p1, L2), mul2(i1, i2)), irs);  // 1/|r1| - 1/|r2|
+        const f2 d = fma2(p1, di, mul2(L2, i2));
+        const f2 gi = mul2(gs, invD);
+        const f2 coef = mul2(gi, d);
+        a.v[0] = fma2(coef, cx, a.v[0]);
+        a.v[1] = fma2(coef, cy, a.v[1]);
+        a.v[2] = fma2(coef, cz, a.v[2]);
+        if (GRAD) {
+            a.v[3] = fma2(coef, r0x, a.v[3]);
+            a.v[4] = fma2(coef, r0y, a.v[4]);
+            a.v[5] = fma2(coef, r0z, a.v[5]);
+            f2 k3;
+            if (vn == 2) {
+                const f2 tmp = mul2(mul2(d, c2), mul2(invD, invD));
+                k3 = add2(tmp, tmp);
+            } else {
+                const f2 tmp = mul2(d, invD);
+                k3 = add2(tmp, tmp);
+            }
+            const f2 i1c = mul2(mul2(i1, i1), i1);
+            const f2 ni2c = mul2(mul2(i2, i2), mul2(i2, splat(-1.f)));
+            const f2 vx = fma2(k3, r0x, fma2(r1x, i1c, mul2(r2x, ni2c)));
+            const f2 vy = fma2(k3, r0y, fma2(r1y, i1c, mul2(r2y, ni2c)));
+            const f2 vz = fma2(k3, r0z, fma2(r1z, i1c, mul2(r2z, ni2c)));
+            const f2 nvx = mul2(vx, splat(-1.f)), nvy = mul2(vy, splat(-1.f)), nvz = mul2(vz, splat(-1.f));
+            const f2 wx = fma2(vy, cz, mul2(nvz, cy));  // w = v x c
+            const f2 wy = fma2(vz, cx, mul2(nvx, cz));
+            const f2 wz = fma2(vx, cy, mul2(nvy, cx));
+            const f2 cg = mul2(gi, splat(-1.0f / 3.0f));  // stored as G' with J = -3 G'
+            const f2 gx = mul2(cg, cx), gy = mul2(cg, cy), gz = mul2(cg, cz);
+            a.v[6] = fma2(gx, wx, a.v[6]);
+            a.v[7] = fma2(gx, wy, a.v[7]);
+            a.v[8] = fma2(gx, wz, a.v[8]);
+            a.v[9] = fma2(gy, wx, a.v[9]);
+            a.v[10] = fma2(gy, wy, a.v[10]);
+            a.v[11] = fma2(gy, wz, a.v[11]);
+            a.v[12] = fma2(gz, wx, a.v[12]);
+            a.v[13] = fma2(gz, wy, a.v[13]);
+        }
+    }
+}
+
+// The sources of a segment tile (S_F4 float4 each) against the thread's two targets.
+template <bool GRAD, bool STRETCH, bool SAFE>
+__device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y,
+                                             f2 Z, int vn)
+{
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) segment_source<GRAD, STRETCH, SAFE>(a, s + j * S_F4, X, Y, Z, vn);
 }
 
 }  // namespace vpm

@@ -518,6 +518,151 @@ __global__ void tree_up_kernel(int level, float4* __restrict__ geo, float4* __re
 }
 
 // ---------------------------------------------------------------------------
+// Segment tree (right-hand side only).  The blade and wake segments (Sec. II.A) form a
+// second source tree, sorted by the Morton keys of their midpoints and split into
+// count-balanced halves like the particle tree.  Segment j is the line strength
+// Gamma_j (b_j - a_j) dt along a_j + t (b_j - a_j), t in [0, 1]; far from it its
+// velocity is the point-vortex kernel integrated along the line, so a node's far field
+// enters the target's local expansion through the moments of these line strengths,
+// which 3-point Gauss-Legendre quadrature in t gives exactly through order 5.  Near
+// nodes are summed with the direct sweep's exact Vatistas kernel.
+// ---------------------------------------------------------------------------
+__global__ void seg_mid_kernel(const float4* __restrict__ a, const float4* __restrict__ b, int m,
+                               float4* __restrict__ mid)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const float4 p = a[j], q = b[j];
+    mid[j] = make_float4(0.5f * (p.x + q.x), 0.5f * (p.y + q.y), 0.5f * (p.z + q.z), 0.f);
+}
+
+// Sorted position k <- segment idx[k], packed like the direct sweep's segment sources:
+//   (-ax,-ax,-ay,-ay) (-az,-az,r0x,r0x) (r0y,r0y,r0z,r0z) (-r0x,-r0x,-r0y,-r0y) (-r0z,-r0z,-L2,-L2) (G,G,e,e)
+// with r0 = b - a, L2 = |r0|^2 and e = (core |r0|)^(2n).
+__global__ void seg_gather_kernel(const float4* __restrict__ sa, const float4* __restrict__ sb,
+                                  const int* __restrict__ idx, int m, float core, int vn, float4* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int j = idx[k];
+    const float4 a = sa[j], b = sb[j];
+    const float rx = b.x - a.x, ry = b.y - a.y, rz = b.z - a.z;
+    const float L2 = rx * rx + ry * ry + rz * rz;
+    const float cl2 = core * core * L2;
+    const float e = vn == 2 ? cl2 * cl2 : cl2;
+    float4* o = out + (size_t)k * S_F4;
+    o[0] = make_float4(-a.x, -a.x, -a.y, -a.y);
+    o[1] = make_float4(-a.z, -a.z, rx, rx);
+    o[2] = make_float4(ry, ry, rz, rz);
+    o[3] = make_float4(-rx, -rx, -ry, -ry);
+    o[4] = make_float4(-rz, -rz, -L2, -L2);
+    o[5] = make_float4(a.w, a.w, e, e);
+}
+
+// Segment leaves: the box and sphere of both end points of every segment, and the
+// moments sum_j sum_i w_i Gamma_j r0_j (y_ij - c)^k / k! over the Gauss points
+// y_ij = a_j + t_i r0_j.  One warp per leaf.
+template <int P>
+__global__ void seg_leaf_kernel(const float4* __restrict__ ssrc, long long m, int D, float4* __restrict__ geo,
+                                float4* __restrict__ box, float* __restrict__ mom)
+{
+    constexpr int NM = nterms(P);
+    const long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (leaf >= (1LL << D)) return;
+    const long long s = run_begin(leaf, m, D), e = run_begin(leaf + 1, m, D);
+    float ax[2], ay[2], az[2], rx[2], ry[2], rz[2], g[2];
+    bool ok[2];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const long long i = s + lane + 32 * h;
+        ok[h] = i < e;
+        ax[h] = ay[h] = az[h] = rx[h] = ry[h] = rz[h] = g[h] = 0.f;
+        if (ok[h]) {
+            const float4* q = ssrc + i * S_F4;
+            const float4 q0 = q[0], q1 = q[1], q2 = q[2], q5 = q[5];
+            ax[h] = -q0.x, ay[h] = -q0.z, az[h] = -q1.x;
+            rx[h] = q1.z, ry[h] = q2.x, rz[h] = q2.z;
+            g[h] = q5.x;
+            const float bx = ax[h] + rx[h], by = ay[h] + ry[h], bz = az[h] + rz[h];
+            lo[0] = fminf(lo[0], fminf(ax[h], bx)), lo[1] = fminf(lo[1], fminf(ay[h], by));
+            lo[2] = fminf(lo[2], fminf(az[h], bz));
+            hi[0] = fmaxf(hi[0], fmaxf(ax[h], bx)), hi[1] = fmaxf(hi[1], fmaxf(ay[h], by));
+            hi[2] = fmaxf(hi[2], fmaxf(az[h], bz));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    const float cx = 0.5f * (lo[0] + hi[0]), cy = 0.5f * (lo[1] + hi[1]), cz = 0.5f * (lo[2] + hi[2]);
+    float r2 = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (ok[h])
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {  // both end points
+                const float dx = ax[h] + t * rx[h] - cx, dy = ay[h] + t * ry[h] - cy, dz = az[h] + t * rz[h] - cz;
+                r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+            }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    const long long id = (1LL << D) - 1 + leaf;
+    if (lane == 0) {
+        geo[id] = make_float4(cx, cy, cz, sqrtf(r2) * 1.000001f);
+        box[2 * id] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        box[2 * id + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+    // Gauss-Legendre nodes and weights on [0, 1]
+    const float gt[3] = {0.5f - 0.38729833462074169f, 0.5f, 0.5f + 0.38729833462074169f};
+    const float gw[3] = {5.f / 18.f, 8.f / 18.f, 5.f / 18.f};
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+        float acc[NM];
+#pragma unroll
+        for (int q = 0; q < NM; ++q) acc[q] = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!ok[h]) continue;
+            const float gl = g[h] * (l == 0 ? rx[h] : (l == 1 ? ry[h] : rz[h]));
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float w = gw[i] * gl;
+                const float px = fmaf(gt[i], rx[h], ax[h]) - cx, py = fmaf(gt[i], ry[h], ay[h]) - cy,
+                            pz = fmaf(gt[i], rz[h], az[h]) - cz;
+                float tx[P + 1], ty[P + 1], tz[P + 1];  // d^a / a! per axis
+                tx[0] = ty[0] = tz[0] = 1.f;
+#pragma unroll
+                for (int a = 1; a <= P; ++a) {
+                    tx[a] = tx[a - 1] * px * (1.f / a);
+                    ty[a] = ty[a - 1] * py * (1.f / a);
+                    tz[a] = tz[a - 1] * pz * (1.f / a);
+                }
+#pragma unroll
+                for (int n2 = 0; n2 <= P; ++n2)
+#pragma unroll
+                    for (int a = n2; a >= 0; --a)
+#pragma unroll
+                        for (int b = n2 - a; b >= 0; --b) {
+                            const int c = n2 - a - b;
+                            acc[midx(a, b, c)] = fmaf(w, tx[a] * ty[b] * tz[c], acc[midx(a, b, c)]);
+                        }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NM; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (lane == (q & 31)) mom[(size_t)id * 3 * NM + l * NM + q] = acc[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Far field through the target leaf's local expansion.
 // ---------------------------------------------------------------------------
 template <int P>
@@ -692,6 +837,7 @@ struct TreeArgs {
     int* counter;
     float* u;
     float* grad;
+    SegTreeView seg;     // the segment tree (seg.m = 0: none)
 };
 
 // The direct sum over the sorted run [s, e) staged through the warp's buffer.  With
@@ -741,6 +887,29 @@ __device__ __forceinline__ void direct_run(Acc<GRAD, false>& acc, const TreeArgs
         }
     }
 }
+
+// Segments of the sorted run [s, e) with the exact Vatistas kernel, staged through the
+// warp's buffer.  SAFE: every target is at least 1e-3 of the longest segment away and
+// the core is positive, so no per-lane guard can trigger.
+constexpr int SEG_STAGE = TREE_STAGE * P_F4 / S_F4 / 32 * 32;
+
+template <bool GRAD, bool SAFE>
+__device__ __forceinline__ void segment_run(Acc<GRAD, false>& acc, const float4* __restrict__ ssrc, long long s,
+                                            long long e, float4* buf, int lane, f2 X, f2 Y, f2 Z, int vn)
+{
+    for (long long c0 = s; c0 < e; c0 += SEG_STAGE) {
+        const int cnt = (int)min((long long)SEG_STAGE, e - c0);
+        __syncwarp();
+        for (int t = lane; t < cnt * S_F4; t += 32) buf[t] = ssrc[c0 * S_F4 + t];
+        __syncwarp();
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) segment_source<GRAD, false, SAFE>(acc, buf + j * S_F4, X, Y, Z, vn);
+    }
+}
+
+// Smallest segment count of a far segment node that enters the local expansion (a
+// segment pair costs about twice a particle pair).
+constexpr int M2L_MIN_SEG = 16;
 
 // Shared memory of one traversal warp: the source staging buffer (also the node's
 // moments) and the dense b_k table (also the finished local coefficients), rounded
@@ -824,7 +993,7 @@ __device__ __forceinline__ int split_leaf(float3 q0, float3 q1, bool v0, bool v1
 }
 
 template <int P, bool GRAD>
-__global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
+__global__ void __launch_bounds__(TREE_WARPS * 32, 2) tree_eval_kernel(TreeArgs A)
 {
     using L = Local<P>;
     static_assert(3 * L::NM <= TREE_STAGE * P_F4 * 4, "moments fit the warp's source buffer");
@@ -928,6 +1097,40 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
                 sp += 2;
             }
         }
+        // the segment tree: far nodes into the same local expansion, the others exactly
+        if (A.seg.m > 0) {
+            int sst = 0, ssp = 1;  // the root
+            while (ssp > 0) {
+                const int id = __shfl_sync(0xffffffffu, sst, ssp - 1);
+                --ssp;
+                const int level = 31 - __clz(id + 1);
+                const long long k = (long long)id + 1 - (1LL << level);
+                const long long ns = run_begin(k, A.seg.m, level), ne = run_begin(k + 1, A.seg.m, level);
+                const float4 g = A.seg.geo[id];
+                const float dx = g.x - tg.x, dy = g.y - tg.y, dz = g.z - tg.z;
+                const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                const float rs = g.w + tg.w;
+                const bool far = rs < A.theta * d && d - rs >= A.seg.sep;
+                if (far && ne - ns >= M2L_MIN_SEG) {
+                    __syncwarp();
+                    const float* src = A.seg.mom + (size_t)id * 3 * L::NM;
+                    for (int t = lane; t < 3 * L::NM; t += 32) mbuf[t] = src[t];
+                    local_table<P>(B, -dx, -dy, -dz, lane, s_abc);
+                    local_accumulate<P>(la, B, mbuf);
+                    any_far = true;
+                } else if (far || level == A.seg.D) {
+                    // a segment inside the node's sphere is at most 2 r long
+                    if (A.seg.core_pos && d - rs >= 2e-3f * g.w)
+                        segment_run<GRAD, true>(acc, A.seg.ssrc, ns, ne, buf, lane, X, Y, Z, A.seg.vn);
+                    else
+                        segment_run<GRAD, false>(acc, A.seg.ssrc, ns, ne, buf, lane, X, Y, Z, A.seg.vn);
+                } else {
+                    if (lane == ssp) sst = 2 * id + 2;
+                    if (lane == ssp + 1) sst = 2 * id + 1;
+                    ssp += 2;
+                }
+            }
+        }
         if (any_far) {
             // the finished local coefficients, signed, into the table's storage
             __syncwarp();
@@ -995,7 +1198,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_eval_kernel(TreeArgs A)
 
 template <int P>
 cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, float theta, bool grad, float* u,
-                        float* grad_u, cudaStream_t st)
+                        float* grad_u, cudaStream_t st, const SegTreeView* segs)
 {
     float4* psrc = reinterpret_cast<float4*>(ws + w.psrc);
     float4* geo = reinterpret_cast<float4*>(ws + w.geo);
@@ -1039,6 +1242,7 @@ cudaError_t launch_tree(const TreeWs& w, char* ws, long long n, float sigma, flo
     A.counter = reinterpret_cast<int*>(ws + w.counter);
     A.u = u;
     A.grad = grad_u;
+    if (segs) A.seg = *segs;
     cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1231,7 +1435,7 @@ cudaError_t tree_workspace(long long n, size_t* bytes)
 }
 
 cudaError_t run_tree_induce(const float* pos, const float* str, long long n, float sigma, float theta, int order,
-                            float* u, float* grad_u, char* ws, cudaStream_t st)
+                            float* u, float* grad_u, char* ws, cudaStream_t st, const SegTreeView* segs)
 {
     if (n == 0) return cudaSuccess;
     TreeWs w;
@@ -1259,9 +1463,9 @@ cudaError_t run_tree_induce(const float* pos, const float* str, long long n, flo
                                                                      (int)n, reinterpret_cast<float4*>(ws + w.psrc));
     const bool grad = grad_u != nullptr;
     switch (order) {
-        case 2: return launch_tree<2>(w, ws, n, sigma, theta, grad, u, grad_u, st);
-        case 3: return launch_tree<3>(w, ws, n, sigma, theta, grad, u, grad_u, st);
-        default: return launch_tree<4>(w, ws, n, sigma, theta, grad, u, grad_u, st);
+        case 2: return launch_tree<2>(w, ws, n, sigma, theta, grad, u, grad_u, st, segs);
+        case 3: return launch_tree<3>(w, ws, n, sigma, theta, grad, u, grad_u, st, segs);
+        default: return launch_tree<4>(w, ws, n, sigma, theta, grad, u, grad_u, st, segs);
     }
 }
 
@@ -1269,27 +1473,114 @@ cudaError_t run_tree_induce(const float* pos, const float* str, long long n, flo
 
 namespace vpm {
 
-// Workspace of the treecode right-hand side: the tree, the tree's u and J, the
-// segment sweep and its u and J, the sorted PSE copies and nu_t.
-cudaError_t tree_rhs_layout(long long n, long long m, bool comp, TreeRhsWs& r)
+// Workspace of the segment tree: midpoints, keys and permutation (twice, for the radix
+// sort), the sort's scratch, the sorted packed segments and the nodes.
+struct SegTreeWs {
+    size_t part, mid, keys0, keys1, idx0, idx1, cub, cub_bytes, ssrc, geo, box, mom, bytes;
+    int D;
+    long long nodes;
+};
+
+static cudaError_t seg_tree_layout(long long m, SegTreeWs& w)
+{
+    Carve cv;
+    w = SegTreeWs{};
+    w.D = tree_depth(m);
+    w.nodes = (2LL << w.D) - 1;
+    w.part = cv.take((size_t)(BOUNDS_BLOCKS + 1) * 6 * sizeof(float));
+    w.mid = cv.take((size_t)m * 16);
+    w.keys0 = cv.take((size_t)m * 8);
+    w.keys1 = cv.take((size_t)m * 8);
+    w.idx0 = cv.take((size_t)m * 4);
+    w.idx1 = cv.take((size_t)m * 4);
+    size_t cb = 0;
+    const cudaError_t e = cub::DeviceRadixSort::SortPairs(
+        nullptr, cb, (const unsigned long long*)nullptr, (unsigned long long*)nullptr, (const int*)nullptr,
+        (int*)nullptr, (int)m, 0, 3 * MORTON_BITS);
+    if (e != cudaSuccess) return e;
+    w.cub_bytes = cb;
+    w.cub = cv.take(cb);
+    w.ssrc = cv.take((size_t)m * S_F4 * 16);
+    w.geo = cv.take((size_t)w.nodes * 16);
+    w.box = cv.take((size_t)w.nodes * 32);
+    w.mom = cv.take((size_t)w.nodes * 3 * nterms(TREE_MAX_P) * sizeof(float));
+    w.bytes = cv.off;
+    return cudaSuccess;
+}
+
+// Builds the segment tree of order P and describes it for the traversal.
+template <int P>
+static cudaError_t build_seg_tree(const SegTreeWs& w, char* ws, const float* seg_a, const float* seg_b, long long m,
+                                  float core, int vn, SegTreeView& v, cudaStream_t st)
+{
+    const float4* a4 = reinterpret_cast<const float4*>(seg_a);
+    const float4* b4 = reinterpret_cast<const float4*>(seg_b);
+    float4* mid = reinterpret_cast<float4*>(ws + w.mid);
+    float* part = reinterpret_cast<float*>(ws + w.part);
+    auto* k0 = reinterpret_cast<unsigned long long*>(ws + w.keys0);
+    auto* k1 = reinterpret_cast<unsigned long long*>(ws + w.keys1);
+    int* i0 = reinterpret_cast<int*>(ws + w.idx0);
+    int* i1 = reinterpret_cast<int*>(ws + w.idx1);
+    float4* ssrc = reinterpret_cast<float4*>(ws + w.ssrc);
+    float4* geo = reinterpret_cast<float4*>(ws + w.geo);
+    float4* box = reinterpret_cast<float4*>(ws + w.box);
+    float* mom = reinterpret_cast<float*>(ws + w.mom);
+    const unsigned grid = (unsigned)((m + 255) / 256);
+    trace_launch();
+    seg_mid_kernel<<<grid, 256, 0, st>>>(a4, b4, (int)m, mid);
+    const int nparts = (int)std::min<long long>(BOUNDS_BLOCKS, (m + 255) / 256);
+    trace_launch();
+    tree_bounds_kernel<<<nparts, 256, 0, st>>>(mid, (int)m, part);
+    trace_launch();
+    tree_box_kernel<<<1, 1024, 0, st>>>(part, nparts);
+    trace_launch();
+    tree_keys_kernel<<<grid, 256, 0, st>>>(mid, (int)m, part + 6 * nparts, k0, i0);
+    size_t cb = w.cub_bytes;
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(ws + w.cub, cb, k0, k1, i0, i1, (int)m, 0, 3 * MORTON_BITS, st);
+    if (e != cudaSuccess) return e;
+    trace_launch();
+    seg_gather_kernel<<<grid, 256, 0, st>>>(a4, b4, i1, (int)m, core, vn, ssrc);
+    const long long leaves = 1LL << w.D;
+    trace_launch();
+    seg_leaf_kernel<P><<<(unsigned)((leaves * 32 + 255) / 256), 256, 0, st>>>(ssrc, m, w.D, geo, box, mom);
+    for (int l = w.D - 1; l >= 0; --l) {
+        const long long t = 3 * (1LL << l);
+        trace_launch();
+        tree_up_kernel<P><<<(unsigned)((t + 127) / 128), 128, 0, st>>>(l, geo, box, mom);
+    }
+    v = SegTreeView{};
+    v.ssrc = ssrc;
+    v.geo = geo;
+    v.mom = mom;
+    v.m = m;
+    v.D = w.D;
+    // beyond sep the Vatistas core changes a segment's velocity by less than 2e-6 of
+    // itself: (r_c / h)^(2n) / n at distance h from the line
+    v.sep = core > 0.f ? (float)((double)core * pow(2e-6 * vn, -0.5 / vn)) : 0.f;
+    v.vn = vn;
+    v.core_pos = core > 0.f;
+    return cudaGetLastError();
+}
+
+// Workspace of the treecode right-hand side: the particle tree, the segment tree, the
+// trees' u and J, the sorted PSE copies and nu_t.
+cudaError_t tree_rhs_layout(long long n, long long m, TreeRhsWs& r)
 {
     r = TreeRhsWs{};
     size_t tb = 0;
     cudaError_t e = tree_workspace(n, &tb);
     if (e != cudaSuccess) return e;
+    SegTreeWs sw{};
+    if (m > 0 && (e = seg_tree_layout(m, sw)) != cudaSuccess) return e;
     Carve cv;
     r.tree = cv.take(tb);
+    r.stree = cv.take(sw.bytes);
     r.up = cv.take((size_t)n * 3 * sizeof(float));
     r.Jp = cv.take((size_t)n * 9 * sizeof(float));
-    r.us = cv.take((size_t)n * 3 * sizeof(float));
-    r.Js = cv.take((size_t)n * 9 * sizeof(float));
     r.sp = cv.take((size_t)n * 16);
     r.sg = cv.take((size_t)n * 16);
     r.nut = cv.take((size_t)n * sizeof(float));
     r.counter = cv.take(sizeof(int));
-    Carve c2;
-    r.seg_plan = plan_sweep(n, 0, m, true, comp, c2);
-    r.seg = cv.take(c2.off);
     r.bytes = cv.off;
     return cudaSuccess;
 }
@@ -1301,24 +1592,26 @@ cudaError_t run_tree_rhs(const TreeRhsWs& r, char* ws, const float* pos, const f
     if (n == 0) return cudaSuccess;
     float* up = reinterpret_cast<float*>(ws + r.up);
     float* Jp = reinterpret_cast<float*>(ws + r.Jp);
-    float* us = reinterpret_cast<float*>(ws + r.us);
-    float* Js = reinterpret_cast<float*>(ws + r.Js);
     float* nut = nu_t ? nu_t : reinterpret_cast<float*>(ws + r.nut);
     char* tws = ws + r.tree;
-    cudaError_t e = run_tree_induce(pos, str, n, prm->sigma, theta, order, up, Jp, tws, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    SegTreeView sv{};
     if (m > 0) {
-        EpilogueOut o;
-        o.mode = 0;
-        o.u = us;
-        o.grad_u = Js;
-        e = run_sweep(r.seg_plan, ws + r.seg, pos, nullptr, nullptr, seg_a, seg_b, prm->sigma, prm->seg_core,
-                      prm->vatistas_n, o, st);
+        SegTreeWs sw;
+        if ((e = seg_tree_layout(m, sw)) != cudaSuccess) return e;
+        const int vn = prm->vatistas_n;
+        switch (order) {
+            case 2: e = build_seg_tree<2>(sw, ws + r.stree, seg_a, seg_b, m, prm->seg_core, vn, sv, st); break;
+            case 3: e = build_seg_tree<3>(sw, ws + r.stree, seg_a, seg_b, m, prm->seg_core, vn, sv, st); break;
+            default: e = build_seg_tree<4>(sw, ws + r.stree, seg_a, seg_b, m, prm->seg_core, vn, sv, st); break;
+        }
         if (e != cudaSuccess) return e;
     }
+    e = run_tree_induce(pos, str, n, prm->sigma, theta, order, up, Jp, tws, st, m > 0 ? &sv : nullptr);
+    if (e != cudaSuccess) return e;
     trace_launch();
     tree_rhs_epilogue_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        (int)n, up, Jp, m > 0 ? us : nullptr, m > 0 ? Js : nullptr, reinterpret_cast<const float4*>(str), prm->sigma,
+        (int)n, up, Jp, nullptr, nullptr, reinterpret_cast<const float4*>(str), prm->sigma,
         prm->c_v, prm->u_inf[0], prm->u_inf[1], prm->u_inf[2], (prm->flags & VPM_STRETCH_CLASSIC) ? 1 : 0,
         (prm->flags & VPM_CHECK_FINITE) ? 1 : 0, dev_err_ptr(), dxdt, dGdt, nut);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
