@@ -12,6 +12,9 @@
 
 namespace vpm {
 
+constexpr int P_F4 = 5;  // float4 per packed particle source
+constexpr int S_F4 = 6;  // float4 per packed segment source
+
 typedef float2 f2;
 
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }

@@ -17,8 +17,6 @@ constexpr int SWEEP_STAGES = 6;              // shared-memory source tiles in fl
 constexpr int TPB = 256;          // threads per adjoint block (8 warps)
 constexpr int ADJ_TILE = 512;     // particles per adjoint tile: two per thread
 constexpr int SRC_TILE = 128;     // sources per particle or segment tile
-constexpr int P_F4 = 5;           // float4 per packed particle source
-constexpr int S_F4 = 6;           // float4 per packed segment source
 constexpr int T_F4 = 4;           // float4 per packed adjoint target (control point)
 constexpr float RHO_FAR = 7.0f;   // beyond 7 sigma the blob is a point vortex in FP32
 constexpr int UNIT_W_P = 10;      // stream-K cost of a particle tile

@@ -5,7 +5,6 @@
 #include <cuda_runtime.h>
 
 #include "vpm_common.cuh"
-#include "vpm_internal.h"
 
 namespace vpm {
 
