@@ -150,8 +150,13 @@ vpm_status vpm_tree_induce(const float* pos_d, const float* str_d, int64_t n, fl
 
 /* The right-hand side of Eq. 4-5 (as vpm_rhs) and one RK3 step (as vpm_step) with the
  * particle-particle u and grad u from the treecode of vpm_tree_induce (theta, order as
- * there) instead of the direct sweep; the segments' u and grad u still come from the
- * direct segment sweep (flags: VPM_COMPENSATED applies to it), Vreman's eddy viscosity
+ * there) instead of the direct sweep.  The segments form a second tree (by midpoint):
+ * a node far from a target leaf enters its local expansion through the moments of the
+ * segments' line strengths (exact through order 5 by 3-point Gauss-Legendre), where
+ * "far" also requires the node to be at least core (2e-6 n)^(-1/(2n)) away (there the
+ * Vatistas core changes the velocity by < 2e-6); nearer segments use the exact kernel
+ * of vpm_segments_induce.  All sums accumulate in plain FP32 (VPM_COMPENSATED has no
+ * effect here).  Vreman's eddy viscosity
  * and the stretching are formed in FP64 from the summed u and grad u (the transposed
  * stretching from J^T Gamma, not pair by pair), and the PSE term is summed over the
  * pairs within 7 sigma found by a walk of the same tree.  theta = 0 gives the direct

@@ -185,7 +185,7 @@ def rhs(pos, strength, seg_a, seg_b, params: Params, ws=None):
 
 
 def rhs_tree(pos, strength, seg_a, seg_b, params: Params, theta: float = 0.5, order: int = 4, ws=None):
-    """As rhs, with the particle-particle u and grad u from the treecode (vpm_rhs_tree)."""
+    """As rhs, with the particle and segment u and grad u from the treecode (vpm_rhs_tree)."""
     _need(pos, "pos", torch.float32, (4,))
     _need(strength, "strength", torch.float32, (4,))
     sa, sb, m = _segs(seg_a, seg_b)
