@@ -38,8 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # hover wake (100,000 particles, 5,120 segments), from one ncu capture of that launch
 # (profiles/sweep_kernel_hover4_100k.md); valid only while the kernel's sources hash to
 # SWEEP_SRC_SHA256, else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = 11_787_776 + 2_304
-SWEEP_SRC_SHA256 = "a4f7a58c1c1b6865d93e971b546bd66349dccba2c13514879f5495e3afd6468c"
+SWEEP_TRAFFIC_BYTES = 11_794_944 + 2_560
+SWEEP_SRC_SHA256 = "a1bb279cf1eb1472e796cbc511cebd68cb42408b03f01739c057fb6a9589b6cf"
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 
