@@ -522,6 +522,42 @@ def run_ours(args):
         except Exception as ex:  # informative, never fatal
             wake = {"unavailable": str(ex)[:200]}
 
+    # the particle-particle and the segment-particle parts of the right-hand side sweep,
+    # each alone (compensated, with the gradient), so that the two pair rates are reported
+    # apart (informative, outside the timed step)
+    parts = None
+    if rank == 0:
+        try:
+            pos, strn = api.pack_state(*make_state(), vol)
+            pws = api.Workspace(dev)
+            st = torch.cuda.current_stream()
+
+            def sweep_ms(fn, reps=3):
+                fn()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(reps):
+                    fn()
+                e1.record(st)
+                e1.synchronize()
+                return e0.elapsed_time(e1) / reps
+
+            p_ms = sweep_ms(lambda: api.induce(pos, strn, pos, w.sigma, compensated=True, ws=pws))
+            s_ms = sweep_ms(lambda: api.segments_induce(sa, sb, pos, w.seg_core, 2, compensated=True, ws=pws))
+            pp, sp_ = n * (n - 1), n * m
+            parts = {
+                "p2p": {"pairs": pp, "ms": p_ms, "pairs_per_s": pp / (p_ms * 1e-3),
+                        "tflops": pp * FLOPS_P2P / (p_ms * 1e-3) / 1e12},
+                "segments": {"pairs": sp_, "ms": s_ms, "pairs_per_s": sp_ / (s_ms * 1e-3),
+                             "tflops": sp_ * FLOPS_SEG / (s_ms * 1e-3) / 1e12},
+                "note": "vpm_induce (particles onto themselves) and vpm_segments_induce (segments onto the "
+                        "particles) alone, compensated, u + grad u; includes each call's packing and epilogue",
+            }
+        except Exception as ex:  # informative, never fatal
+            parts = {"unavailable": str(ex)[:200]}
+
     # the treecode (the O(n log n) variant, outside the timed step) on the 1,000,000-particle
     # BVI wake against the direct plain sum of the same wake (informative)
     tree = None
@@ -612,7 +648,7 @@ def run_ours(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                        "parallelism": "replicas" if ws_n > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_total),
-            "clocks": clk, "plain": plain, "error": err, "wake_convert": wake, "treecode": tree,
+            "clocks": clk, "plain": plain, "error": err, "wake_convert": wake, "sweep_parts": parts, "treecode": tree,
             "kernel_ms": {"sweep_grad": [nl, sms_ms], "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
                           "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL])},
         }
