@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* _
     }
     const float L2 = rx * rx + ry * ry + rz * rz;
     const float cl2 = core * core * L2;
-    const float e = vn == 2 ? cl2 * cl2 : cl2;
+    float e = vn == 2 ? cl2 * cl2 : cl2;
+    if (!(L2 > 0.f)) g = 0.f, e = 1.f;  // a zero-length segment induces nothing; keeps D > 0
     float4* o = out + (size_t)j * S_F4;
     o[0] = make_float4(-ax, -ax, -ay, -ay);
     o[1] = make_float4(-az, -az, rx, rx);
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
             const float margin = 1e-3f * tlo.w;
             Acc<GRAD, false> tf;
             tf.zero();
-            if (A.core_pos && !boxes_near(wbox[warp], tlo, thi, margin * margin))
+            if (A.core_pos && margin > 0.f && !boxes_near(wbox[warp], tlo, thi, margin * margin))
                 segment_tile<GRAD, false, true>(tf, src, cnt, X, Y, Z, A.vn);
             else
                 segment_tile<GRAD, false, false>(tf, src, cnt, X, Y, Z, A.vn);

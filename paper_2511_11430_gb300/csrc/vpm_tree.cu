@@ -549,14 +549,15 @@ __global__ void seg_gather_kernel(const float4* __restrict__ sa, const float4* _
     const float rx = b.x - a.x, ry = b.y - a.y, rz = b.z - a.z;
     const float L2 = rx * rx + ry * ry + rz * rz;
     const float cl2 = core * core * L2;
-    const float e = vn == 2 ? cl2 * cl2 : cl2;
+    float e = vn == 2 ? cl2 * cl2 : cl2, g = a.w;
+    if (!(L2 > 0.f)) g = 0.f, e = 1.f;  // a zero-length segment induces nothing; keeps D > 0
     float4* o = out + (size_t)k * S_F4;
     o[0] = make_float4(-a.x, -a.x, -a.y, -a.y);
     o[1] = make_float4(-a.z, -a.z, rx, rx);
     o[2] = make_float4(ry, ry, rz, rz);
     o[3] = make_float4(-rx, -rx, -ry, -ry);
     o[4] = make_float4(-rz, -rz, -L2, -L2);
-    o[5] = make_float4(a.w, a.w, e, e);
+    o[5] = make_float4(g, g, e, e);
 }
 
 // Segment leaves: the box and sphere of both end points of every segment, and the
@@ -1120,7 +1121,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32, 2) tree_eval_kernel(TreeArgs 
                     any_far = true;
                 } else if (far || level == A.seg.D) {
                     // a segment inside the node's sphere is at most 2 r long
-                    if (A.seg.core_pos && d - rs >= 2e-3f * g.w)
+                    if (A.seg.core_pos && g.w > 0.f && d - rs >= 2e-3f * g.w)
                         segment_run<GRAD, true>(acc, A.seg.ssrc, ns, ne, buf, lane, X, Y, Z, A.seg.vn);
                     else
                         segment_run<GRAD, false>(acc, A.seg.ssrc, ns, ne, buf, lane, X, Y, Z, A.seg.vn);

@@ -92,6 +92,28 @@ def test_segments_random_ragged_and_near(api):
     _check(u, g, ru, rJ, TOL_COMP)
 
 
+def test_segments_of_zero_length(api):
+    """Zero-length segments (b = a) with a nonzero circulation induce nothing (the
+    oracle's L = 0 case): mixed into tiles of ordinary segments, whose far targets take
+    the guard-free path, and as a whole tile of them with targets exactly on their
+    points."""
+    sa, sb = synth.random_segments(5, 256, length=0.2)  # two full 128-segment tiles
+    sb[10:30, :3] = sa[10:30, :3]  # 20 zero-length segments among the first tile
+    pts = np.repeat(sa[:1, :3], 128, axis=0) + np.linspace(0.0, 0.1, 128, dtype=np.float32)[:, None]
+    za = np.concatenate([pts, np.full((128, 1), 0.7, np.float32)], axis=1).astype(np.float32)
+    sa = np.concatenate([sa, za]).astype(np.float32)  # a whole tile of zero-length segments
+    sb = np.concatenate([sb, za]).astype(np.float32)
+    tgt, _ = synth.random_cloud(6, 1000, sigma=0.05)
+    tgt[:5, :3] = za[:5, :3]  # targets on the points of zero-length segments
+    tgt[5:10, :3] = sa[10:15, :3]
+    for core in (0.02, 0.0):
+        ru, rJ = oracle.segments(sa, sb, tgt, core, 2)
+        u, g = api.segments_induce(to_dev(sa), to_dev(sb), to_dev(tgt), core, 2)
+        torch.cuda.synchronize()
+        assert torch.isfinite(u).all() and torch.isfinite(g).all()
+        _check(u, g, ru, rJ, TOL_COMP)
+
+
 @pytest.mark.parametrize("classic", [False, True])
 @pytest.mark.parametrize("compensated", [True, False])
 def test_rhs_config1(api, classic, compensated):

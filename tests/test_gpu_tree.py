@@ -231,6 +231,22 @@ def test_segment_tree_far_field(api):
     assert errs[4][0] < errs[2][0], errs
 
 
+def test_segment_tree_with_zero_length_segments(api):
+    """Zero-length segments with a nonzero circulation in the segment tree (in leaves and
+    in far nodes) induce nothing, as in the direct sum."""
+    w = synth.make(2, n=20000)
+    sa, sb = w.seg_a.copy(), w.seg_b.copy()
+    sb[::7, :3] = sa[::7, :3]
+    strn = np.zeros_like(w.strength)
+    prm = api.Params(sigma=w.sigma, nu=0.0, c_v=w.c_v, seg_core=w.seg_core, compensated=False)
+    P, S, A, B = to_dev(w.pos), to_dev(strn), to_dev(sa), to_dev(sb)
+    dx0, _, _ = api.rhs(P, S, A, B, prm)
+    dx, _, nt = api.rhs_tree(P, S, A, B, prm, theta=0.5, order=4)
+    torch.cuda.synchronize()
+    assert torch.isfinite(dx).all() and torch.isfinite(nt).all()
+    assert rel_l2(planar_to_rows(dx, 3), planar_to_rows(dx0, 3)) <= TREE_TOL_U
+
+
 def test_segment_tree_first_order_vatistas_core(api):
     """With the n = 1 core, which decays slowly (a far node must be about 700 cores
     away), the segment tree still matches the direct sum."""
