@@ -40,10 +40,12 @@
 // walk every target evaluates the local expansion once.  theta = 0 opens every
 // node, which gives the direct sum.
 //
-// Right-hand side (vpm_rhs_tree).  The tree's u and grad u plus the segments' (the
-// direct segment sweep) give Vreman's eddy viscosity, the stretching and dx/dt per
-// particle; the PSE term of Eq. 5 is then summed by a second walk of the same tree
-// that visits only the nodes within 7 sigma of each target leaf.
+// Right-hand side (vpm_rhs_tree).  The segments form a second source tree that every
+// target leaf walks after the particle tree (far nodes into the same local expansion,
+// the others by the exact segment kernel); the summed u and grad u give Vreman's eddy
+// viscosity, the stretching and dx/dt per particle; the PSE term of Eq. 5 is then
+// summed by a second walk of the particle tree that visits only the nodes within
+// 7 sigma of each target leaf.
 #include <math.h>
 
 #include <algorithm>
