@@ -1380,15 +1380,28 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
             const long long k = (long long)id + 1 - (1LL << level);
             const long long ns = run_begin(k, A.n, level), ne = run_begin(k + 1, A.n, level);
             const int cnt = (int)(ne - ns);  // a leaf: at most TREE_STAGE
+            // stage the leaf; a source farther than 7 sigma from the target group's sphere
+            // reaches none of its targets and is left out (warp-uniformly, by ballot)
             __syncwarp();
+            unsigned keep[TREE_STAGE / 32];
 #pragma unroll
             for (int h = 0; h < TREE_STAGE / 32; ++h) {
                 const int t = lane + 32 * h;
-                if (t < cnt) bp[t] = A.sp[ns + t], bg[t] = A.sg[ns + t];
+                bool k = false;
+                if (t < cnt) {
+                    const float4 q = A.sp[ns + t];
+                    bp[t] = q, bg[t] = A.sg[ns + t];
+                    const float ex = q.x - tg.x, ey = q.y - tg.y, ez = q.z - tg.z;
+                    const float lim = tg.w + A.sep;
+                    k = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < lim * lim;
+                }
+                keep[h] = __ballot_sync(0xffffffffu, k);
             }
             __syncwarp();
-#pragma unroll 1
-            for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+            for (int hh = 0; hh < TREE_STAGE / 32; ++hh)
+            for (unsigned m = keep[hh]; m; m &= m - 1) {
+                const int j = 32 * hh + __ffs(m) - 1;
                 const float4 pj = bp[j], gj = bg[j];
                 const float ntj = gj.w;
 #pragma unroll
@@ -1397,7 +1410,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
                     const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
                     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                     if (r2 < A.cut2) {
-                        const float w = fmaf(0.5f, ntj, h ? base1 : base0) * expf(-r2 * A.inv2s2);
+                        const float w = fmaf(0.5f, ntj, h ? base1 : base0) * __expf(-r2 * A.inv2s2);
                         const float vi = pi.w, vj = pj.w;
                         const float tx = __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x));
                         const float ty = __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y));
