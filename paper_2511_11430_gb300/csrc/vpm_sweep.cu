@@ -571,14 +571,29 @@ __global__ void __launch_bounds__(PSE_T) pse_kernel(const float4* __restrict__ p
             const int tile = tb + __ffs(mask) - 1;
             mask &= mask - 1;
             const int j0 = tile * SRC_TILE, cnt = min(SRC_TILE, n - j0);
+            // stage the tile; a source at least 7 sigma from both of the warp's target boxes
+            // reaches none of its targets and is left out (warp-uniformly, by ballot)
             __syncwarp();
-            for (int q = lane; q < cnt; q += 32) {
-                sp[warp][q] = pos[j0 + q];
-                sg[warp][q] = str[j0 + q];
-                snt[warp][q] = nu_t ? nu_t[j0 + q] : 0.f;
+            unsigned keep[SRC_TILE / 32];
+#pragma unroll
+            for (int h = 0; h < SRC_TILE / 32; ++h) {
+                const int q = lane + 32 * h;
+                bool kp = false;
+                if (q < cnt) {
+                    const float4 pq = pos[j0 + q];
+                    sp[warp][q] = pq;
+                    sg[warp][q] = str[j0 + q];
+                    snt[warp][q] = nu_t ? nu_t[j0 + q] : 0.f;
+                    const float4 pt = make_float4(pq.x, pq.y, pq.z, 0.f);
+                    kp = boxes_near(wbox[warp], pt, pt, cut2);
+                }
+                keep[h] = __ballot_sync(0xffffffffu, kp);
             }
             __syncwarp();
-            for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+            for (int h = 0; h < SRC_TILE / 32; ++h)
+            for (unsigned m = keep[h]; m; m &= m - 1) {
+                const int j = 32 * h + __ffs(m) - 1;
                 const float4 pj = sp[warp][j], gj = sg[warp][j];
                 const float ntj = snt[warp][j];
                 pse_pair(p0, g0, base0, pj, gj, ntj, inv2s2, cut2, a0x, a0y, a0z);
