@@ -38,8 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # hover wake (100,000 particles, 5,120 segments), from one ncu capture of that launch
 # (profiles/sweep_kernel_hover4_100k.md); valid only while the kernel's sources hash to
 # SWEEP_SRC_SHA256, else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = 11_826_688 + 6_912
-SWEEP_SRC_SHA256 = "6a04d7b6221156e278767381ddf64fb5f2d5c7eb207025ebd6c92f6e51baac05"
+SWEEP_TRAFFIC_BYTES = 11_791_872 + 3_584
+SWEEP_SRC_SHA256 = "8310509dd5e9d952b30014f01a599cda4f59934a5e8bc295c4982abcda745572"
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 

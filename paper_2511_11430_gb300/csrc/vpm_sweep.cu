@@ -438,10 +438,13 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
             sk.first_at_or_after(c0, tt, kk);
             if (tt != t || sk.unit_start(tt, kk) >= hi_b) continue;  // block b ran no unit of tile t
             const float* P = E.part + (size_t)(b + t) * rows * TGT_TILE + l;
-            for (int c = 0; c < E.ncomp; ++c) {
-                double v = (double)P[(size_t)c * TGT_TILE];
-                if (E.comp) v += (double)P[(size_t)(E.ncomp + c) * TGT_TILE];
-                acc[c] += v;
+#pragma unroll
+            for (int c = 0; c < 17; ++c) {  // a constant bound keeps acc in registers
+                if (c < E.ncomp) {
+                    double v = (double)P[(size_t)c * TGT_TILE];
+                    if (E.comp) v += (double)P[(size_t)(E.ncomp + c) * TGT_TILE];
+                    acc[c] += v;
+                }
             }
         }
     }
