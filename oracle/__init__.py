@@ -64,6 +64,7 @@ def _load():
                 "orc_vreman": [P, i64, d, d, P],
                 "orc_stretch": [P, P, i64, i, P],
                 "orc_pse": [P, P, P, i64, d, d, P],
+                "orc_pse_at": [P, P, P, i64, LP, i64, d, d, P],
                 "orc_rhs": [P, P, i64, P, P, i64, d, d, d, d, i, P, i, P, P, P],
                 "orc_step": [P, P, P, i64, P, P, i64, d, d, d, d, i, P, i, d, i],
                 "orc_aic_build": [P, P, P, i64, d, i, P],
@@ -155,6 +156,17 @@ def pse(pos, strength, nu_t, sigma, nu):
     nt = None if nu_t is None else _f64(nu_t).ravel()
     p = np.zeros((pos.shape[0], 3))
     _load().orc_pse(_p(pos), _p(strength), _p(nt), pos.shape[0], float(sigma), float(nu), _p(p))
+    return p
+
+
+def pse_at(pos, strength, nu_t, sigma, nu, idx):
+    """The exchange term of pse() at the particles idx only, each summed over all particles."""
+    pos, strength = _f64(pos, 4), _f64(strength, 4)
+    nt = None if nu_t is None else _f64(nu_t).ravel()
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    p = np.zeros((ix.size, 3))
+    _load().orc_pse_at(_p(pos), _p(strength), _p(nt), pos.shape[0],
+                       ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ix.size, float(sigma), float(nu), _p(p))
     return p
 
 

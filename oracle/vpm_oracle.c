@@ -303,24 +303,37 @@ void orc_stretch(const double* J, const double* str, int64_t n, int classic, dou
 /* with nu_ij = nu + (nu_t,i + nu_t,j)/2 carrying the Vreman eddy viscosity.  */
 /* The i == j term is zero by construction.                                   */
 /* ------------------------------------------------------------------------- */
+static void pse_one(const double* pos, const double* str, const double* nu_t, int64_t n, int64_t i, double sigma,
+                    double nu, double* p)
+{
+    const double norm = 1.0 / pow(2.0 * PI * sigma * sigma, 1.5);
+    double acc[3] = {0, 0, 0};
+    const double vi = pos[4 * i + 3];
+    for (int64_t j = 0; j < n; ++j) {
+        double r[3] = {pos[4 * i] - pos[4 * j], pos[4 * i + 1] - pos[4 * j + 1], pos[4 * i + 2] - pos[4 * j + 2]};
+        const double rho2 = dot(r, r) / (sigma * sigma);
+        const double zeta = norm * exp(-0.5 * rho2);
+        const double nij = nu + 0.5 * ((nu_t ? nu_t[i] : 0.0) + (nu_t ? nu_t[j] : 0.0));
+        const double vj = pos[4 * j + 3];
+        for (int a = 0; a < 3; ++a) acc[a] += nij * (vi * str[4 * j + a] - vj * str[4 * i + a]) * zeta;
+    }
+    for (int a = 0; a < 3; ++a) p[a] = 2.0 / (sigma * sigma) * acc[a];
+}
+
 void orc_pse(const double* pos, const double* str, const double* nu_t, int64_t n, double sigma, double nu,
              double* p)
 {
-    const double norm = 1.0 / pow(2.0 * PI * sigma * sigma, 1.5);
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t i = 0; i < n; ++i) {
-        double acc[3] = {0, 0, 0};
-        const double vi = pos[4 * i + 3];
-        for (int64_t j = 0; j < n; ++j) {
-            double r[3] = {pos[4 * i] - pos[4 * j], pos[4 * i + 1] - pos[4 * j + 1], pos[4 * i + 2] - pos[4 * j + 2]};
-            const double rho2 = dot(r, r) / (sigma * sigma);
-            const double zeta = norm * exp(-0.5 * rho2);
-            const double nij = nu + 0.5 * ((nu_t ? nu_t[i] : 0.0) + (nu_t ? nu_t[j] : 0.0));
-            const double vj = pos[4 * j + 3];
-            for (int a = 0; a < 3; ++a) acc[a] += nij * (vi * str[4 * j + a] - vj * str[4 * i + a]) * zeta;
-        }
-        for (int a = 0; a < 3; ++a) p[3 * i + a] = 2.0 / (sigma * sigma) * acc[a];
-    }
+    for (int64_t i = 0; i < n; ++i) pse_one(pos, str, nu_t, n, i, sigma, nu, &p[3 * i]);
+}
+
+/* The same sum at the k particles idx[0..k) only, each over all n particles
+ * (p[k][3]); for sampled checks of large particle sets. */
+void orc_pse_at(const double* pos, const double* str, const double* nu_t, int64_t n, const int64_t* idx, int64_t k,
+                double sigma, double nu, double* p)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < k; ++t) pse_one(pos, str, nu_t, n, idx[t], sigma, nu, &p[3 * t]);
 }
 
 /* ------------------------------------------------------------------------- */

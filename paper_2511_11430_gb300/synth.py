@@ -435,6 +435,17 @@ def sample_targets(seed, n, k):
     return np.sort(rng.choice(n, size=k, replace=False))
 
 
+def sample_runs(seed, n, n_runs, run, lo=0, hi=None):
+    """n_runs runs of ``run`` consecutive particle indices in [lo, hi), sorted and
+    non-overlapping (sampled checks of large wakes: consecutive particles of a
+    filament share their neighbourhoods)."""
+    hi = n if hi is None else hi
+    rng = np.random.default_rng(seed + 2000)
+    slots = (hi - lo) // run
+    starts = lo + run * np.sort(rng.choice(slots, size=min(n_runs, slots), replace=False))
+    return np.concatenate([np.arange(s, s + run) for s in starts])
+
+
 def rotor_wake_edges(seed, n_rows, n_span=40, n_blades=4, dpsi_deg=5.0):
     """Edges of n_rows x n_blades near-wake panel rows behind a hover rotor (FP64):
     each row spans r = 0.15R..R between the trailing-edge line at one azimuth and the
