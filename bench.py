@@ -1,16 +1,20 @@
 #!/usr/bin/env python3
 """Throughput of the vortex-particle hot path on GB300.
 
-One step = one pass of the whole hot path over the 4-blade hover wake
-(100,000 particles, 5,120 blade segments, 1,280 control points, sigma = 0.01 R):
-  pack the FP64 state to FP32, induced velocity at the control points, AIC build
-  and FP32-LU/FP64-refined solve, one low-storage RK3 step (three right-hand
-  sides, each a particle + segment u + grad u sweep, Vreman, stretching, PSE,
-  stage update), and the adjoint of the downwash loss at the control points.
-Metric: particle-particle u + grad u pair interactions per second (3 N (N - 1) per
+One step = one pass of the whole hot path over a synthetic rotor wake:
+  pack the FP64 particle state to FP32, the particles' velocity at the blade control
+  points, the AIC build and its FP32-LU / FP64-refined solve, the blade rings'
+  segments with the solved circulations, one stage of the low-storage RK3 time
+  update (its right-hand side: the particle + segment u + grad u sweep, Vreman,
+  stretching, PSE; then the FP64 stage update), and the adjoint of the downwash
+  loss at the control points.  The stage index cycles 0, 1, 2, so three
+  consecutive steps are one full RK3 time step.
+Default workload: two counter-rotating 3-blade rotors (2,000,000 particles, 7,680
+segments, 1,920 control points) -- the largest single-GPU configuration.
+Metric: particle-particle u + grad u pair interactions per second (N (N - 1) per
 step), compensated FP32.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config 1..5]
 """
 from __future__ import annotations
 
@@ -20,7 +24,6 @@ import os
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -34,48 +37,55 @@ UNIT = "pair-interactions/s"
 FLOPS_P2P = 54   # u + grad u, far-field operation tree, FFMA = 2 flops
 FLOPS_SEG = 120  # Vatistas segment u + grad u, same counting convention
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one sweep_kernel<grad, compensated, stretch> launch on the
-# hover wake (100,000 particles, 5,120 segments), from one ncu capture of that launch
-# (profiles/sweep_kernel_hover4_100k.md); valid only while the kernel's sources hash to
-# SWEEP_SRC_SHA256, else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = 11_791_872 + 3_584
-SWEEP_SRC_SHA256 = "8310509dd5e9d952b30014f01a599cda4f59934a5e8bc295c4982abcda745572"
+TOL = {"compensated": 2e-6, "plain": 1e-4, "nu_t": 1e-5}
+# DRAM bytes (read + write) of one sweep_kernel<grad, compensated, stretch> launch, from
+# one ncu capture of that launch per workload (profiles/sweep_kernel_*.md), keyed by
+# (particles, segments); valid only while the kernel's sources hash to SWEEP_SRC_SHA256,
+# else the bench reports traffic null.
+SWEEP_TRAFFIC_BYTES = {}
+SWEEP_SRC_SHA256 = ""
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 
 
-def sweep_traffic(n, m):
-    """The captured DRAM traffic of the sweep launch, if the capture matches the sources
-    and the workload (hover, 100,000 particles, 5,120 segments)."""
+def sweep_src_hash():
     import hashlib
 
     h = hashlib.sha256()
-    root = os.path.dirname(os.path.abspath(__file__))
     for f in SWEEP_SRC:
-        with open(os.path.join(root, f), "rb") as fh:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != SWEEP_SRC_SHA256 or n != 100_000 or m != 5_120:
+    return h.hexdigest()
+
+
+def sweep_traffic(n, m):
+    """The captured DRAM traffic of one sweep launch, if a capture matches the sources
+    and the workload."""
+    if sweep_src_hash() != SWEEP_SRC_SHA256:
         return None
-    return SWEEP_TRAFFIC_BYTES
+    return SWEEP_TRAFFIC_BYTES.get((n, m))
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--particles", type=int, default=None, help="override the particle count (testing only)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the informative extras (segment/particle parts, treecode, wake conversion, "
+                         "the hover-wake line)")
     ap.add_argument("--cpu-seconds", type=float, default=None,
-                    help="seconds of oracle work per CPU-baseline sample (default 12; reference arm: 60 s over all steps)")
-    ap.add_argument("--no-tree", action="store_true", help="skip the informative treecode timing")
+                    help="reference arm: seconds of oracle work per step (default: 60 s over all steps)")
+    ap.add_argument("--error-targets", type=int, default=1024)
     ap.add_argument("--part", choices=["aic", "wake", "tree", "rotor"], default=None,
                     help="time one component alone (for profiling; prints a text line, not the JSON contract)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def run_rotor(args):
@@ -84,8 +94,6 @@ def run_rotor(args):
     step, for --steps revolutions at 10 deg per step (after --warmup revolutions, whose
     loads are reported too).  Prints the thrust and torque coefficients averaged per
     revolution, the particle count and the wall time per step."""
-    import time
-
     import torch
 
     from paper_2511_11430_gb300 import build, synth, wake
@@ -116,13 +124,14 @@ def run_rotor(args):
 
 def run_part(args):
     """One component, repeated --steps times after --warmup: the AIC build + solve of the
-    hover blade lattice, the conversion of 2,000 hover wake rows, or the treecode
-    (theta 0.5, order 4) on the 1,000,000-particle BVI wake (--particles to shrink it)."""
+    blade lattice, the conversion of 2,000 hover wake rows, or the treecode (theta 0.5,
+    order 4) on the 1,000,000-particle BVI wake (--particles to shrink it)."""
     import torch
 
     from paper_2511_11430_gb300 import api, build, synth
 
     build.build()
+
     def T(a, dt=None):
         t = torch.from_numpy(np.ascontiguousarray(a))
         return (t if dt is None else t.to(dt)).cuda()
@@ -174,7 +183,9 @@ def dist_info():
 
 
 def workload_desc(w):
-    return (f"{w.name}: {w.meta.get('blades')}-blade rotor wake, {w.n:,} Gaussian particles (sigma {w.sigma:g} R), "
+    rot = w.meta.get("rotors")
+    head = f"{rot} x {w.meta.get('blades')}-blade rotors" if rot else f"{w.meta.get('blades')}-blade rotor"
+    return (f"{w.name}: {head}, {w.n:,} Gaussian particles (sigma {w.sigma:g} R), "
             f"{w.m:,} Vatistas blade segments, {w.n_ctrl:,} control points")
 
 
@@ -227,7 +238,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# the FP64 oracle on the host cores (CPU baseline and reference arm)
+# the FP64 oracle on the host cores (CPU baseline, reference values, reference arm)
 # ---------------------------------------------------------------------------
 def oracle_rate(w, seconds, cores):
     """P2P u + grad u pair interactions/s of the FP64 oracle on a bounded sample of
@@ -250,24 +261,55 @@ def oracle_rate(w, seconds, cores):
         k = min(n, int(k * max(2.0, seconds / max(dt, 1e-3) * 0.6)))
 
 
-def oracle_values(w, idx):
-    """The FP64 oracle's u and grad u at the sampled particles idx (cpu_baseline leg)."""
-    import oracle
-
-    return oracle.p2p(w.pos, w.strength, w.pos[idx], w.sigma)
-
-
-def oracle_threads_default(cores):
-    import oracle
-
-    oracle.set_threads(cores)
-
-
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+def error_samples(w, k):
+    """Sampled particles of the error report: k random ones (u, grad u, dx/dt, nu_t and
+    dGamma/dt without the eddy viscosity's exchange coupling) and runs of consecutive
+    particles for the full right-hand side (all particles of a small wake)."""
+    from paper_2511_11430_gb300 import synth
+
+    idx_u = synth.sample_targets(11, w.n, k)
+    idx_r = np.arange(w.n) if w.n <= 4000 else synth.sample_runs(12, w.n, 2, 16)
+    return idx_u, idx_r
+
+
+def oracle_reference(w, idx_u, idx_r, cores):
+    """The FP64 oracle's values at the sampled particles, and its timed rate (the
+    cpu_baseline leg: u + grad u at idx_u against every particle)."""
+    import oracle
+    from oracle import sampled
+
+    oracle.build()
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    u, J = oracle.p2p(w.pos, w.strength, w.pos[idx_u], w.sigma)
+    dt = time.perf_counter() - t0
+    rate = len(idx_u) * (w.n - 1) / dt
+    us, Js = oracle.segments(w.seg_a, w.seg_b, w.pos[idx_u], w.seg_core, w.vatistas_n)
+    Jt = J + Js
+    ref = {"u": u, "grad_u": J, "dxdt": u + us + np.asarray(w.u_inf), "nu_t": oracle.vreman(Jt, w.sigma, w.c_v),
+           "dGdt_cv0": oracle.stretch(Jt, w.strength[idx_u]) + oracle.pse_at(w.pos, w.strength, None, w.sigma, w.nu,
+                                                                             idx_u)}
+    rdx, rdG, rnut = sampled.rhs_at(w, idx_r)
+    ref.update({"dxdt_r": rdx, "dGdt": rdG, "nu_t_r": rnut})
+    # one core, on a sample of about 3 s
+    k1 = max(8, int(len(idx_u) * 3.0 / max(dt * cores, 1e-3)))
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.p2p(w.pos, w.strength, w.pos[idx_u[:k1]], w.sigma)
+    d1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(idx_u)} sampled targets x all {w.n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)",
+           "single_thread": {"value": min(k1, len(idx_u)) * (w.n - 1) / d1, "unit": UNIT,
+                             "sample": f"{min(k1, len(idx_u))} sampled targets x all {w.n:,} sources ({d1:.1f} s)"}}
+    return ref, cpu
 
 
 def max_over_ranks(dist, ms, device):
@@ -317,10 +359,329 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args):
+class HotPath:
+    """The benchmark step on one workload, through the public API."""
+
+    def __init__(self, w, dev):
+        import torch
+
+        from paper_2511_11430_gb300 import api
+
+        self.api, self.w, self.dev = api, w, dev
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        self.n, self.m, self.K = w.n, w.m, w.n_ctrl
+        self.x0 = np.ascontiguousarray(w.pos[:, :3].astype(np.float64).T)
+        self.G0 = np.ascontiguousarray(w.strength[:, :3].astype(np.float64).T)
+        self.vol = T(w.pos[:, 3].copy())
+        self.rings, self.colloc, self.normal, self.vrel = T(w.rings), T(w.colloc), T(w.normal), T(w.v_rel)
+        self.nrm = self.normal[:, :3].t().contiguous()
+        self.T = T
+
+    def params(self, compensated):
+        w = self.w
+        return self.api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf,
+                               compensated=compensated)
+
+    def new_state(self):
+        import torch
+
+        return {"x": self.T(self.x0), "G": self.T(self.G0),
+                "q": torch.zeros((6, self.n), dtype=torch.float64, device=self.dev), "k": 0}
+
+    def new_bufs(self):
+        import torch
+
+        n, dev = self.n, self.dev
+        return {"ws": self.api.Workspace(dev), "ws_aic": self.api.Workspace(dev), "ws_adj": self.api.Workspace(dev),
+                "pos": torch.empty((n, 4), dtype=torch.float32, device=dev),
+                "str": torch.empty((n, 4), dtype=torch.float32, device=dev),
+                "sa": torch.empty((4 * self.K, 4), dtype=torch.float32, device=dev),
+                "sb": torch.empty((4 * self.K, 4), dtype=torch.float32, device=dev)}
+
+    def step(self, st, prm, b, x=None, G=None, q=None, vol=None):
+        """One pass of the hot path: one RK3 stage of the particles with the blade
+        circulation solved for the current wake.  Returns (Gamma_b, dL/dx, dL/dGamma)."""
+        api, w = self.api, self.w
+        x = st["x"] if x is None else x
+        G = st["G"] if G is None else G
+        q = st["q"] if q is None else q
+        vol = self.vol if vol is None else vol
+        pos, strn = api.pack_state(x, G, vol, b["pos"], b["str"])
+        u_c = api.induce(pos, strn, self.colloc, w.sigma, compensated=prm.compensated, grad=False, ws=b["ws"])
+        A, rhs = api.aic_build(self.rings, self.colloc, self.normal, w.seg_core, 2, v_rel=self.vrel, w_ind=u_c)
+        gam, _, _ = api.aic_solve(A, rhs, tol=1e-12, max_iter=30, ws=b["ws_aic"])
+        sa, sb = api.ring_segments(self.rings, gam, b["sa"], b["sb"])
+        api.rk3_stage(st["k"], x, G, q, vol, sa, sb, prm, w.dt, ws=b["ws"])
+        st["k"] = (st["k"] + 1) % 3
+        g = 2.0 * (u_c * self.nrm).sum(0, keepdim=True) * self.nrm  # d/du of sum_k (u_k . n_k)^2
+        dx, dG = api.induce_backward(pos, strn, self.colloc, w.sigma, g.contiguous(), compensated=prm.compensated,
+                                     ws=b["ws_adj"])
+        return gam, dx, dG
+
+
+def timed_loop(hp, prm, steps, warmup, flush, dist, trace=False):
+    """W untimed steps, then K steps, each bracketed by CUDA events on the launching
+    stream after an L2 flush outside the events.  Returns (total ms, trace)."""
     import torch
 
-    from paper_2511_11430_gb300 import _lib, api, build, synth
+    from paper_2511_11430_gb300 import _lib
+
+    api = hp.api
+    st = hp.new_state()
+    b = hp.new_bufs()
+    for _ in range(warmup):
+        hp.step(st, prm, b)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    if trace:
+        api.trace_enable(True)
+        api.trace_reset()
+    s = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        hp.step(st, prm, b)
+        e1.record(s)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    tr = None
+    if trace:
+        tr = {k: api.trace_read(k) for k in (_lib.VPM_TRACE_ALL, _lib.VPM_TRACE_SWEEP, _lib.VPM_TRACE_ADJOINT,
+                                             _lib.VPM_TRACE_PSE, _lib.VPM_TRACE_SWEEP_VEL)}
+        api.trace_enable(False)
+    return total, tr
+
+
+def e2e_loop(hp, prm, steps, warmup, flush, dist):
+    """The same step end to end through the public API from pinned host buffers: each
+    timed step copies its inputs (FP64 state and RK register, volumes, blade geometry)
+    host -> device, runs, and copies its results (state, register, blade circulation,
+    adjoint) back, all inside the step's events (the L2 flush stays outside)."""
+    import torch
+
+    n, K = hp.n, hp.K
+    w = hp.w
+    dev = hp.dev
+    xh = torch.from_numpy(hp.x0).pin_memory()
+    Gh = torch.from_numpy(hp.G0).pin_memory()
+    qh = torch.zeros((6, n), dtype=torch.float64).pin_memory()
+    volh = torch.from_numpy(w.pos[:, 3].copy()).pin_memory()
+    geo_h = [torch.from_numpy(a).pin_memory() for a in (w.rings, w.colloc, w.normal, w.v_rel)]
+    xo, Go, qo = torch.empty_like(xh).pin_memory(), torch.empty_like(Gh).pin_memory(), torch.empty_like(qh).pin_memory()
+    gho = torch.empty((K,), dtype=torch.float64).pin_memory()
+    dxo = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    dGo = torch.empty((3, n), dtype=torch.float32).pin_memory()
+    x_d, G_d, q_d = (torch.empty_like(t, device=dev) for t in (xh, Gh, qh))
+    vol_d = torch.empty_like(volh, device=dev)
+    geo_d = [torch.empty_like(h, device=dev) for h in geo_h]
+    b = hp.new_bufs()
+    st = {"k": 0}
+
+    def one():
+        x_d.copy_(xh, non_blocking=True)
+        G_d.copy_(Gh, non_blocking=True)
+        q_d.copy_(qh, non_blocking=True)
+        vol_d.copy_(volh, non_blocking=True)
+        for d_, h_ in zip(geo_d, geo_h):
+            d_.copy_(h_, non_blocking=True)
+        hp.rings, hp.colloc, hp.normal, hp.vrel = geo_d
+        hp.nrm = hp.normal[:, :3].t().contiguous()
+        gam, dx, dG = hp.step(st, prm, b, x=x_d, G=G_d, q=q_d, vol=vol_d)
+        xo.copy_(x_d, non_blocking=True)
+        Go.copy_(G_d, non_blocking=True)
+        qo.copy_(q_d, non_blocking=True)
+        gho.copy_(gam, non_blocking=True)
+        dxo.copy_(dx, non_blocking=True)
+        dGo.copy_(dG, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    s = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        one()
+        e1.record(s)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    h2d = (xh.numel() + Gh.numel() + qh.numel()) * 8 + volh.numel() * 4 + sum(h.numel() * 4 for h in geo_h)
+    d2h = (xo.numel() + Go.numel() + qo.numel() + gho.numel()) * 8 + (dxo.numel() + dGo.numel()) * 4
+    return total, int(h2d), int(d2h)
+
+
+def gpu_error_values(hp, idx_u, idx_r):
+    """The GPU's outputs at the sampled particles, both precision forms, from full-size
+    launches on the initial state: vpm_induce (u, grad u), vpm_rhs with the workload's
+    Vreman coefficient (dx/dt, nu_t, dGamma/dt) and with c_V = 0 (dGamma/dt without
+    the eddy viscosity)."""
+    import torch
+
+    api, w = hp.api, hp.w
+    P, S = hp.T(w.pos), hp.T(w.strength)
+    sa, sb = hp.T(w.seg_a), hp.T(w.seg_b)
+    ws = api.Workspace(hp.dev)
+    rows = lambda t, ix: t[:, ix].double().cpu().numpy().T
+    out = {}
+    for form, comp in (("compensated", True), ("plain", False)):
+        u, g = api.induce(P, S, P, w.sigma, compensated=comp, ws=ws)
+        prm = hp.params(comp)
+        dx, dG, nut = api.rhs(P, S, sa, sb, prm, ws=ws)
+        prm0 = hp.params(comp)
+        prm0.c_v = 0.0
+        _, dG0, _ = api.rhs(P, S, sa, sb, prm0, ws=ws)
+        torch.cuda.synchronize()
+        out[form] = {"u": rows(u, idx_u), "grad_u": rows(g, idx_u).reshape(-1, 3, 3), "dxdt": rows(dx, idx_u),
+                     "nu_t": nut[idx_u].double().cpu().numpy(), "dGdt_cv0": rows(dG0, idx_u),
+                     "dGdt": rows(dG, idx_r), "dxdt_r": rows(dx, idx_r)}
+    return out
+
+
+def error_report(gpu, ref, idx_u, idx_r):
+    rel = lambda a_, b_: float(np.linalg.norm(a_ - b_) / np.linalg.norm(b_))
+    rep = {"sample_targets": len(idx_u), "rhs_sample_targets": len(idx_r),
+           "rhs_sample": ("all particles" if len(idx_r) > 32 else
+                          f"{len(idx_r)} particles in runs of 16 consecutive ones (shared exchange neighbourhoods)"),
+           "tolerance": TOL}
+    for form in ("compensated", "plain"):
+        g = gpu[form]
+        rep[form] = {"u": rel(g["u"], ref["u"]), "grad_u": rel(g["grad_u"], ref["grad_u"]),
+                     "dxdt": rel(g["dxdt"], ref["dxdt"]), "nu_t": rel(g["nu_t"], ref["nu_t"]),
+                     "dGdt_cv0": rel(g["dGdt_cv0"], ref["dGdt_cv0"]), "dGdt": rel(g["dGdt"], ref["dGdt"])}
+    rep["keys"] = ("u, grad_u, dxdt, nu_t, dGdt_cv0 (stretching + exchange at nu, c_V = 0) on sample_targets random "
+                   "particles; dGdt (the full right-hand side with the Vreman exchange coupling) on "
+                   "rhs_sample_targets")
+    return rep
+
+
+def roofline(tr, n, m, sms, clk):
+    from paper_2511_11430_gb300 import _lib
+
+    sm_max = 2070.0
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x FFMA x max SM clock, TFLOP/s
+    nl, sms_ms = tr[_lib.VPM_TRACE_SWEEP]
+    avg_ms = sms_ms / max(nl, 1)
+    flops_launch = FLOPS_P2P * n * (n - 1) + FLOPS_SEG * n * m
+    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": sweep_traffic(n, m), "kernel": "sweep_kernel<grad, compensated, stretch>", "launches": nl,
+            "avg_launch_ms": avg_ms, "flops_per_launch": flops_launch,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {sm_max:.0f} MHz max SM clock (derived)"}
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+    return roof
+
+
+def extras(hp, args, flush, rank):
+    """Informative figures outside the timed step: the particle and segment parts of the
+    sweep alone, the treecode on the 1M BVI wake, the wake conversion, and (when the
+    main workload is another one) the hover wake's step rate."""
+    import torch
+
+    from paper_2511_11430_gb300 import api, synth
+
+    out = {}
+    dev = hp.dev
+    s = torch.cuda.current_stream()
+
+    def ms_of(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    w = hp.w
+    n, m = w.n, w.m
+    try:
+        P, S = hp.T(w.pos), hp.T(w.strength)
+        sa, sb = hp.T(w.seg_a), hp.T(w.seg_b)
+        pws = api.Workspace(dev)
+        reps = 1 if n >= 1_000_000 else 3
+        p_ms = ms_of(lambda: api.induce(P, S, P, w.sigma, compensated=True, ws=pws), reps)
+        pp_ms = ms_of(lambda: api.induce(P, S, P, w.sigma, compensated=False, ws=pws), reps)
+        s_ms = ms_of(lambda: api.segments_induce(sa, sb, P, w.seg_core, 2, compensated=True, ws=pws), 3)
+        pp, sp_ = n * (n - 1), n * m
+        out["sweep_parts"] = {
+            "p2p": {"pairs": pp, "ms": p_ms, "pairs_per_s": pp / (p_ms * 1e-3),
+                    "tflops": pp * FLOPS_P2P / (p_ms * 1e-3) / 1e12},
+            "p2p_plain": {"pairs": pp, "ms": pp_ms, "pairs_per_s": pp / (pp_ms * 1e-3),
+                          "tflops": pp * FLOPS_P2P / (pp_ms * 1e-3) / 1e12},
+            "segments": {"pairs": sp_, "ms": s_ms, "pairs_per_s": sp_ / (s_ms * 1e-3),
+                         "tflops": sp_ * FLOPS_SEG / (s_ms * 1e-3) / 1e12},
+            "note": "vpm_induce (particles onto themselves) and vpm_segments_induce (segments onto the particles) "
+                    "alone, u + grad u; includes each call's packing and epilogue"}
+        del P, S, pws
+    except Exception as ex:  # informative, never fatal
+        out["sweep_parts"] = {"unavailable": str(ex)[:200]}
+
+    if args.config != 2:
+        try:
+            h2 = HotPath(synth.make(2), dev)
+            tot, tr2 = timed_loop(h2, h2.params(True), max(args.steps, 6), max(args.warmup, 3), flush, None, True)
+            k2 = max(args.steps, 6)
+            from paper_2511_11430_gb300 import _lib
+
+            nl, sw = tr2[_lib.VPM_TRACE_SWEEP]
+            out["hover4_100k"] = {"value": h2.n * (h2.n - 1) * k2 / (tot * 1e-3), "unit": UNIT, "steps": k2,
+                                  "ms_per_step": tot / k2, "sweep_launch_ms": sw / max(nl, 1),
+                                  "workload": workload_desc(h2.w)}
+        except Exception as ex:
+            out["hover4_100k"] = {"unavailable": str(ex)[:200]}
+
+    try:
+        wt = synth.make(3)
+        Pt = torch.from_numpy(wt.pos).to(dev)
+        St = torch.from_numpy(wt.strength).to(dev)
+        tws = api.Workspace(dev)
+        tms = ms_of(lambda: api.tree_induce(Pt, St, wt.sigma, theta=0.5, order=4, ws=tws), 3)
+        prm_t = api.Params(sigma=wt.sigma, nu=wt.nu, c_v=wt.c_v, seg_core=wt.seg_core, u_inf=wt.u_inf,
+                           compensated=False)
+        At, Bt = torch.from_numpy(wt.seg_a).to(dev), torch.from_numpy(wt.seg_b).to(dev)
+        rms = ms_of(lambda: api.rhs_tree(Pt, St, At, Bt, prm_t, theta=0.5, order=4, ws=tws), 2)
+        out["treecode"] = {"particles": wt.n, "theta": 0.5, "order": 4, "ms": tms, "rhs_ms": rms,
+                           "note": "O(n log n) variant on the 1M BVI wake (informative)"}
+        del Pt, St, At, Bt, tws
+    except Exception as ex:
+        out["treecode"] = {"unavailable": str(ex)[:200]}
+
+    try:
+        ea, eb, eg, egn, ehn, etr, ds_tip = synth.rotor_wake_edges(5, 2000)
+        Td = lambda a_, dt_: torch.from_numpy(np.ascontiguousarray(a_)).to(dt_).to(dev)
+        wa, wb, wg, wgn = (Td(q, torch.float64) for q in (ea, eb, eg, egn))
+        whn, wtr = Td(ehn, torch.int32), Td(etr, torch.int32)
+        wws = api.Workspace(dev)
+        xw, _ = api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, ws=wws)
+        npart = int(xw.shape[1])
+        wms = ms_of(lambda: api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn,
+                                             capacity=npart, ws=wws), 5)
+        m_e = len(ea)
+        algo = 72 * m_e + 16 * m_e + 48 * npart
+        out["wake_convert"] = {"edges": m_e, "particles": npart, "ms": wms, "particles_per_s": npart / (wms * 1e-3),
+                               "algorithmic_bytes": algo, "achieved_gbs": algo / (wms * 1e-3) / 1e9,
+                               "note": "device time of one vpm_wake_convert call incl. its one host sync"}
+    except Exception as ex:
+        out["wake_convert"] = {"unavailable": str(ex)[:200]}
+    return out
+
+
+def run_ours(args):
+    import torch
 
     ws_n, rank, local = dist_info()
     dev = torch.device("cuda", local)
@@ -330,309 +691,61 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    from paper_2511_11430_gb300 import _lib, api, build, synth
+
     build.build()
     w = synth.make(args.config) if args.particles is None else synth.make(args.config, n=args.particles)
-    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    hp = HotPath(w, dev)
     n, m, K = w.n, w.m, w.n_ctrl
-    x0 = np.ascontiguousarray(w.pos[:, :3].astype(np.float64).T)
-    G0 = np.ascontiguousarray(w.strength[:, :3].astype(np.float64).T)
-    vol = T(w.pos[:, 3].copy())
-    sa, sb = T(w.seg_a), T(w.seg_b)
-    rings, colloc, normal, vrel = T(w.rings), T(w.colloc), T(w.normal), T(w.v_rel)
-    nrm = normal[:, :3].t().contiguous()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def make_state():
-        return T(x0), T(G0)
-
-    def hot_path_step(state, prm, wsb):
-        x, G = state
-        pos, strn = api.pack_state(x, G, vol, wsb["pos"], wsb["str"])
-        u_c = api.induce(pos, strn, colloc, w.sigma, compensated=prm.compensated, grad=False, ws=wsb["ws"])
-        A, b = api.aic_build(rings, colloc, normal, w.seg_core, 2, v_rel=vrel, w_ind=u_c)
-        gam, it, be = api.aic_solve(A, b, tol=1e-12, max_iter=30, ws=wsb["ws"])
-        api.step(x, G, vol, sa, sb, prm, w.dt, ws=wsb["ws"])
-        g = 2.0 * (u_c * nrm).sum(0, keepdim=True) * nrm  # d/du of sum_k (u_k . n_k)^2
-        dx, dG = api.induce_backward(pos, strn, colloc, w.sigma, g.contiguous(), compensated=prm.compensated,
-                                     ws=wsb["ws"])
-        return gam, dx, dG
-
-    def new_bufs():
-        return {"ws": api.Workspace(dev), "pos": torch.empty((n, 4), dtype=torch.float32, device=dev),
-                "str": torch.empty((n, 4), dtype=torch.float32, device=dev)}
-
-    def timed(prm, steps, warmup, trace=False):
-        state = make_state()
-        bufs = new_bufs()
-        for _ in range(warmup):
-            hot_path_step(state, prm, bufs)
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        if trace:
-            api.trace_enable(True)
-            api.trace_reset()
-        st = torch.cuda.current_stream()
-        total = 0.0
-        for _ in range(steps):
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            hot_path_step(state, prm, bufs)
-            e1.record(st)
-            e1.synchronize()
-            total += e0.elapsed_time(e1)
-        torch.cuda.synchronize()
-        tr = None
-        if trace:
-            tr = {k: api.trace_read(k) for k in (_lib.VPM_TRACE_ALL, _lib.VPM_TRACE_SWEEP, _lib.VPM_TRACE_ADJOINT,
-                                                 _lib.VPM_TRACE_PSE, _lib.VPM_TRACE_SWEEP_VEL)}
-            api.trace_enable(False)
-        return max_over_ranks(dist, total, dev), tr
-
-    prm_c = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=True)
-    prm_p = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=False)
-    pairs_step = 3 * n * (n - 1)
-    seg_pairs_step = 3 * n * m
+    pairs_step = n * (n - 1)
+    side = max(3, args.steps // 6)  # steps of the plain and end-to-end legs
 
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.start()
-    total_ms, tr = timed(prm_c, args.steps, args.warmup, trace=True)
+    total_ms, tr = timed_loop(hp, hp.params(True), args.steps, args.warmup, flush, dist, trace=True)
     clk = clocks.stop() if clocks else None
-    ms_step = total_ms / args.steps
+    total_ms = max_over_ranks(dist, total_ms, dev)
     value = whole_job_rate(ws_n, pairs_step, args.steps, total_ms)
 
     plain = None
     if not args.no_plain:
-        pm, _ = timed(prm_p, max(3, args.steps // 2), 1)
-        plain = {"value": whole_job_rate(ws_n, pairs_step, max(3, args.steps // 2), pm), "unit": UNIT,
-                 "ms_per_step": pm / max(3, args.steps // 2), "dtype": "f32 (plain accumulation)"}
+        pm, _ = timed_loop(hp, hp.params(False), side, 1, flush, dist)
+        pm = max_over_ranks(dist, pm, dev)
+        plain = {"value": whole_job_rate(ws_n, pairs_step, side, pm), "unit": UNIT, "steps": side,
+                 "ms_per_step": pm / side, "dtype": "f32 (plain accumulation)"}
 
-    # roofline of the dominant kernel: the particle + segment u + grad u sweep
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    sm_max = 2070.0
-    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x FFMA x max SM clock, TFLOP/s
-    nl, sms_ms = tr[_lib.VPM_TRACE_SWEEP]
-    avg_ms = sms_ms / max(nl, 1)
-    flops_launch = FLOPS_P2P * n * (n - 1) + FLOPS_SEG * n * m
-    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": sweep_traffic(n, m), "kernel": "sweep_kernel<grad, compensated>", "launches": nl,
-            "avg_launch_ms": avg_ms, "flops_per_launch": flops_launch,
-            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {sm_max:.0f} MHz (fallback-free derivation)"}
-    if clk and clk.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
-
-    # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        xh = torch.from_numpy(x0).pin_memory()
-        Gh = torch.from_numpy(G0).pin_memory()
-        xo = torch.empty_like(xh).pin_memory()
-        Go = torch.empty_like(Gh).pin_memory()
-        gho = torch.empty((K,), dtype=torch.float64).pin_memory()
-        dxo = torch.empty((3, n), dtype=torch.float32).pin_memory()
-        dGo = torch.empty((3, n), dtype=torch.float32).pin_memory()
-        volh = torch.from_numpy(w.pos[:, 3].copy()).pin_memory()
-        host_in = [torch.from_numpy(a).pin_memory() for a in (w.seg_a, w.seg_b, w.rings, w.colloc, w.normal,
-                                                              w.v_rel)]
-        bufs = new_bufs()
-        x_d, G_d = torch.empty_like(xh, device=dev), torch.empty_like(Gh, device=dev)
-        dev_in = [torch.empty_like(h, device=dev) for h in host_in]
-        vol_d = torch.empty_like(volh, device=dev)
+        em, h2d, d2h = e2e_loop(hp, hp.params(True), side, 1, flush, dist)
+        em = max_over_ranks(dist, em, dev)
+        e2e = {"value": whole_job_rate(ws_n, pairs_step, side, em), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": side, "ms_per_step": em / side,
+               "note": "per step: L2 flush outside the events; H2D of the inputs, the step, D2H of the results "
+                       "inside them (as the device-timed loop)"}
 
-        def e2e_step():
-            x_d.copy_(xh, non_blocking=True)
-            G_d.copy_(Gh, non_blocking=True)
-            vol_d.copy_(volh, non_blocking=True)
-            for d_, h_ in zip(dev_in, host_in):
-                d_.copy_(h_, non_blocking=True)
-            gam, dx, dG = hot_path_step((x_d, G_d), prm_c, bufs)
-            xo.copy_(x_d, non_blocking=True)
-            Go.copy_(G_d, non_blocking=True)
-            gho.copy_(gam, non_blocking=True)
-            dxo.copy_(dx, non_blocking=True)
-            dGo.copy_(dG, non_blocking=True)
+    props = torch.cuda.get_device_properties(dev)
+    roof = roofline(tr, n, m, props.multi_processor_count, clk)
 
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
-        torch.cuda.synchronize()
-        st = torch.cuda.current_stream()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        ksteps = max(2, args.steps // 2)
-        e0.record(st)
-        for _ in range(ksteps):
-            e2e_step()
-        e1.record(st)
-        e1.synchronize()
-        e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
-        h2d = (xh.numel() + Gh.numel()) * 8 + volh.numel() * 4 + sum(h.numel() * 4 for h in host_in)
-        d2h = (xo.numel() + Go.numel() + gho.numel()) * 8 + (dxo.numel() + dGo.numel()) * 4
-        e2e = {"value": whole_job_rate(ws_n, pairs_step, ksteps, e2e_ms), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": e2e_ms / ksteps}
-
-    # error at the stated tolerance, on a sample (outside every timed region): the GPU
-    # side here, the FP64 reference values in the cpu_baseline leg below
-    err_gpu = None
-    err_idx = synth.sample_targets(11, n, 96)
-    if rank == 0:
-        try:
-            pos, strn = api.pack_state(*make_state(), vol)
-            u, gr = api.induce(pos, strn, pos, w.sigma, compensated=True)
-            up, gp = api.induce(pos, strn, pos, w.sigma, compensated=False)
-            U = lambda t: t[:, err_idx].double().cpu().numpy().T
-            Jm = lambda t: t[:, err_idx].double().cpu().numpy().T.reshape(-1, 3, 3)
-            err_gpu = (U(u), Jm(gr), U(up), Jm(gp))
-        except Exception as ex:  # the error report is informative, never fatal
-            err_gpu = str(ex)[:200]
-
-    # the wake panel -> particle conversion (Eq. 6-8), outside the timed step: the edges of
-    # 2,000 wake panel rows of the 4-blade hover rotor, n_tip = 4 (informative)
-    wake = None
-    if rank == 0:
-        try:
-            ea, eb, eg, egn, ehn, etr, ds_tip = synth.rotor_wake_edges(5, 2000)
-            Td = lambda a_, dt_: torch.from_numpy(np.ascontiguousarray(a_)).to(dt_).to(dev)
-            wa, wb, wg, wgn = (Td(q, torch.float64) for q in (ea, eb, eg, egn))
-            whn, wtr = Td(ehn, torch.int32), Td(etr, torch.int32)
-            wws = api.Workspace(dev)
-            xw, Gw = api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, ws=wws)
-            npart = int(xw.shape[1])
-            reps = 5
-            torch.cuda.synchronize()
-            st = torch.cuda.current_stream()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for _ in range(reps):
-                api.wake_convert(wa, wb, wg, wtr, ds_tip, 4, 1, gamma_nb=wgn, has_nb=whn, capacity=npart, ws=wws)
-            e1.record(st)
-            e1.synchronize()
-            wms = e0.elapsed_time(e1) / reps
-            m_e = len(ea)
-            algo = 72 * m_e + 16 * m_e + 48 * npart  # edges in, counts/offsets out, particles out
-            wake = {"edges": m_e, "particles": npart, "ms": wms, "particles_per_s": npart / (wms * 1e-3),
-                    "algorithmic_bytes": algo, "achieved_gbs": algo / (wms * 1e-3) / 1e9,
-                    "note": "device time of one vpm_wake_convert call incl. its one host sync"}
-        except Exception as ex:  # informative, never fatal
-            wake = {"unavailable": str(ex)[:200]}
-
-    # the particle-particle and the segment-particle parts of the right-hand side sweep,
-    # each alone (compensated, with the gradient), so that the two pair rates are reported
-    # apart (informative, outside the timed step)
-    parts = None
-    if rank == 0:
-        try:
-            pos, strn = api.pack_state(*make_state(), vol)
-            pws = api.Workspace(dev)
-            st = torch.cuda.current_stream()
-
-            def sweep_ms(fn, reps=3):
-                fn()
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                for _ in range(reps):
-                    fn()
-                e1.record(st)
-                e1.synchronize()
-                return e0.elapsed_time(e1) / reps
-
-            p_ms = sweep_ms(lambda: api.induce(pos, strn, pos, w.sigma, compensated=True, ws=pws))
-            s_ms = sweep_ms(lambda: api.segments_induce(sa, sb, pos, w.seg_core, 2, compensated=True, ws=pws))
-            pp, sp_ = n * (n - 1), n * m
-            parts = {
-                "p2p": {"pairs": pp, "ms": p_ms, "pairs_per_s": pp / (p_ms * 1e-3),
-                        "tflops": pp * FLOPS_P2P / (p_ms * 1e-3) / 1e12},
-                "segments": {"pairs": sp_, "ms": s_ms, "pairs_per_s": sp_ / (s_ms * 1e-3),
-                             "tflops": sp_ * FLOPS_SEG / (s_ms * 1e-3) / 1e12},
-                "note": "vpm_induce (particles onto themselves) and vpm_segments_induce (segments onto the "
-                        "particles) alone, compensated, u + grad u; includes each call's packing and epilogue",
-            }
-        except Exception as ex:  # informative, never fatal
-            parts = {"unavailable": str(ex)[:200]}
-
-    # the treecode (the O(n log n) variant, outside the timed step) on the 1,000,000-particle
-    # BVI wake against the direct plain sum of the same wake (informative)
-    tree = None
-    wt = tree_idx = tree_gpu = None
-    if rank == 0 and not args.no_tree:
-        try:
-            wt = synth.make(3)
-            Pt = torch.from_numpy(wt.pos).to(dev)
-            St = torch.from_numpy(wt.strength).to(dev)
-            tws = api.Workspace(dev)
-            st = torch.cuda.current_stream()
-
-            def timed(fn, reps):
-                fn()
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                for _ in range(reps):
-                    fn()
-                e1.record(st)
-                e1.synchronize()
-                return e0.elapsed_time(e1) / reps
-
-            out = {}
-            tms = timed(lambda: out.__setitem__("t", api.tree_induce(Pt, St, wt.sigma, theta=0.5, order=4, ws=tws)), 3)
-            dms = timed(lambda: api.induce(Pt, St, Pt, wt.sigma, compensated=False, ws=tws), 1)
-            # the whole right-hand side (segments, Vreman, stretching, PSE) with the treecode
-            # against the direct one
-            prm_t = api.Params(sigma=wt.sigma, nu=wt.nu, c_v=wt.c_v, seg_core=wt.seg_core, u_inf=wt.u_inf,
-                               compensated=False)
-            At = torch.from_numpy(wt.seg_a).to(dev)
-            Bt = torch.from_numpy(wt.seg_b).to(dev)
-            rms = timed(lambda: api.rhs_tree(Pt, St, At, Bt, prm_t, theta=0.5, order=4, ws=tws), 2)
-            rdms = timed(lambda: api.rhs(Pt, St, At, Bt, prm_t, ws=tws), 1)
-            ut, gt = out["t"]
-            tree_idx = synth.sample_targets(11, wt.n, 32)
-            tree_gpu = (ut.cpu().numpy().T[tree_idx].astype(np.float64),
-                        gt.cpu().numpy().T[tree_idx].reshape(-1, 3, 3).astype(np.float64))
-            tree = {"particles": wt.n, "theta": 0.5, "order": 4, "ms": tms, "direct_plain_ms": dms,
-                    "speedup": dms / tms, "rhs_ms": rms, "rhs_direct_plain_ms": rdms}
-            del Pt, St, At, Bt, tws, out, ut, gt
-        except Exception as ex:  # informative, never fatal
-            tree = {"unavailable": str(ex)[:200]}
-
-    # the cpu_baseline leg: the FP64 oracle on the host cores, timed, and the same oracle's
-    # values at the sampled targets of the error reports (the only place the main arm
-    # runs it)
-    cpu = None
     err = {"unavailable": "the FP64 reference values come from the cpu_baseline leg (skipped)"}
-    rel = lambda a_, b_: float(np.linalg.norm(a_ - b_) / np.linalg.norm(b_))
-    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
-        cores = host_cores()
-        rate, k, dt = oracle_rate(w, 12.0 if args.cpu_seconds is None else args.cpu_seconds, cores)
-        rate1, k1, dt1 = oracle_rate(w, 3.0, 1)
-        oracle_threads_default(cores)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{k} sampled targets x all {n:,} sources, P2P u + grad u in FP64 ({dt:.1f} s)",
-               "single_thread": {"value": rate1, "unit": UNIT,
-                                 "sample": f"{k1} sampled targets x all {n:,} sources ({dt1:.1f} s)"}}
+    cpu = None
+    ext = {}
+    if rank == 0:
+        idx_u, idx_r = error_samples(w, args.error_targets)
         try:
-            ru, rJ = oracle_values(w, err_idx)
-            if isinstance(err_gpu, tuple):
-                cu, cg, pu, pg = err_gpu
-                err = {"sample_targets": len(err_idx), "compensated": {"u": rel(cu, ru), "grad_u": rel(cg, rJ)},
-                       "plain": {"u": rel(pu, ru), "grad_u": rel(pg, rJ)},
-                       "tolerance": {"compensated": 2e-6, "plain": 1e-4}}
-            else:
-                err = {"unavailable": str(err_gpu)}
-            if tree_gpu is not None and "unavailable" not in tree:
-                tu, tJ = oracle_values(wt, tree_idx)
-                tree["error_vs_oracle"] = {"sample_targets": len(tree_idx), "u": rel(tree_gpu[0], tu),
-                                           "grad_u": rel(tree_gpu[1], tJ)}
-        except Exception as ex:  # informative, never fatal
-            err = {"unavailable": str(ex)[:200]}
+            gpu_vals = gpu_error_values(hp, idx_u, idx_r)
+        except Exception as ex:  # the error report is informative, never fatal
+            gpu_vals = str(ex)[:200]
+        if not args.no_extras:
+            ext = extras(hp, args, flush, rank)
+        if ws_n == 1 and not args.no_cpu_baseline:
+            try:
+                ref, cpu = oracle_reference(w, idx_u, idx_r, host_cores())
+                err = (error_report(gpu_vals, ref, idx_u, idx_r) if isinstance(gpu_vals, dict)
+                       else {"unavailable": gpu_vals})
+            except Exception as ex:
+                err = {"unavailable": str(ex)[:200]}
 
     if dist is not None:
         dist.barrier()
@@ -640,18 +753,21 @@ def run_ours(args):
         launches_total = tr[_lib.VPM_TRACE_ALL][0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(w), "particles": n, "segments": m, "control_points": K,
-                       "pairs_per_step": pairs_step, "segment_pairs_per_step": seg_pairs_step,
+                       "pairs_per_step": pairs_step, "segment_pairs_per_step": n * m,
+                       "step": "one RK3 stage of the particles with the AIC solve, control-point velocity and "
+                               "adjoint (stages cycle 0, 1, 2)",
                        "precision": "compensated FP32 pair sums, FP64 state/refinement",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                        "parallelism": "replicas" if ws_n > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_total),
-            "clocks": clk, "plain": plain, "error": err, "wake_convert": wake, "sweep_parts": parts, "treecode": tree,
-            "kernel_ms": {"sweep_grad": [nl, sms_ms], "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
+            "clocks": clk, "plain": plain, "error": err,
+            "kernel_ms": {"sweep_grad": list(tr[_lib.VPM_TRACE_SWEEP]), "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
                           "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL])},
         }
+        line.update(ext)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

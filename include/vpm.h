@@ -33,6 +33,9 @@
  *    non-finite output when VPM_CHECK_FINITE is set) are latched in a device
  *    word read by vpm_device_error().
  *  - Calls on different streams must not share a workspace.
+ *  - Per-device set-up done once (the treecode's interpolation table) does not
+ *    survive cudaDeviceReset: after resetting a device, reload the library before
+ *    using it on that device again.
  */
 #ifndef VPM_H
 #define VPM_H
@@ -73,6 +76,7 @@ typedef enum vpm_status {
 #define VPM_OP_TREE 10
 #define VPM_OP_RHS_TREE 11
 #define VPM_OP_STEP_TREE 12
+#define VPM_OP_STAGE 13
 
 /* Largest particle / target / segment count accepted (int32 indexing). */
 #define VPM_MAX_ITEMS (1 << 30)
@@ -111,6 +115,7 @@ vpm_status vpm_device_error(int* code);
  *   VPM_OP_LOADS:     m_seg bound segments, n_tgt panels
  *   VPM_OP_TREE:      n_src particles (vpm_tree_induce)
  *   VPM_OP_RHS_TREE, VPM_OP_STEP_TREE: n_src particles, m_seg segments
+ *   VPM_OP_STAGE:     n_src particles, m_seg segments (vpm_rk3_stage)
  * `flags` as passed to the operation.  Host-only; does not launch. */
 vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_seg, int flags, size_t* bytes);
 
@@ -211,6 +216,20 @@ vpm_status vpm_pack_state(const double* x_d, const double* G_d, const float* vol
 vpm_status vpm_step(double* x_d, double* G_d, const float* vol_d, int64_t n, const float* seg_a_d,
                     const float* seg_b_d, int64_t m, const vpm_params* prm, double dt, void* ws_d, size_t ws_bytes,
                     void* stream);
+
+/* One stage k in {0, 1, 2} of vpm_step's low-storage RK3, with the register q kept
+ * by the caller between stages:
+ *   q <- A_k q + dt f(y);  y <- y + B_k q      (A_0 = 0: stage 0 does not read q),
+ * f evaluated by vpm_rhs on the state rounded to FP32.  Calls with k = 0, 1, 2 in turn
+ * on the same q run the kernels of one vpm_step in the same order and give its
+ * result bit for bit; a caller can put other work between the stages (the blade
+ * circulation solve of Sec. II.A, for instance).
+ *   x_d, G_d [3][n] double, updated in place; q_d [6][n] double (rows 0-2 for x,
+ *   3-5 for Gamma), read for k > 0 and written; vol_d [n] float; segments as
+ *   vpm_rhs.  Workspace: VPM_OP_STAGE (n_src = n, m_seg = m). */
+vpm_status vpm_rk3_stage(int k, double* x_d, double* G_d, double* q_d, const float* vol_d, int64_t n,
+                         const float* seg_a_d, const float* seg_b_d, int64_t m, const vpm_params* prm, double dt,
+                         void* ws_d, size_t ws_bytes, void* stream);
 
 /* ---- Sec. II.A: blade influence-coefficient system -------------------------
  * A[k][l] = u(ring l, unit circulation)(y_k) . n_k with ring l the four segments
@@ -348,11 +367,16 @@ vpm_status vpm_wake_convert_row(const double* U_d, const double* D_d, const doub
  * that must not allocate.  Arguments and results are those of vpm_induce; the
  * scratch is a fixed VPM_NOALLOC_SCRATCH_BYTES array in the library's own device
  * memory, held by every GPU that loads the library until the process exits.
- *  - The first call on a device (with that device current) looks the array's
- *    device address up; make that first call before any stream capture.
+ *  - Every call looks the array's device address up on the current device; the
+ *    first call on a device also loads the library's device code there, so make
+ *    that first call before any stream capture.
  *  - Problems whose scratch would exceed the array return VPM_ERR_LIMIT (message
- *    in vpm_last_error) without launching anything; about 100,000 particles onto
- *    themselves with the gradient fit on a 152-SM GB300.
+ *    in vpm_last_error) without launching anything.  The scratch of n_src sources
+ *    onto n_tgt targets is about 80 bytes per source plus 112 KiB per target tile
+ *    of 1,024 and per resident sweep block (one block per SM) with the gradient in
+ *    compensated mode (56 KiB plain; 24 and 12 KiB velocity only): on a 152-SM
+ *    GB300 up to about 250,000 particles onto themselves with the gradient
+ *    (compensated) fit.
  *  - Every call uses the same array and nothing in it needs to start at zero;
  *    calls whose GPU work overlaps (other streams, other host threads) race on it
  *    and must be ordered by the caller.

@@ -36,6 +36,7 @@ VPM_OP_LOADS = 9
 VPM_OP_TREE = 10
 VPM_OP_RHS_TREE = 11
 VPM_OP_STEP_TREE = 12
+VPM_OP_STAGE = 13
 
 VPM_TRACE_ALL = 0
 VPM_TRACE_SWEEP = 1
@@ -89,6 +90,8 @@ SIGNATURES = {
     "vpm_rhs": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _P, _P, _P, _P, _SZ, _P]),
     "vpm_pack_state": (_INT, [_P, _P, _P, _I64, _P, _P, _P]),
     "vpm_step": (_INT, [_P, _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _D, _P, _SZ, _P]),
+    "vpm_rk3_stage": (_INT, [_INT, _P, _P, _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _D, _P, _SZ,
+                              _P]),
     "vpm_rhs_tree": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _F, _INT, _P, _P, _P, _P, _SZ,
                             _P]),
     "vpm_step_tree": (_INT, [_P, _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(VpmParams), _F, _INT, _D, _P, _SZ, _P]),

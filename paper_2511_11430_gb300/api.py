@@ -233,6 +233,26 @@ def step(x, G, vol, seg_a, seg_b, params: Params, dt: float, ws=None):
     return x, G
 
 
+def rk3_stage(k: int, x, G, q, vol, seg_a, seg_b, params: Params, dt: float, ws=None):
+    """Stage k (0, 1, 2) of the low-storage RK3 step, in place on x, G [3, n] and the
+    register q [6, n] (float64, kept by the caller between stages)."""
+    _need(x, "x", torch.float64)
+    _need(G, "G", torch.float64)
+    _need(q, "q", torch.float64)
+    _need(vol, "vol", torch.float32)
+    if x.dim() != 2 or x.shape[0] != 3 or G.shape != x.shape or vol.shape != (x.shape[1],):
+        raise ValueError("x and G must be [3, n] and vol [n]")
+    if tuple(q.shape) != (6, x.shape[1]):
+        raise ValueError("q must be [6, n]")
+    sa, sb, m = _segs(seg_a, seg_b)
+    n = x.shape[1]
+    cp = params.to_c()
+    w = _ws(ws, workspace_size(_lib.VPM_OP_STAGE, n, 0, m, cp.flags), x.device)
+    check(_lib.load().vpm_rk3_stage(int(k), _void(x), _void(G), _void(q), _void(vol), n, _void(sa), _void(sb), m,
+                                    ctypes.byref(cp), float(dt), _void(w), w.numel(), _stream()))
+    return x, G
+
+
 def step_tree(x, G, vol, seg_a, seg_b, params: Params, dt: float, theta: float = 0.5, order: int = 4, ws=None):
     """As step, with the treecode right-hand side (vpm_step_tree)."""
     _need(x, "x", torch.float64)
@@ -266,6 +286,20 @@ def aic_build(rings, colloc, normal, core: float, vatistas_n: int = 2, v_rel=Non
     check(_lib.load().aic_build(_void(rings), _void(colloc), _void(normal), n, float(core), int(vatistas_n),
                                 _void(v_rel), _void(w_ind), _void(A), _void(b), _stream()))
     return A, b
+
+
+def ring_segments(rings, gamma, seg_a=None, seg_b=None):
+    """The 4 n segments c0->c1->c2->c3->c0 of n blade rings [n, 4, 4] carrying the
+    circulations gamma [n] (float64): seg_a, seg_b [4 n, 4] (float32, a.w = circulation)."""
+    _need(rings, "rings", torch.float32, (4, 4))
+    _need(gamma, "gamma", torch.float64)
+    n = rings.shape[0]
+    if seg_a is None:
+        seg_a = torch.empty((4 * n, 4), dtype=torch.float32, device=rings.device)
+    if seg_b is None:
+        seg_b = torch.empty((4 * n, 4), dtype=torch.float32, device=rings.device)
+    check(_lib.load().vpm_ring_segments(_void(rings), _void(gamma), n, _void(seg_a), _void(seg_b), _stream()))
+    return seg_a, seg_b
 
 
 def aic_solve(A, b, tol: float = 1e-12, max_iter: int = 30, ws=None, raise_on_fail: bool = True):

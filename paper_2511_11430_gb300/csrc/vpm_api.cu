@@ -77,6 +77,27 @@ StepWs step_layout(int64_t n, int64_t m, bool comp, bool classic)
     return s;
 }
 
+// Scratch of one vpm_rk3_stage call: the sweep, nu_t, the packed state and the
+// right-hand side (the RK register q belongs to the caller).
+struct StageWs {
+    SweepPlan p;
+    size_t nut, pos, str, dxdt, dGdt, bytes;
+};
+
+StageWs stage_layout(int64_t n, int64_t m, bool comp, bool classic)
+{
+    StageWs s;
+    Carve cv;
+    s.p = plan_sweep(n, n, m, true, comp, cv, !classic);
+    s.nut = cv.take((size_t)n * sizeof(float));
+    s.pos = cv.take((size_t)n * 16);
+    s.str = cv.take((size_t)n * 16);
+    s.dxdt = cv.take((size_t)n * 3 * sizeof(float));
+    s.dGdt = cv.take((size_t)n * 3 * sizeof(float));
+    s.bytes = cv.off;
+    return s;
+}
+
 // The buffers vpm_step_tree adds after the treecode right-hand side's workspace.
 size_t tree_step_extra(int64_t n)
 {
@@ -163,6 +184,9 @@ vpm_status vpm_workspace_size(int op, int64_t n_src, int64_t n_tgt, int64_t m_se
         break;
     case VPM_OP_STEP:
         *bytes = step_layout(n_src, m_seg, comp, flags & VPM_STRETCH_CLASSIC).bytes;
+        break;
+    case VPM_OP_STAGE:
+        *bytes = stage_layout(n_src, m_seg, comp, flags & VPM_STRETCH_CLASSIC).bytes;
         break;
     case VPM_OP_AIC_SOLVE:
         REQUIRE(n_tgt <= VPM_MAX_AIC, "AIC order %lld above %d", (long long)n_tgt, VPM_MAX_AIC);
@@ -397,6 +421,42 @@ vpm_status vpm_step(double* x_d, double* G_d, const float* vol_d, int64_t n, con
         if (e != cudaSuccess) return cuda_fail(e, "vpm_step");
     }
     return ok();
+}
+
+vpm_status vpm_rk3_stage(int k, double* x_d, double* G_d, double* q_d, const float* vol_d, int64_t n,
+                         const float* seg_a_d, const float* seg_b_d, int64_t m, const vpm_params* prm, double dt,
+                         void* ws_d, size_t ws_bytes, void* stream)
+{
+    vpm_status s;
+    if ((s = check_params(prm)) != VPM_OK) return s;
+    if ((s = check_count(n, "n")) != VPM_OK) return s;
+    if ((s = check_count(m, "m")) != VPM_OK) return s;
+    REQUIRE(k >= 0 && k <= 2, "stage k must be 0, 1 or 2 (got %d)", k);
+    REQUIRE(isfinite(dt), "dt must be finite");
+    if (n == 0) return ok();
+    REQUIRE(x_d && G_d && q_d && vol_d && aligned8(x_d) && aligned8(G_d) && aligned8(q_d) && aligned4(vol_d),
+            "x/G/q/vol must be aligned device pointers");
+    REQUIRE(m == 0 || (seg_a_d && seg_b_d && aligned16(seg_a_d) && aligned16(seg_b_d)),
+            "seg_a/seg_b must be 16-byte aligned device pointers when m > 0");
+    const bool comp = prm->flags & VPM_COMPENSATED;
+    const StageWs L = stage_layout(n, m, comp, prm->flags & VPM_STRETCH_CLASSIC);
+    if (!overflow_guard(L.p)) return fail(VPM_ERR_LIMIT, "problem too large for the stream-K split");
+    if (!ws_d || ws_bytes < L.bytes || !aligned16(ws_d))
+        return fail(VPM_ERR_WORKSPACE, "workspace needs %zu bytes (16-byte aligned), got %zu", L.bytes, ws_bytes);
+    if (!dev_err_ptr()) return fail(VPM_ERR_CUDA, "no CUDA device");
+    char* ws = static_cast<char*>(ws_d);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* nut = reinterpret_cast<float*>(ws + L.nut);
+    float* pos = reinterpret_cast<float*>(ws + L.pos);
+    float* str = reinterpret_cast<float*>(ws + L.str);
+    float* dxdt = reinterpret_cast<float*>(ws + L.dxdt);
+    float* dGdt = reinterpret_cast<float*>(ws + L.dGdt);
+    cudaError_t e = run_cast_state(x_d, G_d, vol_d, (int)n, pos, str, st);
+    if (e != cudaSuccess) return cuda_fail(e, "vpm_rk3_stage");
+    s = rhs_into(L.p, ws, pos, str, n, seg_a_d, seg_b_d, prm, dxdt, dGdt, nut, st);
+    if (s != VPM_OK) return s;
+    e = run_rk3_stage(k, dt, x_d, G_d, q_d, q_d + 3 * (size_t)n, dxdt, dGdt, vol_d, (int)n, nullptr, nullptr, st);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "vpm_rk3_stage");
 }
 
 vpm_status vpm_rhs_tree(const float* pos_d, const float* str_d, int64_t n, const float* seg_a_d, const float* seg_b_d,
@@ -694,7 +754,8 @@ vpm_status vpm_selftest_wait(double limit_ms, int* completed, void* stream)
 // manager, or a time-critical loop that is not allowed to allocate.  The scratch
 // is a fixed array in the library's own device memory, reserved on every GPU that
 // loads the library and kept until the process exits.  Its device address is
-// looked up once per device, on the first call made with that device current.
+// looked up on every call, with the caller's device current; the first lookup on a
+// device loads the library's module there.
 // Nothing in it has to start at zero: each call writes every byte it later
 // reads.  All calls share the one array, so calls whose GPU work overlaps race
 // on it.
@@ -703,23 +764,14 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[VPM_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_na_mu;
-void* g_na_ptr[64];
-
+// The array's device address on the current device, looked up on every call (a
+// cheap query once the module is loaded), so that it is never stale.
 cudaError_t noalloc_scratch_address(void** out)
 {
-    int d = 0;
-    cudaError_t e = cudaGetDevice(&d);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[d]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_ptr[d] = p;
-    }
-    *out = g_na_ptr[d];
+    *out = p;
     return cudaSuccess;
 }
 

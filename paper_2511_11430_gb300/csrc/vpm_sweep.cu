@@ -624,7 +624,6 @@ __device__ int g_dev_err;  // device error word (one instance per device)
 namespace {
 std::mutex g_mu;
 int g_sm[64];
-int* g_err[64];
 int g_blocks[64][8];
 bool g_attr[64][8];
 }  // namespace
@@ -649,17 +648,13 @@ int sm_count()
     return g_sm[d];
 }
 
+// The device error word of the current device, looked up on every call (a cheap
+// query once the module is loaded) so that the address is never stale.
 int* dev_err_ptr()
 {
-    const int d = cur_dev();
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (d < 0 || d >= 64) return nullptr;
-    if (!g_err[d]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_dev_err) != cudaSuccess) return nullptr;
-        g_err[d] = static_cast<int*>(p);
-    }
-    return g_err[d];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_dev_err) != cudaSuccess) return nullptr;
+    return static_cast<int*>(p);
 }
 
 static int variant(bool G, bool C, bool S) { return (G ? 4 : 0) + (C ? 2 : 0) + (S ? 1 : 0); }

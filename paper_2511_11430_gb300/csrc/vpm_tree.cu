@@ -1410,7 +1410,7 @@ __global__ void __launch_bounds__(TREE_WARPS * 32) tree_pse_kernel(PseArgs A)
                     const float rx = pi.x - pj.x, ry = pi.y - pj.y, rz = pi.z - pj.z;
                     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                     if (r2 < A.cut2) {
-                        const float w = fmaf(0.5f, ntj, h ? base1 : base0) * __expf(-r2 * A.inv2s2);
+                        const float w = fmaf(0.5f, ntj, h ? base1 : base0) * expf(-r2 * A.inv2s2);
                         const float vi = pi.w, vj = pj.w;
                         const float tx = __fsub_rn(__fmul_rn(vi, gj.x), __fmul_rn(vj, gi.x));
                         const float ty = __fsub_rn(__fmul_rn(vi, gj.y), __fmul_rn(vj, gi.y));

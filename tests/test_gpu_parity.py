@@ -160,6 +160,40 @@ def test_step_config1(api):
     assert rel_l2(gG - G0, rG - G0) <= 1e-5
 
 
+def test_rk3_stages_equal_one_step(api):
+    """Three vpm_rk3_stage calls (k = 0, 1, 2, the register kept by the caller) give
+    vpm_step's state bit for bit, and the staged step matches the oracle's step."""
+    w = synth.make(1)
+    x0 = np.ascontiguousarray(w.pos[:, :3].astype(np.float64).T)
+    G0 = np.ascontiguousarray(w.strength[:, :3].astype(np.float64).T)
+    vol, sa, sb = to_dev(w.pos[:, 3].copy()), to_dev(w.seg_a), to_dev(w.seg_b)
+    dt = w.dt * 20
+    prm = api.Params(sigma=w.sigma, nu=w.nu, c_v=w.c_v, seg_core=w.seg_core, u_inf=w.u_inf, compensated=True)
+    X1, G1 = to_dev(x0), to_dev(G0)
+    api.step(X1, G1, vol, sa, sb, prm, dt)
+    X2, G2 = to_dev(x0), to_dev(G0)
+    q = torch.full((6, w.n), float("nan"), dtype=torch.float64, device="cuda")
+    for k in range(3):
+        api.rk3_stage(k, X2, G2, q, vol, sa, sb, prm, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(X1, X2) and torch.equal(G1, G2)
+    rx, rG = oracle.step(x0.T, G0.T, w.pos[:, 3].copy(), w.seg_a, w.seg_b, w.sigma, dt, nu=w.nu, c_v=w.c_v,
+                         seg_core=w.seg_core, u_inf=w.u_inf, cast_f32=True)
+    assert rel_l2(X2.cpu().numpy().T - x0.T, rx - x0.T) <= 1e-5
+    assert rel_l2(G2.cpu().numpy().T - G0.T, rG - G0.T) <= 1e-5
+
+
+def test_rk3_stage_rejects_bad_stage(api):
+    from paper_2511_11430_gb300 import _lib
+
+    x = torch.zeros((3, 4), dtype=torch.float64, device="cuda")
+    q = torch.zeros((6, 4), dtype=torch.float64, device="cuda")
+    vol = torch.ones(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(_lib.VpmError) as ei:
+        api.rk3_stage(3, x, x.clone(), q, vol, None, None, api.Params(sigma=0.1), 1e-3)
+    assert ei.value.status == _lib.VPM_ERR_INVALID_ARG
+
+
 def test_aic_build_and_solve(api):
     w = synth.make(1)
     A_ref = oracle.aic_build(w.rings, w.colloc, w.normal, w.seg_core)
