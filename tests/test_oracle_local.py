@@ -131,3 +131,65 @@ def test_rhs_is_assembled_from_its_parts():
     s = oracle.stretch(Jt, strn)
     p = oracle.pse(pos, strn, nu_ref, 0.04, 1e-3)
     np.testing.assert_allclose(dG, s + p, rtol=1e-13, atol=1e-16)
+
+
+def _rings(n, sigma):
+    """Two vortex rings of blobs (radii 1 and 0.8, axes tilted against each other), n
+    equally spaced particles each with strength tangent to the ring: a closed,
+    well-overlapped blob set (sigma / h = sigma n / (2 pi R))."""
+    pos, strn = [], []
+    for R, c, ax in ((1.0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0)), (0.8, (0.3, 0.1, 0.6), (0.3, 0.2, 1.0))):
+        ax = np.asarray(ax) / np.linalg.norm(ax)
+        e1 = np.cross(ax, [0.3, 0.5, 0.8])
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(ax, e1)
+        th = (np.arange(n) + 0.5) * 2.0 * np.pi / n
+        x = np.asarray(c) + R * (np.cos(th)[:, None] * e1 + np.sin(th)[:, None] * e2)
+        t = -np.sin(th)[:, None] * e1 + np.cos(th)[:, None] * e2
+        pos.append(np.c_[x, np.full(n, sigma ** 3)])
+        strn.append(np.c_[t * 2.0 * np.pi * R / n, np.zeros(n)])
+    return np.concatenate(pos), np.concatenate(strn)
+
+
+def _impulse(x, G):
+    """Linear impulse I = (1/2) sum_i x_i x Gamma_i."""
+    return 0.5 * np.cross(x[:, :3], G[:, :3]).sum(axis=0)
+
+
+def test_impulse_rate_identity_of_the_transposed_scheme():
+    """With the transposed stretching s_i = J_i^T Gamma_i (inviscid), pairing the terms
+    (i, j) and (j, i) gives sum_i x_i x s_i = sum_{i<j} K(r) r x (Gamma_i x Gamma_j) =
+    sum_i u_i x Gamma_i for any blob set (the H terms of s are parallel to r and cancel
+    in the pair), so dI/dt = (1/2) sum (u x Gamma + x x s) = sum_i u_i x Gamma_i: the
+    discrete form of dI/dt = integral of u x omega.  The classic form J Gamma does not
+    satisfy it."""
+    rng = np.random.default_rng(7)
+    n = 300
+    pos = np.c_[rng.uniform(-1, 1, (n, 3)), np.full(n, 1e-3)]
+    strn = np.c_[rng.normal(size=(n, 3)), np.zeros(n)]
+    u, s, _ = oracle.rhs(pos, strn, None, None, 0.1, nu=0.0, c_v=0.0)
+    lhs = np.cross(pos[:, :3], s).sum(axis=0)
+    rhs = np.cross(u, strn[:, :3]).sum(axis=0)
+    assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(rhs)
+    _, s_c, _ = oracle.rhs(pos, strn, None, None, 0.1, nu=0.0, c_v=0.0, classic=True)
+    assert np.linalg.norm(np.cross(pos[:, :3], s_c).sum(axis=0) - rhs) > 1e-3 * np.linalg.norm(rhs)
+
+
+def test_linear_impulse_conserved_by_closed_rings():
+    """For blobs on closed circles sum_i u_i x Gamma_i vanishes, so the rate of the
+    linear impulse is zero to round-off; over one RK3 step (inviscid, the fastest
+    particle moving sigma/4) the rings deform and I drifts only at second order in dt
+    (measured 5e-7 of |I| for sigma/h = 3.2)."""
+    sigma = 0.1
+    pos, strn = _rings(200, sigma)
+    I0 = _impulse(pos, strn)
+    u, s, _ = oracle.rhs(pos, strn, None, None, sigma, nu=0.0, c_v=0.0)
+    dI = 0.5 * (np.cross(u, strn[:, :3]).sum(axis=0) + np.cross(pos[:, :3], s).sum(axis=0))
+    U = np.abs(u).max()
+    assert np.linalg.norm(dI) <= 1e-12 * np.linalg.norm(I0) * U
+    dt = 0.25 * sigma / U
+    x1, G1 = oracle.step(pos[:, :3], strn[:, :3], pos[:, 3].copy(), None, None, sigma, dt, nu=0.0, c_v=0.0)
+    drift = np.linalg.norm(_impulse(x1, G1) - I0) / np.linalg.norm(I0)
+    assert drift <= 5e-6
+    # the step did move and stretch the rings (the bound is not met by standing still)
+    assert np.linalg.norm(G1 - strn[:, :3]) > 1e-3 * np.linalg.norm(strn[:, :3])

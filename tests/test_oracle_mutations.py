@@ -28,6 +28,7 @@ MUTATIONS = {
     "stretch_not_transposed": ("t += classic ? Jp[3 * a + b] * G[b] : Jp[3 * b + a] * G[b];",
                                "t += classic ? Jp[3 * a + b] * G[b] : Jp[3 * a + b] * G[b];"),
     "pse_factor": ("p[a] = 2.0 / (sigma * sigma) * acc[a];", "p[a] = 1.0 / (sigma * sigma) * acc[a];"),
+    "stretch_dropped": ("            s[3 * p + a] = t;", "            s[3 * p + a] = 0.0 * t;"),
     "rk3_coefficient": ("-153.0 / 128.0", "-153.0 / 126.0"),
     "lu_no_pivoting": ("if (fabs(A[n * i + k]) > fabs(A[n * piv + k])) piv = i;", "if (0) piv = i;"),
     "adjoint_sign": ("ax[b] -= t;", "ax[b] += t;"),
