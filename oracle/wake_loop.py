@@ -12,13 +12,17 @@ circulation (Kutta), and the oldest row beyond max_rows converted by Eq. 6-8.  T
 blade geometry and motion are the same synthetic input (rounded to FP32, as the
 library gets it): hover, or forward flight with the pitch and flapping schedules of
 Eq. 12 form and a free stream, which convects the node lines and the particles and
-enters the loads with each blade's own angular velocity.
+enters the loads with each blade's own angular velocity.  The blade placement, its
+angular velocity and the lattice come from oracle/kinematics.py, written apart from
+the product's generator; only the rotor's static description (synth.Kinematics:
+radius, chord, schedule coefficients) and the air constants are shared.
 """
 from __future__ import annotations
 
 import numpy as np
 
 import oracle
+from oracle import kinematics
 from paper_2511_11430_gb300 import synth
 
 
@@ -50,7 +54,7 @@ class OracleRotorWake:
         self.history = []
 
     def _geometry(self, t):
-        L = synth.rotor_lattice(self.kin, t, self.nb, self.S, self.nc)
+        L = kinematics.lattice(self.kin, t, self.nb, self.S, self.nc)
         return _f32(L.rings), _f32(L.colloc), _f32(L.normal), _f32(L.v_rel), L.te, L.te_idx, L.omega_b
 
     @property
@@ -85,7 +89,7 @@ class OracleRotorWake:
         A = oracle.aic_build(rings, colloc, normal, self.core)
         b = oracle.aic_rhs(vrel, _f32(u_c), normal)
         gam = oracle.lu_solve(_f32(A), b)
-        bsa, bsb = synth.ring_segments(rings, _f32(gam))
+        bsa, bsb = kinematics.ring_segments(rings, _f32(gam))
         sa = np.concatenate([bsa, wsa]) if len(wsa) else bsa
         sb = np.concatenate([bsb, wsb]) if len(wsb) else bsb
         self._loads(rings, normal, gam, te_idx, omega_b, bsa, bsb, sa, sb)

@@ -69,33 +69,46 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     assert res.returncode != 0, f"no pin caught mutation {name}:\n{res.stdout[-2000:]}"
 
 
-# Mistakes planted in the oracle's near-wake time loop (oracle/wake_loop.py): the copy of
-# the oracle package with the mutated loop is put first on the import path of a
-# subprocess that runs the loop's pins (the C routines are the unmutated library).
-LOOP_SRC = os.path.join(ROOT, "oracle", "wake_loop.py")
+# Mistakes planted in the oracle's near-wake time loop (oracle/wake_loop.py) and in its
+# blade kinematics (oracle/kinematics.py): a copy of the oracle package with the mutated
+# file is put first on the import path of a subprocess that runs the pins (the C
+# routines are the unmutated library).  The kinematics mutants run against the
+# kinematics pins without the comparison with the product's generator, so that the
+# oracle's own pins (schedules read back, central differences, hover) must catch them.
 LOOP_PINS = ["tests/test_oracle_wake_loop.py"]
+KIN_PINS = ["tests/test_oracle_kinematics.py", "-k", "not agrees"]
 LOOP_MUTATIONS = {
-    "nodes_drop_free_stream": ("self.nodes = (pts + self.dt * (_f32(u_n) + self.u_inf)).reshape(self.nodes.shape)",
+    "nodes_drop_free_stream": ("wake_loop.py", LOOP_PINS,
+                               "self.nodes = (pts + self.dt * (_f32(u_n) + self.u_inf)).reshape(self.nodes.shape)",
                                "self.nodes = (pts + self.dt * _f32(u_n)).reshape(self.nodes.shape)"),
-    "particles_drop_free_stream": ("seg_core=self.core, u_inf=self.u_inf, cast_f32=True)",
+    "particles_drop_free_stream": ("wake_loop.py", LOOP_PINS, "seg_core=self.core, u_inf=self.u_inf, cast_f32=True)",
                                    "seg_core=self.core, cast_f32=True)"),
-    "kutta_sign": ("shed = -gam[te_idx.ravel()].reshape(1, self.nb, self.S)",
+    "kutta_sign": ("wake_loop.py", LOOP_PINS, "shed = -gam[te_idx.ravel()].reshape(1, self.nb, self.S)",
                    "shed = gam[te_idx.ravel()].reshape(1, self.nb, self.S)"),
+    "flap_rate_sign": ("kinematics.py", KIN_PINS, "- dbe * (Z @ _dry(-be) @ X)", "+ dbe * (Z @ _dry(-be) @ X)"),
+    "flap_about_wrong_axis": ("kinematics.py", KIN_PINS, "Z, Y, X = _rz(psi), _ry(-be), _rx(th)",
+                              "Z, Y, X = _rz(psi), _ry(be), _rx(th)"),
+    "pitch_schedule_sine_sign": ("kinematics.py", KIN_PINS, "a = c0 + c1c * np.cos(psi) + c1s * np.sin(psi)",
+                                 "a = c0 + c1c * np.cos(psi) - c1s * np.sin(psi)"),
+    "v_rel_sign": ("kinematics.py", KIN_PINS, "v_rel.append(u_inf - np.cross(w, y - hub))",
+                   "v_rel.append(u_inf + np.cross(w, y - hub))"),
 }
 
 
-def _run_loop_pins(loop_text, tmp_path):
+def _run_loop_pins(fname, text, pins, tmp_path):
+    import glob
     import shutil
 
     pkg = tmp_path / "oracle"
     pkg.mkdir()
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), pkg / "__init__.py")
-    (pkg / "wake_loop.py").write_text(loop_text)
+    for f in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        shutil.copy(f, pkg / os.path.basename(f))
+    (pkg / fname).write_text(text)
     os.symlink(os.path.join(ROOT, "paper_2511_11430_gb300"), tmp_path / "paper_2511_11430_gb300")
     os.symlink(os.path.join(ROOT, "tests"), tmp_path / "tests")
     lib = os.path.join(ROOT, "oracle", "liboracle.so")
     env = dict(os.environ, VPM_ORACLE_LIB=lib, OMP_NUM_THREADS="4")
-    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *LOOP_PINS],
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins],
                           cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=900)
 
 
@@ -104,7 +117,8 @@ def test_unmutated_loop_passes_its_pins(tmp_path):
     import oracle
 
     oracle.build()
-    res = _run_loop_pins(open(LOOP_SRC).read(), tmp_path)
+    src = open(os.path.join(ROOT, "oracle", "wake_loop.py")).read()
+    res = _run_loop_pins("wake_loop.py", src, LOOP_PINS + ["tests/test_oracle_kinematics.py"], tmp_path)
     assert res.returncode == 0, res.stdout[-2000:]
 
 
@@ -114,8 +128,8 @@ def test_loop_pins_catch_planted_mistake(name, tmp_path):
     import oracle
 
     oracle.build()
-    old, new = LOOP_MUTATIONS[name]
-    src = open(LOOP_SRC).read()
+    fname, pins, old, new = LOOP_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
-    res = _run_loop_pins(src.replace(old, new), tmp_path)
+    res = _run_loop_pins(fname, src.replace(old, new), pins, tmp_path)
     assert res.returncode != 0, f"no pin caught mutation {name}:\n{res.stdout[-2000:]}"

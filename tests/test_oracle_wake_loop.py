@@ -5,6 +5,7 @@ closed rings' zero net circulation, and Eq. 8 needs fewer particles than the uni
 count with the same tip resolution."""
 import numpy as np
 
+from oracle import kinematics
 from oracle.wake_loop import OracleRotorWake
 from paper_2511_11430_gb300 import synth
 
@@ -43,7 +44,7 @@ def test_kutta_joukowski_pins():
     import oracle
 
     ring = np.array([[[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0]]], float)
-    a, b = synth.ring_segments(ring, np.array([2.0]))
+    a, b = kinematics.ring_segments(ring, np.array([2.0]))
     nrm = np.array([[0.0, 0.0, 1.0, 0.0]])
     F, _ = oracle.blade_loads(a, b, np.zeros((4, 3)), [0, 0, 0], [0, 0, 0], [3.0, 1.0, 0.5], ring, nrm, [2.0], None,
                               1e-3, rho=1.2)
@@ -89,7 +90,7 @@ def test_zero_lift_forward_flight_convects_with_the_free_stream():
         gam = o.step()
         assert np.all(gam == 0.0) and o.history[-1][1] == 0.0 and o.history[-1][2] == 0.0
         for r in range(o.rows + 1):  # line r was shed at time t - r dt (t after the step)
-            te = synth.rotor_lattice(kin, o.t - r * o.dt, 2, 6, 2).te
+            te = kinematics.lattice(kin, o.t - r * o.dt, 2, 6, 2).te
             np.testing.assert_allclose(o.nodes[r], te + r * o.dt * u, rtol=0, atol=1e-12)
         if x_prev is not None and len(x_prev):
             np.testing.assert_allclose(o.x[:len(x_prev)], x_prev + o.dt * u, rtol=0, atol=1e-12)
