@@ -136,11 +136,11 @@ def test_bvi_1m_rhs_sampled():
     idx = np.sort(np.concatenate([synth.sample_runs(3, n_hel, 4, 16), *[np.arange(s, s + 16) for s in fil]]))
     rdx, rdG, rnut = sampled.rhs_at(w, idx)
     res = _rhs_both_forms(api, w)
-    for comp, tol in ((True, TOL_COMP), (False, TOL_PLAIN)):
+    for comp, tol, tol_nu in ((True, TOL_COMP, 1e-5), (False, TOL_PLAIN, 1e-3)):
         dx, dG, nut = res[comp]
         assert rel_l2(_rows(dx, idx, 3), rdx) <= tol
         assert rel_l2(_rows(dG, idx, 3), rdG) <= tol
-        assert rel_l2(nut[idx].double().cpu().numpy(), rnut) <= 1e-5
+        assert rel_l2(nut[idx].double().cpu().numpy(), rnut) <= tol_nu
 
 
 def test_multirotor_2m_rhs_sampled():
@@ -162,10 +162,10 @@ def test_multirotor_2m_rhs_sampled():
     _, rdG, _ = sampled.rhs_at(w, idx_r)
     full = _rhs_both_forms(api, w)
     cv0 = _rhs_both_forms(api, w, c_v=0.0)
-    for comp, tol in ((True, TOL_COMP), (False, TOL_PLAIN)):
+    for comp, tol, tol_nu in ((True, TOL_COMP, 1e-5), (False, TOL_PLAIN, 1e-3)):
         dx, dG, nut = full[comp]
         assert rel_l2(_rows(dx, idx, 3), rdx) <= tol
-        assert rel_l2(nut[idx].double().cpu().numpy(), rnut) <= 1e-5
+        assert rel_l2(nut[idx].double().cpu().numpy(), rnut) <= tol_nu
         assert rel_l2(_rows(dG, idx_r, 3), rdG) <= tol
         assert rel_l2(_rows(cv0[comp][1], idx, 3), rdG0) <= tol
 
