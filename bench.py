@@ -42,8 +42,8 @@ TOL = {"compensated": 2e-6, "plain": 1e-4, "nu_t": {"compensated": 1e-5, "plain"
 # one ncu capture of that launch per workload (profiles/sweep_kernel_*.md), keyed by
 # (particles, segments); valid only while the kernel's sources hash to SWEEP_SRC_SHA256,
 # else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = {}
-SWEEP_SRC_SHA256 = ""
+SWEEP_TRAFFIC_BYTES = {(2_000_000, 7_680): 156_304_597_000 + 354_574_336}
+SWEEP_SRC_SHA256 = "62f6d7358d3cbd4cd8ffa46bcebdc3f6295c49c5cfde357ba15f135e6d13bf8c"
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 
@@ -743,14 +743,17 @@ def run_ours(args):
     cpu = None
     ext = {}
     if rank == 0:
+        with_ref = ws_n == 1 and not args.no_cpu_baseline
         idx_u, idx_r = error_samples(w, args.error_targets)
-        try:
-            gpu_vals = gpu_error_values(hp, idx_u, idx_r)
-        except Exception as ex:  # the error report is informative, never fatal
-            gpu_vals = str(ex)[:200]
+        gpu_vals = None
+        if with_ref:  # the GPU side of the error report (its reference comes from the oracle leg)
+            try:
+                gpu_vals = gpu_error_values(hp, idx_u, idx_r)
+            except Exception as ex:  # the error report is informative, never fatal
+                gpu_vals = str(ex)[:200]
         if not args.no_extras:
             ext = extras(hp, args, flush, rank)
-        if ws_n == 1 and not args.no_cpu_baseline:
+        if with_ref:
             try:
                 ref, cpu = oracle_reference(w, idx_u, idx_r, host_cores())
                 err = (error_report(gpu_vals, ref, idx_u, idx_r) if isinstance(gpu_vals, dict)
