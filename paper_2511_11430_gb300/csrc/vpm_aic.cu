@@ -14,6 +14,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "vpm_internal.h"
 
 namespace vpm {
@@ -102,7 +104,6 @@ cudaError_t run_aic_build(const float* rings, const float* colloc, const float* 
 // result is LAPACK's: P A = L U with the row exchanges applied to whole rows.
 // ---------------------------------------------------------------------------
 constexpr int NB = 32;
-constexpr int LU_THREADS = 1024;  // the triangular solves
 
 // The end of a panel, after a barrier that made the final position map `pos2phys`
 // visible (and with *nmov zeroed before it): lists the changed positions as (source,
@@ -472,12 +473,28 @@ __global__ void __launch_bounds__(ROWS_THREADS, 4) lu_rows_kernel(float* __restr
 
 // A22 -= L21 U12 over rows [k0+nb, n) and columns [cb, ce): 64x64 output tile per
 // block, 4x4 per thread.
-__global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, int n, int k0, int nb, int cb, int ce)
+__global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, int n, int k0, int nb, int cb, int ce,
+                                                        const float* __restrict__ dsrc)
 {
     __shared__ float Ls[64][NB + 1];
     __shared__ float Us[NB][64 + 1];
+    if (dsrc && blockIdx.x == 0 && blockIdx.y == 0)  // the panel's factored diagonal block, into place
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            const int i = e / nb, c = e - i * nb;
+            A[(size_t)(k0 + i) * n + k0 + c] = dsrc[e];
+        }
     const int s0 = k0 + nb;
     const int r0 = s0 + blockIdx.y * 64, c0 = cb + blockIdx.x * 64;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    // this thread's 4 x 4 outputs are read first, so that they arrive with the tiles
+    float out[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int r = r0 + ty * 4 + q, c = c0 + tx * 4 + w;
+            out[q][w] = (r < n && c < ce) ? A[(size_t)r * n + c] : 0.f;
+        }
     for (int e = threadIdx.x; e < 64 * NB; e += blockDim.x) {
         const int i = e / NB, p = e % NB;
         const int r = r0 + i;
@@ -487,7 +504,6 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
         Us[pp][cc] = (c < ce && pp < nb) ? A[(size_t)(k0 + pp) * n + c] : 0.f;
     }
     __syncthreads();
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float acc[4][4] = {};
 #pragma unroll 8
     for (int p = 0; p < NB; ++p) {
@@ -506,8 +522,148 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int c = c0 + tx * 4 + w;
-            if (c < ce) A[(size_t)r * n + c] -= acc[q][w];
+            if (c < ce) A[(size_t)r * n + c] = out[q][w] - acc[q][w];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LU without row exchanges, for matrices that are strictly diagonally dominant by
+// rows (|a_ii| > sum_{j != i} |a_ij| for every i).  Gaussian elimination keeps that
+// property in every Schur complement, so no pivot is ever zero and the elements grow
+// by at most a factor two: it is stable without pivoting (Wilkinson).  The blade AIC
+// systems are of this kind (the self-influence of a ring at its own collocation point
+// dominates its row).  Without the pivot search a panel needs no block-wide
+// reduction per column: lu_np_panel_kernel factors the 32 x 32 diagonal block in one
+// warp and then forms L21 = A21 U11^-1 (one thread per row) and U12 = L11^-1 A12 (one
+// thread per column) in parallel over the whole panel; lu_update_kernel follows.
+// ---------------------------------------------------------------------------
+
+// flag |= 1 when some row is not strictly diagonally dominant (one warp per row, FP64 sums).
+__global__ void __launch_bounds__(256) lu_dominance_kernel(const float* __restrict__ A, int n, int* __restrict__ flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += fabs((double)A[(size_t)i * n + c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const double d = fabs((double)A[(size_t)i * n + i]);
+        if (!(2.0 * d > s)) atomicOr(flag, 1);
+    }
+}
+
+constexpr int NP_THREADS = 256;
+
+// Panel [k0, k0 + nb) of the row-dominant LU: grid (chunks, 2); blockIdx.y 0 forms the
+// rows of L21 (NP_THREADS rows per block), 1 the columns of U12.  Every block factors
+// the diagonal block in shared memory (one warp, no exchanges); block (0, 0) writes it
+// to dout (lu_update_kernel copies it into place) or, for the last panel, launched as
+// that one block with dout NULL, into A; it also records the first zero or non-finite
+// pivot in *info (1-based column) and, for the first panel, sets the permutation to
+// the identity and clears *info.
+__global__ void __launch_bounds__(NP_THREADS) lu_np_panel_kernel(float* __restrict__ A, int n, int k0, int nb,
+                                                                 int* __restrict__ info, int* __restrict__ perm,
+                                                                 float* __restrict__ dout)
+{
+    __shared__ float D[NB][NB + 1];
+    __shared__ float Rinv[NB];
+    __shared__ float W[NP_THREADS][NB + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool head = blockIdx.x == 0 && blockIdx.y == 0;
+    if (head && k0 == 0) {
+        for (int i = tid; i < n; i += NP_THREADS) perm[i] = i;
+        if (tid == 0) *info = 0;
+    }
+    const int rest = n - k0 - nb;
+    const int base = blockIdx.x * NP_THREADS;
+    const int rows = blockIdx.y == 0 ? max(0, min(NP_THREADS, rest - base)) : 0;
+    const int col = k0 + nb + base + tid;
+    const bool col_ok = blockIdx.y == 1 && base + tid < rest;
+    // This block's own part of the panel is requested first, so that it arrives while
+    // the diagonal block is factored: the rows of A21 into W (asynchronous copies), the
+    // column of A12 into registers.
+    for (int e = tid; e < rows * NB; e += NP_THREADS) {
+        const int r = e / NB, c = e - r * NB;
+        if (c < nb)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(&W[r][c])),
+                         "l"(A + (size_t)(k0 + nb + base + r) * n + k0 + c)
+                         : "memory");
+        else
+            W[r][c] = 0.f;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    float y[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) y[i] = (col_ok && i < nb) ? A[(size_t)(k0 + i) * n + col] : 0.f;
+    for (int e = tid; e < NB * NB; e += NP_THREADS) {
+        const int i = e / NB, c = e - i * NB;
+        D[i][c] = (i < nb && c < nb) ? A[(size_t)(k0 + i) * n + k0 + c] : (i == c ? 1.f : 0.f);
+    }
+    __syncthreads();
+    if (warp == 0) {  // D = L11 U11 (unit lower L below the diagonal): lane i holds row i in registers
+        float v[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) v[c] = D[lane][c];
+#pragma unroll
+        for (int j = 0; j < NB - 1; ++j) {
+            const float l = v[j] / __shfl_sync(0xffffffffu, v[j], j);
+#pragma unroll
+            for (int c = j + 1; c < NB; ++c) {
+                const float u = __shfl_sync(0xffffffffu, v[c], j);  // the pivot row's entry
+                if (lane > j) v[c] = fmaf(-l, u, v[c]);
+            }
+            if (lane > j) v[j] = l;
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c) D[lane][c] = v[c];
+        Rinv[lane] = 1.0f / D[lane][lane];  // this lane's own diagonal entry
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (head) {
+        // the factored diagonal block goes to dout (the other blocks of this launch are
+        // still reading the original from A), or to A itself when it is the only block
+        for (int e = tid; e < nb * nb; e += NP_THREADS) {
+            const int i = e / nb, c = e - i * nb;
+            if (dout)
+                dout[e] = D[i][c];
+            else
+                A[(size_t)(k0 + i) * n + k0 + c] = D[i][c];
+        }
+        if (tid < nb) {
+            const float d = D[tid][tid];
+            if (!(fabsf(d) > 0.f) || !isfinite(d)) atomicCAS(info, 0, k0 + tid + 1);
+        }
+    }
+    if (blockIdx.y == 0) {  // rows of L21: x = a U11^-1 on the rows staged in W
+        if (rows <= 0) return;
+        if (tid < rows) {
+            float x[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                float v = W[tid][j];
+#pragma unroll
+                for (int p = 0; p < j; ++p) v = fmaf(-x[p], D[p][j], v);
+                x[j] = v * Rinv[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NB; ++j) W[tid][j] = x[j];
+        }
+        __syncthreads();
+        for (int e = tid; e < rows * NB; e += NP_THREADS) {
+            const int r = e / NB, c = e - r * NB;
+            if (c < nb) A[(size_t)(k0 + nb + base + r) * n + k0 + c] = W[r][c];
+        }
+    } else if (col_ok) {  // columns of U12: y = L11^-1 a (unit lower), coalesced across the threads
+#pragma unroll
+        for (int i = 1; i < NB; ++i)
+#pragma unroll
+            for (int p = 0; p < i; ++p) y[i] = fmaf(-D[i][p], y[p], y[i]);
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+            if (i < nb) A[(size_t)(k0 + i) * n + col] = y[i];
     }
 }
 
@@ -529,176 +685,248 @@ __global__ void __launch_bounds__(256) lu_transpose_kernel(const float* __restri
     }
 }
 
-// Solves (LU) z = P r in FP32 for a FP64 right-hand side (one block, the vector in
-// shared memory) and writes z, or adds it to `out` when `accumulate` is set; both in
-// FP64.  T = LU^T, so column p of the factors is the contiguous row p of T.  The
-// substitution runs over 32-row diagonal blocks: warp 0 solves the block (lane = row,
-// a shuffle per column), then every thread updates one remaining row with a 32-long
-// dot product.  Nothing the loads of a step fetch depends on the solution, so each
-// thread issues its first row's 32 factor entries (coalesced across the warp) and one
-// entry of the next diagonal block before the block is solved; the diagonal blocks
-// are staged in shared memory one step ahead.
-__device__ __forceinline__ float solve_dot(const float* col, int n, const float* yb, int bn)
-{
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int p = 0;
-    for (; p + 4 <= bn; p += 4) {
-        s0 = fmaf(col[(size_t)p * n], yb[p], s0);
-        s1 = fmaf(col[(size_t)(p + 1) * n], yb[p + 1], s1);
-        s2 = fmaf(col[(size_t)(p + 2) * n], yb[p + 2], s2);
-        s3 = fmaf(col[(size_t)(p + 3) * n], yb[p + 3], s3);
-    }
-    for (; p < bn; ++p) s0 = fmaf(col[(size_t)p * n], yb[p], s0);
-    return (s0 + s1) + (s2 + s3);
-}
+// ---------------------------------------------------------------------------
+// Triangular solves on a cluster of SOLVE_CL blocks.  The substitution runs over the
+// SB-row diagonal blocks of the factors; the inverse of every diagonal block is formed
+// once (lu_diag_inv_kernel), so solving a block is an SB x SB matrix-vector product
+// rather than SB dependent steps.  The rows are split into SOLVE_CL contiguous ranges
+// of whole SB-row blocks, one per block of the cluster, each of which keeps a full copy
+// of the vector in shared memory.  Per diagonal block k: its owner solves it (warps 0
+// and 1, one row of the block per thread) and writes the SB values into every block's
+// copy (distributed shared memory), one cluster barrier makes them visible, and every
+// block subtracts their contribution from its own rows, with the SB factor entries per
+// row loaded one step ahead (T = LU^T, so column p of the factors is the contiguous
+// row p of T).  One cluster barrier per SB rows bounds the solve's latency; SOLVE_CL
+// blocks read the factors from L2 SOLVE_CL times faster than one.
+// ---------------------------------------------------------------------------
+constexpr int SOLVE_CL = 8;
+constexpr int SOLVE_T = 256;
+constexpr int SB = 64;
 
-// sum_p t[p] yb[p] over a 32-entry block of the solution (16-byte aligned, read as float4).
-__device__ __forceinline__ float dot32(const float* t, const float* yb)
+// Inverses of the SB x SB diagonal blocks, transposed: Dinv[(w * nblk + k) * SB * SB + q * SB + i]
+// = inverse(block k)[i][q], w = 0 for the unit lower factor L, 1 for the upper U.  One block of
+// SB = 64 threads per diagonal block and factor.  Each warp inverts one 32 x 32 diagonal
+// sub-block (lane c forms column c by substitution); the off-diagonal sub-block of the
+// inverse follows from them by two 32 x 32 products: for L = [[A, 0], [C, B]] it is
+// -B^-1 C A^-1, for U = [[A, C], [0, B]] it is -A^-1 C B^-1.  A partial last block is padded
+// with the identity.
+__global__ void __launch_bounds__(SB) lu_diag_inv_kernel(const float* __restrict__ LU, int n,
+                                                         float* __restrict__ Dinv)
 {
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int p4 = 0; p4 < 8; ++p4) {
-        const float4 v = reinterpret_cast<const float4*>(yb)[p4];
-        s0 = fmaf(t[4 * p4], v.x, s0);
-        s1 = fmaf(t[4 * p4 + 1], v.y, s1);
-        s0 = fmaf(t[4 * p4 + 2], v.z, s0);
-        s1 = fmaf(t[4 * p4 + 3], v.w, s1);
-    }
-    return s0 + s1;
-}
-
-// Element (tid / 32, tid % 32) of the diagonal block starting at c0 (zero outside it).
-__device__ __forceinline__ float diag_entry(const float* __restrict__ T, int n, int c0)
-{
-    const int p = threadIdx.x >> 5, r = threadIdx.x & 31, cn = min(32, n - c0);
-    return (c0 >= 0 && c0 < n && p < cn && r < cn) ? T[(size_t)(c0 + p) * n + c0 + r] : 0.f;
-}
-
-__global__ void __launch_bounds__(LU_THREADS) lu_solve_kernel(const float* __restrict__ T,
-                                                              const int* __restrict__ perm, int n,
-                                                              const double* __restrict__ rhs,
-                                                              double* __restrict__ out, int accumulate)
-{
-    extern __shared__ __align__(16) float y[];  // n entries and 32 zeros: a partial block reads zeros past n
-    __shared__ float dblk[2][32][33];  // [slot][column p][row r] of a diagonal block
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nblk = (n + 31) / 32;
-    for (int i = tid; i < n + 32; i += LU_THREADS) y[i] = i < n ? (float)rhs[perm[i]] : 0.f;
-    dblk[0][tid >> 5][tid & 31] = diag_entry(T, n, 0);
+    static_assert(SB == 64, "two 32 x 32 sub-blocks per diagonal block");
+    __shared__ float M[SB][SB + 1];
+    __shared__ float Iv[2][32][33];  // inverses of the two diagonal sub-blocks
+    __shared__ float Tm[32][33];
+    const int k = blockIdx.x, w = blockIdx.y, tid = threadIdx.x, nblk = gridDim.x;
+    const int lane = tid & 31, h = tid >> 5;
+    const int b0 = SB * k, nb = min(SB, n - b0);
+    for (int i = 0; i < SB; ++i)
+        M[i][tid] = (i < nb && tid < nb) ? LU[(size_t)(b0 + i) * n + b0 + tid] : (i == tid ? 1.f : 0.f);
     __syncthreads();
-    // forward: L (unit lower), blocks in increasing order
-    for (int k = 0; k < nblk; ++k) {
-        const int b0 = 32 * k, bn = min(32, n - b0), i0 = b0 + bn + tid;
-        float t0[32];
+    {
+        const int o = 32 * h;
+        float x[32];
+        if (w == 0) {  // L x = e_c, L unit lower: x_i = -sum_{c <= p < i} L[i][p] x_p
 #pragma unroll
-        for (int p = 0; p < 32; ++p) t0[p] = (i0 < n && p < bn) ? T[(size_t)(b0 + p) * n + i0] : 0.f;
-        const float dn = diag_entry(T, n, k + 1 < nblk ? b0 + 32 : -1);
-        if (warp == 0) {
-            const float(*D)[33] = dblk[k & 1];
-            float v = lane < bn ? y[b0 + lane] : 0.f;
+            for (int i = 0; i < 32; ++i) {
+                float v = i == lane ? 1.f : 0.f;
 #pragma unroll
-            for (int p = 0; p < 32; ++p) {
-                const float yp = __shfl_sync(0xffffffffu, v, p);
-                if (lane > p) v = fmaf(-D[p][lane], yp, v);
+                for (int p = 0; p < i; ++p) v = fmaf(-M[o + i][o + p], x[p], v);
+                x[i] = i < lane ? 0.f : v;
             }
-            if (lane < bn) y[b0 + lane] = v;
+        } else {  // U x = e_c: x_i = (delta_ic - sum_{i < p <= c} U[i][p] x_p) / U[i][i]
+#pragma unroll
+            for (int i = 31; i >= 0; --i) {
+                float v = i == lane ? 1.f : 0.f;
+#pragma unroll
+                for (int p = i + 1; p < 32; ++p) v = fmaf(-M[o + i][o + p], x[p], v);
+                x[i] = i > lane ? 0.f : v / M[o + i][o + i];
+            }
         }
-        dblk[(k + 1) & 1][tid >> 5][tid & 31] = dn;
-        __syncthreads();
-        if (i0 < n) y[i0] -= dot32(t0, y + b0);
-        for (int i = i0 + LU_THREADS; i < n; i += LU_THREADS) y[i] -= solve_dot(T + (size_t)b0 * n + i, n, y + b0, bn);
-        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Iv[h][i][lane] = x[i];
     }
-    // backward: U, blocks in decreasing order
-    dblk[0][tid >> 5][tid & 31] = diag_entry(T, n, 32 * (nblk - 1));
     __syncthreads();
-    for (int k = nblk - 1, s = 0; k >= 0; --k, ++s) {
-        const int b0 = 32 * k, bn = min(32, n - b0), i0 = tid;
-        float t0[32];
+    // Tm = C A^-1 (L) or C B^-1 (U); thread (h, lane) forms rows 16 h .. 16 h + 15 of column lane
+    const int j = lane, ib = 16 * h;
+    float s[16];
 #pragma unroll
-        for (int p = 0; p < 32; ++p) t0[p] = (i0 < b0 && p < bn) ? T[(size_t)(b0 + p) * n + i0] : 0.f;
-        const float dn = diag_entry(T, n, k > 0 ? b0 - 32 : -1);
-        if (warp == 0) {
-            const float(*D)[33] = dblk[s & 1];
-            float v = lane < bn ? y[b0 + lane] : 0.f;
-            const float rd = lane < bn ? 1.0f / D[lane][lane] : 0.f;
+    for (int q = 0; q < 16; ++q) s[q] = 0.f;
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) {
+        const float ivp = Iv[w][p][j];
 #pragma unroll
-            for (int p = 31; p >= 0; --p) {
-                if (p < bn) {
-                    if (lane == p) v *= rd;
-                    const float yp = __shfl_sync(0xffffffffu, v, p);
-                    if (lane < p) v = fmaf(-D[p][lane], yp, v);
+        for (int q = 0; q < 16; ++q)
+            s[q] = fmaf(w == 0 ? M[32 + ib + q][p] : M[ib + q][32 + p], ivp, s[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) Tm[ib + q][j] = s[q];
+    __syncthreads();
+    // off-diagonal sub-block: -B^-1 Tm (L) or -A^-1 Tm (U)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s[q] = 0.f;
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) {
+        const float tp = Tm[p][j];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s[q] = fmaf(-Iv[1 - w][ib + q][p], tp, s[q]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) Tm[ib + q][j] = s[q];
+    __syncthreads();
+    float* out = Dinv + ((size_t)w * nblk + k) * SB * SB;
+    for (int e = tid; e < SB * SB; e += SB) {  // out[q SB + i] = inverse[i][q]
+        const int q = e / SB, i = e % SB;
+        float v;
+        if ((i < 32) == (q < 32))
+            v = Iv[i >= 32][i & 31][q & 31];
+        else if (w == 0)
+            v = i >= 32 ? Tm[i - 32][q] : 0.f;
+        else
+            v = i < 32 ? Tm[i][q - 32] : 0.f;
+        out[e] = v;
+    }
+}
+
+// (LU) z = P r in FP32 for a FP64 right-hand side; writes z, or adds it to `out` when
+// `accumulate` is set (both FP64).  Launched as one cluster of SOLVE_CL blocks of
+// SOLVE_T threads with (n + SB) floats of dynamic shared memory.
+__global__ void __cluster_dims__(SOLVE_CL, 1, 1) __launch_bounds__(SOLVE_T)
+    lu_solve_cluster_kernel(const float* __restrict__ T, const float* __restrict__ Dinv,
+                            const int* __restrict__ perm, int n, const double* __restrict__ rhs,
+                            double* __restrict__ out, int accumulate)
+{
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) float y[];  // n entries and SB zeros
+    cg::cluster_group cl = cg::this_cluster();
+    const int cr = (int)cl.block_rank(), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nblk = (n + SB - 1) / SB;
+    const int per = SB * ((nblk + SOLVE_CL - 1) / SOLVE_CL);  // rows per block of the cluster
+    const int r0 = min(n, cr * per), r1 = min(n, r0 + per);
+    for (int i = tid; i < n + SB; i += SOLVE_T) y[i] = i < n ? (float)rhs[perm[i]] : 0.f;
+    cl.sync();
+    const int i0 = r0 + tid;  // this thread's first row (later rows, n > SOLVE_CL SOLVE_T, unprefetched)
+    // one direction of the substitution: forward (L, blocks ascending, rows below) or
+    // backward (U, blocks descending, rows above)
+    auto sweep = [&](bool fwd) {
+        const float* Dw = Dinv + (size_t)(fwd ? 0 : nblk) * SB * SB;
+        float t[SB];
+        auto fetch = [&](int k) {  // row i0's entries of block column k
+#pragma unroll
+            for (int p = 0; p < SB; ++p) {
+                const int c = SB * k + p;
+                t[p] = (i0 < r1 && k >= 0 && k < nblk && c < n) ? T[(size_t)c * n + i0] : 0.f;
+            }
+        };
+        float d[SB];  // warps 0 and 1: row 32 warp + lane of the inverse of block k, a step ahead
+        auto fetch_d = [&](int k) {
+            if (warp < 2 && k >= 0 && k < nblk) {
+                const float* Dk = Dw + (size_t)k * SB * SB + 32 * warp + lane;
+#pragma unroll
+                for (int q = 0; q < SB; ++q) d[q] = Dk[q * SB];
+            }
+        };
+        int k = fwd ? 0 : nblk - 1;
+        fetch(k);
+        fetch_d(k);
+        for (int step = 0; step < nblk; ++step, k += fwd ? 1 : -1) {
+            const int b0 = SB * k;
+            if (warp < 2 && b0 >= r0 && b0 < r1) {  // this block owns diagonal block k: solve and send
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+#pragma unroll
+                for (int q = 0; q < SB; q += 4) {
+                    v0 = fmaf(d[q], y[b0 + q], v0);
+                    v1 = fmaf(d[q + 1], y[b0 + q + 1], v1);
+                    v2 = fmaf(d[q + 2], y[b0 + q + 2], v2);
+                    v3 = fmaf(d[q + 3], y[b0 + q + 3], v3);
                 }
+                const float v = (v0 + v1) + (v2 + v3);
+                // both warps have read the block before either overwrites it
+                asm volatile("bar.sync 1, 64;" ::: "memory");
+                const int row = b0 + 32 * warp + lane;
+                if (row < n)
+                    for (int r = 0; r < SOLVE_CL; ++r) *cl.map_shared_rank(&y[row], r) = v;
             }
-            if (lane < bn) y[b0 + lane] = v;
+            fetch_d(k + (fwd ? 1 : -1));
+            cl.sync();
+            // subtract block k's contribution from this block's rows beyond it
+            const float* yb = y + b0;
+            const bool mine = i0 < r1 && (fwd ? i0 >= b0 + SB : i0 < b0);
+            float a0 = 0.f, a1 = 0.f;
+            if (mine)
+#pragma unroll
+                for (int p = 0; p < SB; p += 2) {
+                    a0 = fmaf(t[p], yb[p], a0);
+                    a1 = fmaf(t[p + 1], yb[p + 1], a1);
+                }
+            fetch(k + (fwd ? 1 : -1));
+            if (mine) y[i0] -= a0 + a1;
+            for (int i = i0 + SOLVE_T; i < r1; i += SOLVE_T)
+                if (fwd ? i >= b0 + SB : i < b0) {
+                    float a2 = 0.f;
+                    for (int p = 0; p < SB && b0 + p < n; ++p) a2 = fmaf(T[(size_t)(b0 + p) * n + i], yb[p], a2);
+                    y[i] -= a2;
+                }
+            __syncthreads();  // the owner of the next block reads these rows
         }
-        dblk[(s + 1) & 1][tid >> 5][tid & 31] = dn;
-        __syncthreads();
-        if (i0 < b0) y[i0] -= dot32(t0, y + b0);
-        for (int i = i0 + LU_THREADS; i < b0; i += LU_THREADS) y[i] -= solve_dot(T + (size_t)b0 * n + i, n, y + b0, bn);
-        __syncthreads();
-    }
-    for (int i = tid; i < n; i += LU_THREADS) out[i] = accumulate ? out[i] + (double)y[i] : (double)y[i];
+        cl.sync();
+    };
+    sweep(true);
+    sweep(false);
+    for (int i = r0 + tid; i < r1; i += SOLVE_T) out[i] = accumulate ? out[i] + (double)y[i] : (double)y[i];
 }
 
-// r = b - A x in FP64 (A's FP32 entries promoted exactly); also row |A| sums on the first pass.
+// r = b - A x in FP64 (A's FP32 entries promoted exactly), one warp per row, with the
+// row |A| sums stored on the first pass (`first`) and read back on later ones.  The
+// maxima of |r_i| (+inf where r_i or x_i is not finite), |x_i|, |b_i| and the row sums
+// are folded into out[0..3], zeroed before the launch, by atomic max on their bit
+// patterns (non-negative doubles order as their unsigned 64-bit patterns); out[4] and
+// out[5] receive the zero-pivot status and the dominance flag.
 __global__ void __launch_bounds__(256) residual_kernel(const float* __restrict__ A, const double* __restrict__ b,
                                                        const double* __restrict__ x, int n, double* __restrict__ r,
-                                                       double* __restrict__ rowabs)
+                                                       double* __restrict__ rowabs, int first,
+                                                       const int* __restrict__ info, double* __restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[4][8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
-    double s = 0.0, a = 0.0;
-    for (int c = lane; c < n; c += 32) {
-        const double v = (double)A[(size_t)i * n + c];
-        s = fma(v, x[c], s);
-        a += fabs(v);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-    }
-    if (lane == 0) {
-        r[i] = b[i] - s;
-        if (rowabs) rowabs[i] = a;
-    }
-}
-
-// out = (max|r|, max|x|, max|b|, max rowabs) ; one block.
-__global__ void __launch_bounds__(1024) norms_kernel(const double* __restrict__ r, const double* __restrict__ x,
-                                                     const double* __restrict__ b,
-                                                     const double* __restrict__ rowabs, int n,
-                                                     double* __restrict__ out)
-{
-    __shared__ double s[4][32];
-    double m[4] = {0, 0, 0, 0};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        m[0] = fmax(m[0], fabs(r[i]));
-        m[1] = fmax(m[1], fabs(x[i]));
-        m[2] = fmax(m[2], fabs(b[i]));
-        m[3] = fmax(m[3], rowabs[i]);
-        if (!isfinite(r[i]) || !isfinite(x[i])) m[0] = INFINITY;
-    }
-    for (int q = 0; q < 4; ++q)
-        for (int o = 16; o > 0; o >>= 1) m[q] = fmax(m[q], __shfl_xor_sync(0xffffffffu, m[q], o));
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-        for (int q = 0; q < 4; ++q) s[q][w] = m[q];
-    __syncthreads();
-    if (w == 0) {
-        for (int q = 0; q < 4; ++q) {
-            double v = lane < (int)(blockDim.x >> 5) ? s[q][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0) out[q] = v;
+    double m[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+        double s = 0.0, a = 0.0;
+        for (int c = lane; c < n; c += 32) {
+            const double v = (double)A[(size_t)i * n + c];
+            s = fma(v, x[c], s);
+            a += fabs(v);
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+        }
+        const double ri = b[i] - s, xi = x[i];
+        if (lane == 0) {
+            r[i] = ri;
+            if (first) rowabs[i] = a;
+        }
+        m[0] = isfinite(ri) && isfinite(xi) ? fabs(ri) : INFINITY;
+        m[1] = fabs(xi);
+        m[2] = fabs(b[i]);
+        m[3] = first ? a : rowabs[i];
     }
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[q][wib] = m[q];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v = fmax(v, red[threadIdx.x][w]);
+        atomicMax(reinterpret_cast<unsigned long long*>(out) + threadIdx.x, (unsigned long long)__double_as_longlong(v));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[4] = (double)info[0], out[5] = (double)info[1];
 }
-
 
 namespace {
 struct AicWs {
-    size_t lu, t, perm, moves, info, pscratch, r, xbest, rowabs, norms, bytes;
+    size_t lu, t, perm, moves, info, dblk, dinv, pscratch, r, xbest, rowabs, norms, bytes;
 };
 AicWs aic_layout(int n)
 {
@@ -708,12 +936,14 @@ AicWs aic_layout(int n)
     w.t = cv.take((size_t)n * n * sizeof(float));
     w.perm = cv.take((size_t)n * sizeof(int));
     w.moves = cv.take((1 + 4 * NB) * sizeof(int));
-    w.info = cv.take(sizeof(int));
+    w.info = cv.take(2 * sizeof(int));  // the factorisation's status, then the dominance test
+    w.dblk = cv.take((size_t)NB * NB * sizeof(float));
+    w.dinv = cv.take((size_t)2 * ((n + SB - 1) / SB) * SB * SB * sizeof(float));
     w.pscratch = cv.take((size_t)n * PLD * sizeof(float));
     w.r = cv.take((size_t)n * sizeof(double));
     w.xbest = cv.take((size_t)n * sizeof(double));
     w.rowabs = cv.take((size_t)n * sizeof(double));
-    w.norms = cv.take(4 * sizeof(double));
+    w.norms = cv.take(6 * sizeof(double));
     w.bytes = cv.off;
     return w;
 }
@@ -743,6 +973,8 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     int* perm = reinterpret_cast<int*>(ws + L.perm);
     int* moves = reinterpret_cast<int*>(ws + L.moves);
     int* info = reinterpret_cast<int*>(ws + L.info);
+    float* dblk = reinterpret_cast<float*>(ws + L.dblk);
+    float* dinv = reinterpret_cast<float*>(ws + L.dinv);
     float* pscratch = reinterpret_cast<float*>(ws + L.pscratch);
     double* r = reinterpret_cast<double*>(ws + L.r);
     double* xbest = reinterpret_cast<double*>(ws + L.xbest);
@@ -769,8 +1001,9 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         for (const void* f : reg_kernels)
             VPM_CU(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, reg_smem));
     }
-    const size_t solve_smem = (size_t)(n + 32) * sizeof(float);
-    VPM_CU(cudaFuncSetAttribute(lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem));
+    const size_t solve_smem = (size_t)(n + SB) * sizeof(float);
+    VPM_CU(cudaFuncSetAttribute(lu_solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)solve_smem));
     // Factor panel k0 on stream ps.
     auto launch_panel = [&](int k0, cudaStream_t ps) {
         const int nb = n - k0 < NB ? n - k0 : NB, rows = n - k0;
@@ -800,41 +1033,76 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
         else
             lu_panel_kernel<false><<<1, PANEL_THREADS, psmem, ps>>>(LU, n, k0, nb, info, perm, moves, pscratch, srows);
     };
-    for (int k0 = 0; k0 < n; k0 += NB) {
-        const int nb = n - k0 < NB ? n - k0 : NB;
-        launch_panel(k0, st);
-        if (n - nb > 0) {
+    // Strictly row-dominant matrices (the blade AIC systems) need no row exchanges
+    // (Gaussian elimination keeps them dominant, with growth at most 2), so the LU
+    // without them runs first and the dominance test is read with the first
+    // residual: any other matrix is then factored again with partial pivoting.  The
+    // zero-pivot status is read at the same synchronisation.
+    int* dflag = info + 1;
+    auto factor = [&](bool pivot) -> cudaError_t {
+        for (int k0 = 0; !pivot && k0 < n; k0 += NB) {
+            const int nb = n - k0 < NB ? n - k0 : NB;
+            const int rest = n - k0 - nb;
             trace_launch();
-            lu_rows_kernel<<<(n - nb + ROWS_THREADS - 1) / ROWS_THREADS, ROWS_THREADS, 0, st>>>(LU, n, k0, nb, moves);
+            if (rest > 0)
+                lu_np_panel_kernel<<<dim3((rest + NP_THREADS - 1) / NP_THREADS, 2), NP_THREADS, 0, st>>>(
+                    LU, n, k0, nb, info, perm, dblk);
+            else
+                lu_np_panel_kernel<<<dim3(1, 1), NP_THREADS, 0, st>>>(LU, n, k0, nb, info, perm, nullptr);
+            if (rest > 0) {
+                trace_launch();
+                lu_update_kernel<<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, 0, st>>>(LU, n, k0, nb, k0 + nb,
+                                                                                           n, dblk);
+            }
         }
-        const int rest = n - k0 - nb;
-        if (rest > 0) {
-            trace_launch();
-            lu_update_kernel<<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, 0, st>>>(LU, n, k0, nb, k0 + nb, n);
+        for (int k0 = 0; pivot && k0 < n; k0 += NB) {
+            const int nb = n - k0 < NB ? n - k0 : NB;
+            launch_panel(k0, st);
+            if (n - nb > 0) {
+                trace_launch();
+                lu_rows_kernel<<<(n - nb + ROWS_THREADS - 1) / ROWS_THREADS, ROWS_THREADS, 0, st>>>(LU, n, k0, nb,
+                                                                                                    moves);
+            }
+            const int rest = n - k0 - nb;
+            if (rest > 0) {
+                trace_launch();
+                lu_update_kernel<<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, 0, st>>>(LU, n, k0, nb, k0 + nb,
+                                                                                           n, nullptr);
+            }
         }
-    }
+        trace_launch();
+        lu_transpose_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(LU, T, n);
+        trace_launch();
+        lu_diag_inv_kernel<<<dim3((n + SB - 1) / SB, 2), SB, 0, st>>>(LU, n, dinv);
+        trace_launch();
+        lu_solve_cluster_kernel<<<SOLVE_CL, SOLVE_T, solve_smem, st>>>(T, dinv, perm, n, b, x, 0);
+        return cudaGetLastError();
+    };
+    VPM_CU(cudaMemsetAsync(dflag, 0, sizeof(int), st));
     trace_launch();
-    lu_transpose_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(LU, T, n);
-    VPM_CU(cudaGetLastError());
-    int hinfo = 0;
-    VPM_CU(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VPM_CU(cudaStreamSynchronize(st));
-    if (hinfo != 0) {
-        *msg = "aic_solve: matrix is singular in FP32 (zero pivot)";
-        return VPM_ERR_NOT_CONVERGED;
-    }
-    trace_launch();
-    lu_solve_kernel<<<1, LU_THREADS, solve_smem, st>>>(T, perm, n, b, x, 0);
-    double h[4];
+    lu_dominance_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, n, dflag);
+    VPM_CU(factor(false));
+    bool pivoted = false;
+    double h[6];
     double best = INFINITY;
     for (int it = 0;; ++it) {
+        VPM_CU(cudaMemsetAsync(norms, 0, 4 * sizeof(double), st));
         trace_launch();
-        residual_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, b, x, n, r, it == 0 ? rowabs : nullptr);
-        trace_launch();
-        norms_kernel<<<1, 1024, 0, st>>>(r, x, b, rowabs, n, norms);
+        residual_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, b, x, n, r, rowabs, it == 0, info, norms);
         VPM_CU(cudaGetLastError());
         VPM_CU(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, st));
         VPM_CU(cudaStreamSynchronize(st));
+        if (!pivoted && h[5] != 0.0) {  // not row-dominant: factor again with row exchanges
+            pivoted = true;
+            VPM_CU(cudaMemcpyAsync(LU, A, (size_t)n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            VPM_CU(factor(true));
+            it = -1;
+            continue;
+        }
+        if (h[4] != 0.0) {
+            *msg = "aic_solve: matrix is singular in FP32 (zero pivot)";
+            return VPM_ERR_NOT_CONVERGED;
+        }
         const double den = h[3] * h[1] + h[2];
         const double be = den > 0.0 ? h[0] / den : (h[0] > 0.0 ? INFINITY : 0.0);
         if (iters) *iters = it;
@@ -855,7 +1123,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
             return VPM_ERR_NOT_CONVERGED;
         }
         trace_launch();
-        lu_solve_kernel<<<1, LU_THREADS, solve_smem, st>>>(T, perm, n, r, x, 1);
+        lu_solve_cluster_kernel<<<SOLVE_CL, SOLVE_T, solve_smem, st>>>(T, dinv, perm, n, r, x, 1);
     }
 #undef VPM_CU
 }

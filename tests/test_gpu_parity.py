@@ -247,6 +247,25 @@ def test_aic_solve_needs_pivoting(api, n, kind):
     assert rel_l2(x.cpu().numpy(), xr) <= max(1e-10, 10 * cond * 1e-12)
 
 
+@pytest.mark.parametrize("n", [1, 31, 33, 100, 257, 1280])
+@pytest.mark.parametrize("dominant", [True, False])
+def test_aic_solve_row_dominant_and_not(api, n, dominant):
+    """A strictly row-dominant matrix is factored without row exchanges, any other with
+    partial pivoting; both are refined to the FP64 solution of the FP32 matrix.  The
+    non-dominant case is the dominant matrix with one row's diagonal made small."""
+    rng = np.random.default_rng(1000 + n)
+    A = rng.uniform(-1.0, 1.0, (n, n))
+    A[np.arange(n), np.arange(n)] = (np.abs(A).sum(axis=1) + 0.05) * np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+    if not dominant and n > 1:
+        A[n // 2, n // 2] = 0.25
+    A = A.astype(np.float32)
+    b = rng.normal(size=n)
+    x, it, be = api.aic_solve(to_dev(A), to_dev(b), tol=1e-12, max_iter=30)
+    assert be <= 1e-12
+    ref = oracle.lu_solve(A.astype(np.float64), b)
+    np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
 def test_aic_solve_not_converged_returns_best_iterate(api):
     """With an unreachable tolerance the solve stops after max_iter corrections and
     returns the iterate of smallest backward error, whose error it reports."""
