@@ -38,8 +38,8 @@ FLOPS_P2P = 54   # u + grad u, far-field operation tree, FFMA = 2 flops
 FLOPS_SEG = 120  # Vatistas segment u + grad u, same counting convention
 L2_FLUSH_BYTES = 256 << 20
 TOL = {"compensated": 2e-6, "plain": 1e-4, "nu_t": {"compensated": 1e-5, "plain": 1e-3}}
-# DRAM bytes (read + write) of one sweep_kernel<grad, compensated, stretch> launch, from
-# one ncu capture of that launch per workload (profiles/sweep_kernel_*.md), keyed by
+# DRAM bytes (read + write) of one sweep_kernel<grad, compensated, stretch> launch over the
+# particle tiles, from one ncu capture of that launch per workload (profiles/sweep_kernel_*.md), keyed by
 # (particles, segments); valid only while the kernel's sources hash to SWEEP_SRC_SHA256,
 # else the bench reports traffic null.
 SWEEP_TRAFFIC_BYTES = {(2_000_000, 7_680): 156_304_597_000 + 354_574_336}
@@ -463,7 +463,8 @@ def timed_loop(hp, prm, steps, warmup, flush, dist, trace=False):
     tr = None
     if trace:
         tr = {k: api.trace_read(k) for k in (_lib.VPM_TRACE_ALL, _lib.VPM_TRACE_SWEEP, _lib.VPM_TRACE_ADJOINT,
-                                             _lib.VPM_TRACE_PSE, _lib.VPM_TRACE_SWEEP_VEL)}
+                                             _lib.VPM_TRACE_PSE, _lib.VPM_TRACE_SWEEP_VEL,
+                                             _lib.VPM_TRACE_SEGMENTS)}
         api.trace_enable(False)
     return total, tr
 
@@ -582,12 +583,20 @@ def roofline(tr, n, m, sms, clk):
     peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x FFMA x max SM clock, TFLOP/s
     nl, sms_ms = tr[_lib.VPM_TRACE_SWEEP]
     avg_ms = sms_ms / max(nl, 1)
-    flops_launch = FLOPS_P2P * n * (n - 1) + FLOPS_SEG * n * m
+    ns_, seg_ms = tr.get(_lib.VPM_TRACE_SEGMENTS, (0, 0.0))
+    # a small problem sweeps its segment tiles in the particle launch (no segment launch)
+    flops_launch = FLOPS_P2P * n * (n - 1) + (FLOPS_SEG * n * m if not ns_ else 0)
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": sweep_traffic(n, m), "kernel": "sweep_kernel<grad, compensated, stretch>", "launches": nl,
-            "avg_launch_ms": avg_ms, "flops_per_launch": flops_launch,
+            "traffic": sweep_traffic(n, m), "kernel": "sweep_kernel<grad, compensated, stretch, particle tiles>",
+            "launches": nl, "avg_launch_ms": avg_ms, "flops_per_launch": flops_launch,
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 (FFMA) x {sm_max:.0f} MHz max SM clock (derived)"}
+    if ns_ and m:
+        seg_avg = seg_ms / ns_
+        seg_t = FLOPS_SEG * n * m / (seg_avg * 1e-3) / 1e12
+        roof["segment_launch"] = {"kernel": "sweep_kernel<grad, compensated, stretch, segment tiles>",
+                                  "launches": ns_, "avg_launch_ms": seg_avg, "flops_per_launch": FLOPS_SEG * n * m,
+                                  "achieved": seg_t, "frac": seg_t / peak}
     if clk and clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
     return roof
@@ -626,7 +635,13 @@ def extras(hp, args, flush, rank):
         reps = 1 if n >= 1_000_000 else 3
         p_ms = ms_of(lambda: api.induce(P, S, P, w.sigma, compensated=True, ws=pws), reps)
         pp_ms = ms_of(lambda: api.induce(P, S, P, w.sigma, compensated=False, ws=pws), reps)
+        from paper_2511_11430_gb300 import _lib
+
+        api.trace_reset()
+        api.trace_enable(True)
         s_ms = ms_of(lambda: api.segments_induce(sa, sb, P, w.seg_core, 2, compensated=True, ws=pws), 3)
+        nls, tls = api.trace_read(_lib.VPM_TRACE_SEGMENTS)
+        api.trace_enable(False)
         pp, sp_ = n * (n - 1), n * m
         out["sweep_parts"] = {
             "p2p": {"pairs": pp, "ms": p_ms, "pairs_per_s": pp / (p_ms * 1e-3),
@@ -634,7 +649,9 @@ def extras(hp, args, flush, rank):
             "p2p_plain": {"pairs": pp, "ms": pp_ms, "pairs_per_s": pp / (pp_ms * 1e-3),
                           "tflops": pp * FLOPS_P2P / (pp_ms * 1e-3) / 1e12},
             "segments": {"pairs": sp_, "ms": s_ms, "pairs_per_s": sp_ / (s_ms * 1e-3),
-                         "tflops": sp_ * FLOPS_SEG / (s_ms * 1e-3) / 1e12},
+                         "tflops": sp_ * FLOPS_SEG / (s_ms * 1e-3) / 1e12,
+                         "launch_ms": tls / max(nls, 1),
+                         "launch_tflops": sp_ * FLOPS_SEG / (tls / max(nls, 1) * 1e-3) / 1e12 if nls else None},
             "note": "vpm_induce (particles onto themselves) and vpm_segments_induce (segments onto the particles) "
                     "alone, u + grad u; includes each call's packing and epilogue"}
         del P, S, pws
@@ -779,7 +796,8 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_total),
             "clocks": clk, "plain": plain, "error": err,
             "kernel_ms": {"sweep_grad": list(tr[_lib.VPM_TRACE_SWEEP]), "adjoint": list(tr[_lib.VPM_TRACE_ADJOINT]),
-                          "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL])},
+                          "pse": list(tr[_lib.VPM_TRACE_PSE]), "sweep_vel": list(tr[_lib.VPM_TRACE_SWEEP_VEL]),
+                          "segments": list(tr[_lib.VPM_TRACE_SEGMENTS])},
         }
         line.update(ext)
         print(json.dumps(line), flush=True)

@@ -43,6 +43,7 @@ VPM_TRACE_SWEEP = 1
 VPM_TRACE_ADJOINT = 2
 VPM_TRACE_PSE = 3
 VPM_TRACE_SWEEP_VEL = 4
+VPM_TRACE_SEGMENTS = 5
 
 VPM_MAX_ITEMS = 1 << 30
 VPM_MAX_AIC = 8192

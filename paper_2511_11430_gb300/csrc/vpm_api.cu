@@ -114,7 +114,7 @@ size_t tree_step_extra(int64_t n)
 bool overflow_guard(const SweepPlan& p)
 {
     // keep tot * B < 2^62 for the 64-bit stream-K arithmetic
-    return (double)p.sk.tot * (double)p.sk.B < 4.0e18;
+    return (double)p.sk.tot * (double)p.sk.B < 4.0e18 && (double)p.sks.tot * (double)p.sks.B < 4.0e18;
 }
 
 vpm_status check_params(const vpm_params* prm)

@@ -36,7 +36,7 @@ struct Carve {
 
 int sm_count();
 int* dev_err_ptr();          // device error word of the current device
-int sweep_blocks(bool grad, bool comp, bool stretch);  // resident sweep blocks on the current device
+int sweep_blocks(bool grad, bool comp, bool stretch, bool segments = false);  // resident sweep blocks (current device)
 int adjoint_blocks(bool comp);
 
 struct SweepPlan {
@@ -45,12 +45,16 @@ struct SweepPlan {
     bool grad = false, comp = false;
     bool stretch = false;  // accumulate the transposed stretching J^T Gamma_i per target
     int ncomp = 0;         // logical accumulator rows (3, 14 or 17)
-    StreamK sk{};
-    size_t off_psrc = 0, off_pbox = 0, off_ssrc = 0, off_sbox = 0, off_part = 0, bytes = 0;
+    bool mixed = false;  // particle and segment tiles in one launch (small problems)
+    StreamK sk{};        // particle tiles, and the segment tiles when mixed (one launch)
+    StreamK sks{};       // otherwise the segment tiles (a launch of their own)
+    size_t off_psrc = 0, off_pbox = 0, off_ssrc = 0, off_sbox = 0, off_part = 0, off_part_s = 0, bytes = 0;
 };
 
-// Plans a particle + segment sweep onto `n_tgt` targets starting at offset `base`
-// of a workspace carve; fills sk and the sub-buffer offsets.
+// Plans a particle + segment sweep onto `n_tgt` targets from a workspace carve: the
+// particle tiles and the segment tiles are split stream-K in two launches (sk, sks),
+// each with its own partial sums, or in one (sk) for a small problem; fills the
+// sub-buffer offsets.
 SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv,
                      bool stretch = false);
 
@@ -137,7 +141,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
                          double* berr, char* ws, cudaStream_t st, const char** msg);
 
 // Launch tracing (vpm_trace_*): count launches; time the bracketed kernels.
-constexpr int TRACE_KINDS = 5;
+constexpr int TRACE_KINDS = 6;
 void trace_launch(int count = 1);
 class TraceScope {
   public:

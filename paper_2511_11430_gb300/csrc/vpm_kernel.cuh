@@ -267,19 +267,13 @@ __device__ __forceinline__ void seg_lane(float n1, float n2, float c2, float L2,
 // SAFE: the warp's targets are at least 1e-3 of the longest segment away from the
 // tile's bounding box and the core is positive, so no guard can trigger and every
 // reciprocal is taken on both lanes at once.
+// One segment (r0 = b - a and its negation, L2 = |r0|^2, e, circulation gs) against
+// the thread's two targets at r1 = x - a, r2 = x - b.
 template <bool GRAD, bool STRETCH, bool SAFE>
-__device__ __forceinline__ void segment_source(Acc<GRAD, STRETCH>& a, const float4* __restrict__ e4, f2 X, f2 Y, f2 Z,
-                                               int vn)
+__device__ __forceinline__ void segment_pair(Acc<GRAD, STRETCH>& a, f2 r0x, f2 r0y, f2 r0z, f2 nr0x, f2 nr0y, f2 nr0z,
+                                             f2 L2, f2 e, f2 gs, f2 r1x, f2 r1y, f2 r1z, f2 r2x, f2 r2y, f2 r2z, int vn)
 {
     {
-        const float4 s0 = e4[0], s1 = e4[1], s2 = e4[2], s3 = e4[3], s4 = e4[4], s5 = e4[5];
-        const f2 r0x = make_float2(s1.z, s1.w), r0y = make_float2(s2.x, s2.y), r0z = make_float2(s2.z, s2.w);
-        const f2 nr0x = make_float2(s3.x, s3.y), nr0y = make_float2(s3.z, s3.w), nr0z = make_float2(s4.x, s4.y);
-        const f2 nL2 = make_float2(s4.z, s4.w), gs = make_float2(s5.x, s5.y);
-        const f2 r1x = add2(X, make_float2(s0.x, s0.y));
-        const f2 r1y = add2(Y, make_float2(s0.z, s0.w));
-        const f2 r1z = add2(Z, make_float2(s1.x, s1.y));
-        const f2 r2x = add2(r1x, nr0x), r2y = add2(r1y, nr0y), r2z = add2(r1z, nr0z);
         const f2 cx = fma2(r0y, r1z, mul2(nr0z, r1y));
         const f2 cy = fma2(r0z, r1x, mul2(nr0x, r1z));
         const f2 cz = fma2(r0x, r1y, mul2(nr0y, r1x));
@@ -291,14 +285,12 @@ __device__ __forceinline__ void segment_source(Acc<GRAD, STRETCH>& a, const floa
         if (SAFE) {
             i1 = rsqrt2_approx(n1);
             i2 = rsqrt2_approx(n2);
-            const f2 e = make_float2(s5.z, s5.w);
             invD = vn == 2 ? rsqrt2_approx(fma2(c2, c2, e)) : rcp2_approx(add2(c2, e));
             irs = rcp2_approx(fma2(n1, i1, mul2(n2, i2)));
         } else {
-            seg_lane(n1.x, n2.x, c2.x, -s4.z, s5.z, vn, i1.x, i2.x, irs.x, invD.x);
-            seg_lane(n1.y, n2.y, c2.y, -s4.z, s5.z, vn, i1.y, i2.y, irs.y, invD.y);
+            seg_lane(n1.x, n2.x, c2.x, L2.x, e.x, vn, i1.x, i2.x, irs.x, invD.x);
+            seg_lane(n1.y, n2.y, c2.y, L2.y, e.y, vn, i1.y, i2.y, irs.y, invD.y);
         }
-        const f2 L2 = mul2(nL2, splat(-1.f));
         const f2 di = mul2(mul2(fma2(splat(-2.f), p1, L2), mul2(i1, i2)), irs);  // 1/|r1| - 1/|r2|
         const f2 d = fma2(p1, di, mul2(L2, i2));
         const f2 gi = mul2(gs, invD);
@@ -341,6 +333,22 @@ __device__ __forceinline__ void segment_source(Acc<GRAD, STRETCH>& a, const floa
     }
 }
 
+template <bool GRAD, bool STRETCH, bool SAFE>
+__device__ __forceinline__ void segment_source(Acc<GRAD, STRETCH>& a, const float4* __restrict__ e4, f2 X, f2 Y, f2 Z,
+                                               int vn)
+{
+    const float4 s0 = e4[0], s1 = e4[1], s2 = e4[2], s3 = e4[3], s4 = e4[4], s5 = e4[5];
+    const f2 r0x = make_float2(s1.z, s1.w), r0y = make_float2(s2.x, s2.y), r0z = make_float2(s2.z, s2.w);
+    const f2 nr0x = make_float2(s3.x, s3.y), nr0y = make_float2(s3.z, s3.w), nr0z = make_float2(s4.x, s4.y);
+    const f2 L2 = mul2(make_float2(s4.z, s4.w), splat(-1.f));
+    const f2 r1x = add2(X, make_float2(s0.x, s0.y));
+    const f2 r1y = add2(Y, make_float2(s0.z, s0.w));
+    const f2 r1z = add2(Z, make_float2(s1.x, s1.y));
+    const f2 r2x = add2(r1x, nr0x), r2y = add2(r1y, nr0y), r2z = add2(r1z, nr0z);
+    segment_pair<GRAD, STRETCH, SAFE>(a, r0x, r0y, r0z, nr0x, nr0y, nr0z, L2, make_float2(s5.z, s5.w),
+                                      make_float2(s5.x, s5.y), r1x, r1y, r1z, r2x, r2y, r2z, vn);
+}
+
 // The sources of a segment tile (S_F4 float4 each) against the thread's two targets.
 template <bool GRAD, bool STRETCH, bool SAFE>
 __device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y,
@@ -348,6 +356,142 @@ __device__ __forceinline__ void segment_tile(Acc<GRAD, STRETCH>& a, const float4
 {
 #pragma unroll 2
     for (int j = 0; j < cnt; ++j) segment_source<GRAD, STRETCH, SAFE>(a, s + j * S_F4, X, Y, Z, vn);
+}
+
+// ---------------------------------------------------------------------------
+// Closed four-sided rings (the blade and wake vortex rings of Sec. II.A): side k runs
+// from corner c_k to corner c_(k+1 mod 4), so side k's r2 = x - c_(k+1) is side k+1's r1.
+// A tile whose segments all form such rings (in groups of four, bit-exact shared end
+// points) is packed by ring, and each target evaluates x - c, |x - c|^2, 1/|x - c|,
+// |x - c| and 1/|x - c|^3 once per corner instead of once per side end.  Packed ring
+// (24 float4 = four segments' worth; pair p = floats 2p, 2p + 1, both lanes equal):
+//   pairs  0..11  -c_k (k = 0..3; x, y, z)
+//   pairs 12..23  r0_k = c_(k+1) - c_k        pairs 24..35  -r0_k
+//   pairs 36..43  (L2_k, e_k)                 pairs 44..47  G_k
+// The side terms are those of segment_source, with 1/|r1| - 1/|r2| formed as
+// (L2 - 2 r0.r1) / (|r1| |r2| (|r1| + |r2|)) from one reciprocal.
+// ---------------------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ f2 ring_pair(const float4* __restrict__ e4)
+{
+    const float4 q = e4[P >> 1];
+    return (P & 1) ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+}
+
+struct RingCorner {
+    f2 x, y, z;  // x - c
+    f2 n;        // |x - c|^2
+    f2 i;        // 1 / |x - c|
+    f2 len;      // |x - c|
+    f2 i3;       // 1 / |x - c|^3
+};
+
+template <int K>
+__device__ __forceinline__ RingCorner ring_corner(const float4* __restrict__ e4, f2 X, f2 Y, f2 Z)
+{
+    RingCorner c;
+    c.x = add2(X, ring_pair<3 * K>(e4));
+    c.y = add2(Y, ring_pair<3 * K + 1>(e4));
+    c.z = add2(Z, ring_pair<3 * K + 2>(e4));
+    c.n = fma2(c.z, c.z, fma2(c.y, c.y, mul2(c.x, c.x)));
+    c.i = rsqrt2_approx(c.n);
+    c.len = mul2(c.n, c.i);
+    c.i3 = mul2(mul2(c.i, c.i), c.i);
+    return c;
+}
+
+// Side K of a ring between corners c1 = c_K and c2 = c_(K+1), for targets clear of the
+// tile (no guard can trigger; as SAFE in segment_source).
+template <bool GRAD, int K>
+__device__ __forceinline__ void ring_side(Acc<GRAD, false>& a, const float4* __restrict__ e4, const RingCorner& c1,
+                                          const RingCorner& c2, int vn)
+{
+    const f2 r0x = ring_pair<12 + 3 * K>(e4), r0y = ring_pair<13 + 3 * K>(e4), r0z = ring_pair<14 + 3 * K>(e4);
+    const f2 nr0x = ring_pair<24 + 3 * K>(e4), nr0y = ring_pair<25 + 3 * K>(e4), nr0z = ring_pair<26 + 3 * K>(e4);
+    const f2 L2 = ring_pair<36 + 2 * K>(e4), e = ring_pair<37 + 2 * K>(e4), gs = ring_pair<44 + K>(e4);
+    const f2 r1x = c1.x, r1y = c1.y, r1z = c1.z;
+    const f2 cx = fma2(r0y, r1z, mul2(nr0z, r1y));
+    const f2 cy = fma2(r0z, r1x, mul2(nr0x, r1z));
+    const f2 cz = fma2(r0x, r1y, mul2(nr0y, r1x));
+    const f2 p1 = fma2(r0z, r1z, fma2(r0y, r1y, mul2(r0x, r1x)));
+    const f2 c2n = fma2(cz, cz, fma2(cy, cy, mul2(cx, cx)));
+    const f2 invD = vn == 2 ? rsqrt2_approx(fma2(c2n, c2n, e)) : rcp2_approx(add2(c2n, e));
+    const f2 rP = rcp2_approx(mul2(mul2(c1.len, c2.len), add2(c1.len, c2.len)));
+    const f2 i2 = c2.i, i1c = c1.i3, ni2c = mul2(c2.i3, splat(-1.f));
+    const f2 di = mul2(fma2(splat(-2.f), p1, L2), rP);  // 1/|r1| - 1/|r2|
+    const f2 d = fma2(p1, di, mul2(L2, i2));
+    const f2 gi = mul2(gs, invD);
+    const f2 coef = mul2(gi, d);
+    a.v[0] = fma2(coef, cx, a.v[0]);
+    a.v[1] = fma2(coef, cy, a.v[1]);
+    a.v[2] = fma2(coef, cz, a.v[2]);
+    if (GRAD) {
+        a.v[3] = fma2(coef, r0x, a.v[3]);
+        a.v[4] = fma2(coef, r0y, a.v[4]);
+        a.v[5] = fma2(coef, r0z, a.v[5]);
+        f2 k3;
+        if (vn == 2) {
+            const f2 tmp = mul2(mul2(d, c2n), mul2(invD, invD));
+            k3 = add2(tmp, tmp);
+        } else {
+            const f2 tmp = mul2(d, invD);
+            k3 = add2(tmp, tmp);
+        }
+        const f2 vx = fma2(k3, r0x, fma2(r1x, i1c, mul2(c2.x, ni2c)));
+        const f2 vy = fma2(k3, r0y, fma2(r1y, i1c, mul2(c2.y, ni2c)));
+        const f2 vz = fma2(k3, r0z, fma2(r1z, i1c, mul2(c2.z, ni2c)));
+        const f2 nvx = mul2(vx, splat(-1.f)), nvy = mul2(vy, splat(-1.f)), nvz = mul2(vz, splat(-1.f));
+        const f2 wx = fma2(vy, cz, mul2(nvz, cy));  // w = v x c
+        const f2 wy = fma2(vz, cx, mul2(nvx, cz));
+        const f2 wz = fma2(vx, cy, mul2(nvy, cx));
+        const f2 cg = mul2(gi, splat(-1.0f / 3.0f));  // stored as G' with J = -3 G'
+        const f2 gx = mul2(cg, cx), gy = mul2(cg, cy), gz = mul2(cg, cz);
+        a.v[6] = fma2(gx, wx, a.v[6]);
+        a.v[7] = fma2(gx, wy, a.v[7]);
+        a.v[8] = fma2(gx, wz, a.v[8]);
+        a.v[9] = fma2(gy, wx, a.v[9]);
+        a.v[10] = fma2(gy, wy, a.v[10]);
+        a.v[11] = fma2(gy, wz, a.v[11]);
+        a.v[12] = fma2(gz, wx, a.v[12]);
+        a.v[13] = fma2(gz, wy, a.v[13]);
+    }
+}
+
+// The rings of a ring-packed segment tile (cnt rings, 4 S_F4 float4 each).  Targets
+// close to the tile (SAFE false) take segment_pair's guarded form side by side, with
+// r2 = x - c_(k+1) read from the next corner.
+template <bool GRAD, bool SAFE>
+__device__ __forceinline__ void ring_tile(Acc<GRAD, false>& a, const float4* __restrict__ s, int cnt, f2 X, f2 Y,
+                                          f2 Z, int vn)
+{
+    if constexpr (SAFE) {
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) {
+            const float4* e4 = s + j * 4 * S_F4;
+            const RingCorner c0 = ring_corner<0>(e4, X, Y, Z);
+            const RingCorner c1 = ring_corner<1>(e4, X, Y, Z);
+            ring_side<GRAD, 0>(a, e4, c0, c1, vn);
+            const RingCorner c2 = ring_corner<2>(e4, X, Y, Z);
+            ring_side<GRAD, 1>(a, e4, c1, c2, vn);
+            const RingCorner c3 = ring_corner<3>(e4, X, Y, Z);
+            ring_side<GRAD, 2>(a, e4, c2, c3, vn);
+            ring_side<GRAD, 3>(a, e4, c3, c0, vn);
+        }
+    } else {
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) {
+            const float2* p = reinterpret_cast<const float2*>(s + j * 4 * S_F4);
+#pragma unroll 1
+            for (int k = 0; k < 4; ++k) {
+                const int k1 = (k + 1) & 3;
+                const f2 r1x = add2(X, p[3 * k]), r1y = add2(Y, p[3 * k + 1]), r1z = add2(Z, p[3 * k + 2]);
+                const f2 r2x = add2(X, p[3 * k1]), r2y = add2(Y, p[3 * k1 + 1]), r2z = add2(Z, p[3 * k1 + 2]);
+                segment_pair<GRAD, false, false>(a, p[12 + 3 * k], p[13 + 3 * k], p[14 + 3 * k], p[24 + 3 * k],
+                                                 p[25 + 3 * k], p[26 + 3 * k], p[36 + 2 * k], p[37 + 2 * k],
+                                                 p[44 + k], r1x, r1y, r1z, r2x, r2y, r2z, vn);
+            }
+        }
+    }
 }
 
 }  // namespace vpm

@@ -132,29 +132,60 @@ __global__ void __launch_bounds__(SRC_TILE) pack_particles_kernel(const float4* 
 
 __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* __restrict__ sa,
                                                                  const float4* __restrict__ sb, int m, float core,
-                                                                 int vn, float4* __restrict__ out,
+                                                                 int vn, int rings, float4* __restrict__ out,
                                                                  float4* __restrict__ box)
 {
     const int j = blockIdx.x * SRC_TILE + threadIdx.x;
     const bool valid = j < m;
     float ax = 0.f, ay = 0.f, az = 0.f, rx = 1.f, ry = 0.f, rz = 0.f, g = 0.f;
+    float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
-        const float4 a = sa[j], b = sb[j];
+        const float4 a = sa[j];
+        bb = sb[j];
         ax = a.x, ay = a.y, az = a.z;
-        rx = b.x - a.x, ry = b.y - a.y, rz = b.z - a.z;
+        rx = bb.x - a.x, ry = bb.y - a.y, rz = bb.z - a.z;
         g = a.w;
     }
     const float L2 = rx * rx + ry * ry + rz * rz;
     const float cl2 = core * core * L2;
     float e = vn == 2 ? cl2 * cl2 : cl2;
     if (!(L2 > 0.f)) g = 0.f, e = 1.f;  // a zero-length segment induces nothing; keeps D > 0
-    float4* o = out + (size_t)j * S_F4;
-    o[0] = make_float4(-ax, -ax, -ay, -ay);
-    o[1] = make_float4(-az, -az, rx, rx);
-    o[2] = make_float4(ry, ry, rz, rz);
-    o[3] = make_float4(-rx, -rx, -ry, -ry);
-    o[4] = make_float4(-rz, -rz, -L2, -L2);
-    o[5] = make_float4(g, g, e, e);
+    // Closed four-sided rings: in every group of four segments of the tile, each one's
+    // end point is the next one's start point (k -> k + 1 mod 4), bit for bit; groups
+    // wholly past the end do not count.  Such a tile is packed by ring.
+    const int lane = threadIdx.x & 31, nxt = (lane & ~3) | ((lane + 1) & 3);
+    const float nax = __shfl_sync(0xffffffffu, ax, nxt), nay = __shfl_sync(0xffffffffu, ay, nxt),
+                naz = __shfl_sync(0xffffffffu, az, nxt);
+    const bool joins = valid && __float_as_uint(bb.x) == __float_as_uint(nax) &&
+                       __float_as_uint(bb.y) == __float_as_uint(nay) && __float_as_uint(bb.z) == __float_as_uint(naz);
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid), jmask = __ballot_sync(0xffffffffu, joins);
+    const int g4 = lane & ~3;
+    const bool ring_ok = ((vmask >> g4) & 0xFu) == 0u || ((jmask >> g4) & 0xFu) == 0xFu;
+    const bool closed = __syncthreads_and(ring_ok && rings) != 0;
+    if (closed) {
+        float2* o2 = reinterpret_cast<float2*>(out + (size_t)blockIdx.x * SRC_TILE * S_F4) + (threadIdx.x >> 2) * 48;
+        const int k = threadIdx.x & 3;
+        o2[3 * k] = make_float2(-ax, -ax);
+        o2[3 * k + 1] = make_float2(-ay, -ay);
+        o2[3 * k + 2] = make_float2(-az, -az);
+        o2[12 + 3 * k] = make_float2(rx, rx);
+        o2[13 + 3 * k] = make_float2(ry, ry);
+        o2[14 + 3 * k] = make_float2(rz, rz);
+        o2[24 + 3 * k] = make_float2(-rx, -rx);
+        o2[25 + 3 * k] = make_float2(-ry, -ry);
+        o2[26 + 3 * k] = make_float2(-rz, -rz);
+        o2[36 + 2 * k] = make_float2(L2, L2);
+        o2[37 + 2 * k] = make_float2(e, e);
+        o2[44 + k] = make_float2(g, g);
+    } else {
+        float4* o = out + (size_t)j * S_F4;
+        o[0] = make_float4(-ax, -ax, -ay, -ay);
+        o[1] = make_float4(-az, -az, rx, rx);
+        o[2] = make_float4(ry, ry, rz, rz);
+        o[3] = make_float4(-rx, -rx, -ry, -ry);
+        o[4] = make_float4(-rz, -rz, -L2, -L2);
+        o[5] = make_float4(g, g, e, e);
+    }
     // tile box of both end points, and the longest segment (in lo.w)
     const float bx = ax + rx, by = ay + ry, bz = az + rz;
     float lo[4] = {valid ? fminf(ax, bx) : INFINITY, valid ? fminf(ay, by) : INFINITY,
@@ -181,7 +212,7 @@ __global__ void __launch_bounds__(SRC_TILE) pack_segments_kernel(const float4* _
             for (int c = 0; c < 3; ++c) hi[c] = fmaxf(hi[c], sbx[ww][4 + c]);
         }
         box[2 * blockIdx.x] = make_float4(lo[0], lo[1], lo[2], -lo[3]);
-        box[2 * blockIdx.x + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        box[2 * blockIdx.x + 1] = make_float4(hi[0], hi[1], hi[2], closed ? 1.f : 0.f);
     }
 }
 
@@ -223,7 +254,15 @@ __host__ __device__ constexpr size_t sweep_smem_bytes()
     return (size_t)SWEEP_STAGES * BUF_F4 * 16 + (size_t)n_rows<GRAD, STRETCH>() * (COMP ? 2 : 1) * SWEEP_CW * 32 * 8;
 }
 
-template <bool GRAD, bool COMP, bool STRETCH>
+// KIND: the source tiles a launch sweeps.  SWEEP_PARTICLES takes particle tiles and,
+// in the one-launch plan of small problems, segment tiles one segment at a time;
+// SWEEP_SEGMENTS takes only segment tiles, including those packed as closed rings.
+// The ring loop needs more registers than the particle loop; in a launch of its own
+// it costs the particle tiles nothing.  (Measured: the particle launch compiled
+// without its segment loop is allocated fewer registers and runs 4% slower.)
+constexpr int SWEEP_PARTICLES = 0, SWEEP_SEGMENTS = 1;
+
+template <bool GRAD, bool COMP, bool STRETCH, int KIND>
 __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
 {
     extern __shared__ __align__(128) float4 dsm[];
@@ -328,7 +367,7 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
         // stretching from the tile's sums afterwards.  Near particle tiles accumulate the
         // stretching pair by pair (it cancels there) with the strengths loaded for them.
         const int ti0 = t * TGT_TILE + warp * 64 + lane, ti1 = ti0 + 32;
-        if (k < sk.np) {
+        if (KIND == SWEEP_PARTICLES && k < sk.np) {
             const int cnt = min(SRC_TILE, A.n_src - k * SRC_TILE);
             const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
             if (boxes_near(wbox[warp], tlo, thi, A.nc.far2)) {
@@ -353,12 +392,19 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
             const int cnt = min(SRC_TILE, A.m_seg - (k - sk.np) * SRC_TILE);
             const float4 tlo = src[SRC_TILE * S_F4], thi = src[SRC_TILE * S_F4 + 1];
             const float margin = 1e-3f * tlo.w;
+            const bool safe = A.core_pos && margin > 0.f && !boxes_near(wbox[warp], tlo, thi, margin * margin);
             Acc<GRAD, false> tf;
             tf.zero();
-            if (A.core_pos && margin > 0.f && !boxes_near(wbox[warp], tlo, thi, margin * margin))
+            if (KIND == SWEEP_SEGMENTS && thi.w != 0.f) {  // closed four-sided rings, packed by corner
+                if (safe)
+                    ring_tile<GRAD, true>(tf, src, cnt >> 2, X, Y, Z, A.vn);
+                else
+                    ring_tile<GRAD, false>(tf, src, cnt >> 2, X, Y, Z, A.vn);
+            } else if (safe) {
                 segment_tile<GRAD, false, true>(tf, src, cnt, X, Y, Z, A.vn);
-            else
+            } else {
                 segment_tile<GRAD, false, false>(tf, src, cnt, X, Y, Z, A.vn);
+            }
             finish_tile<GRAD, STRETCH>(acc, tf, A.tstr, ti0, ti1, A.n_tgt);
         }
         __syncwarp();
@@ -405,8 +451,9 @@ __global__ void __launch_bounds__(SWEEP_TPB, 1) sweep_kernel(const SweepArgs A)
 // Reduction of the stream-K partial sums (fixed order, FP64) and epilogue.
 // ---------------------------------------------------------------------------
 struct EpiArgs {
-    StreamK sk;
+    StreamK sk, sks;  // the particle and the segment launch
     const float* part;
+    const float* part_s;
     int n, ncomp, comp;
     EpilogueOut o;
     int* dev_err;
@@ -421,13 +468,16 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= E.n) return;
-    const StreamK& sk = E.sk;
     const int t = i / TGT_TILE, l = i % TGT_TILE;
-    const int nunits = sk.np + sk.ns;
     double acc[17];
 #pragma unroll
     for (int c = 0; c < 17; ++c) acc[c] = 0.0;
-    if (nunits > 0) {
+    // the partial sums of the particle launch, then those of the segment launch
+    for (int launch = 0; launch < 2; ++launch) {
+        const StreamK& sk = launch ? E.sks : E.sk;
+        const float* part = launch ? E.part_s : E.part;
+        const int nunits = sk.np + sk.ns;
+        if (nunits == 0) continue;
         const int b0 = sk.block_of(sk.unit_start(t, 0));
         const int b1 = sk.block_of(sk.unit_start(t, nunits - 1));
         const int rows = E.comp ? 2 * E.ncomp : E.ncomp;
@@ -437,7 +487,7 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
             int tt, kk;
             sk.first_at_or_after(c0, tt, kk);
             if (tt != t || sk.unit_start(tt, kk) >= hi_b) continue;  // block b ran no unit of tile t
-            const float* P = E.part + (size_t)(b + t) * rows * TGT_TILE + l;
+            const float* P = part + (size_t)(b + t) * rows * TGT_TILE + l;
 #pragma unroll
             for (int c = 0; c < 17; ++c) {  // a constant bound keeps acc in registers
                 if (c < E.ncomp) {
@@ -624,8 +674,8 @@ __device__ int g_dev_err;  // device error word (one instance per device)
 namespace {
 std::mutex g_mu;
 int g_sm[64];
-int g_blocks[64][8];
-bool g_attr[64][8];
+int g_blocks[64][16];
+bool g_attr[64][16];
 }  // namespace
 
 static int cur_dev()
@@ -657,21 +707,21 @@ int* dev_err_ptr()
     return static_cast<int*>(p);
 }
 
-static int variant(bool G, bool C, bool S) { return (G ? 4 : 0) + (C ? 2 : 0) + (S ? 1 : 0); }
+static int variant(bool G, bool C, bool S, int K) { return 8 * K + (G ? 4 : 0) + (C ? 2 : 0) + (S ? 1 : 0); }
 
 // Opts the kernel into its dynamic shared memory (once per device) and returns the resident blocks per SM.
-template <bool G, bool C, bool S>
+template <bool G, bool C, bool S, int K>
 static int prepare_kernel(int d)
 {
-    const int v = variant(G, C, S);
+    const int v = variant(G, C, S, K);
     const size_t smem = sweep_smem_bytes<G, C, S>();
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (d >= 0 && d < 64 && g_attr[d][v]) return g_blocks[d][v];
     }
-    cudaFuncSetAttribute(sweep_kernel<G, C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(sweep_kernel<G, C, S, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, C, S>, SWEEP_TPB, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<G, C, S, K>, SWEEP_TPB, smem) != cudaSuccess)
         nb = 1;
     if (nb < 1) nb = 1;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -682,18 +732,24 @@ static int prepare_kernel(int d)
     return nb;
 }
 
-static int blocks_per_sm(bool g, bool c, bool s)
+template <int K>
+static int blocks_per_sm_kind(bool g, bool c, bool s)
 {
     const int d = cur_dev();
-    if (g && s) return c ? prepare_kernel<true, true, true>(d) : prepare_kernel<true, false, true>(d);
-    if (g) return c ? prepare_kernel<true, true, false>(d) : prepare_kernel<true, false, false>(d);
-    return c ? prepare_kernel<false, true, false>(d) : prepare_kernel<false, false, false>(d);
+    if (g && s) return c ? prepare_kernel<true, true, true, K>(d) : prepare_kernel<true, false, true, K>(d);
+    if (g) return c ? prepare_kernel<true, true, false, K>(d) : prepare_kernel<true, false, false, K>(d);
+    return c ? prepare_kernel<false, true, false, K>(d) : prepare_kernel<false, false, false, K>(d);
 }
 
-int sweep_blocks(bool grad, bool comp, bool stretch)
+static int blocks_per_sm(bool g, bool c, bool s, bool segments)
+{
+    return segments ? blocks_per_sm_kind<SWEEP_SEGMENTS>(g, c, s) : blocks_per_sm_kind<SWEEP_PARTICLES>(g, c, s);
+}
+
+int sweep_blocks(bool grad, bool comp, bool stretch, bool segments)
 {
     const int sms = sm_count();
-    return blocks_per_sm(grad, comp, stretch && grad) * (sms > 0 ? sms : 1);
+    return blocks_per_sm(grad, comp, stretch && grad, segments) * (sms > 0 ? sms : 1);
 }
 
 SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, bool comp, Carve& cv, bool stretch)
@@ -709,33 +765,46 @@ SweepPlan plan_sweep(int64_t n_tgt, int64_t n_src, int64_t m_seg, bool grad, boo
     p.TT = (int)((n_tgt + TGT_TILE - 1) / TGT_TILE);
     p.SP = (int)((n_src + SRC_TILE - 1) / SRC_TILE);
     p.SS = (int)((m_seg + SRC_TILE - 1) / SRC_TILE);
-    StreamK& sk = p.sk;
-    sk.TT = p.TT;
-    sk.np = p.SP;
-    sk.ns = p.SS;
-    sk.wp = UNIT_W_P;
-    sk.ws = grad ? UNIT_W_S_GRAD : UNIT_W_S_VEL;
-    sk.C = (long long)sk.np * sk.wp + (long long)sk.ns * sk.ws;
-    sk.tot = (long long)sk.TT * sk.C;
-    const long long units = (long long)sk.TT * (sk.np + sk.ns);
-    long long B = sweep_blocks(grad, comp, p.stretch);
-    if (B > units) B = units;
-    if (B < 1) B = 1;
-    sk.B = (int)B;
+    // particle tiles and segment tiles: one stream-K plan (and launch) each
+    auto plan = [&](StreamK& sk, int np, int ns) {
+        sk.TT = p.TT;
+        sk.np = np;
+        sk.ns = ns;
+        sk.wp = UNIT_W_P;
+        sk.ws = grad ? UNIT_W_S_GRAD : UNIT_W_S_VEL;
+        sk.C = (long long)sk.np * sk.wp + (long long)sk.ns * sk.ws;
+        sk.tot = (long long)sk.TT * sk.C;
+        const long long units = (long long)sk.TT * (sk.np + sk.ns);
+        long long B = sweep_blocks(grad, comp, p.stretch, ns > 0);
+        if (B > units) B = units;
+        if (B < 1) B = 1;
+        sk.B = (int)B;
+    };
+    // A small problem (fewer cost units than four waves of resident blocks) sweeps both
+    // kinds of tile in one launch; a larger one gives the segment tiles a launch of
+    // their own, where closed rings are packed by corner.
+    const long long units_all = (long long)p.TT * (p.SP + p.SS);
+    p.mixed = p.SP > 0 && p.SS > 0 && units_all < 4LL * sweep_blocks(grad, comp, p.stretch, false);
+    plan(p.sk, p.SP, p.mixed ? p.SS : 0);
+    plan(p.sks, 0, p.mixed ? 0 : p.SS);
     p.off_psrc = cv.take((size_t)p.SP * SRC_TILE * P_F4 * 16);
     p.off_pbox = cv.take((size_t)p.SP * 2 * 16);
     p.off_ssrc = cv.take((size_t)p.SS * SRC_TILE * S_F4 * 16);
     p.off_sbox = cv.take((size_t)p.SS * 2 * 16);
     const size_t rows = (size_t)(comp ? 2 : 1) * p.ncomp;
-    p.off_part = cv.take((size_t)(sk.TT + sk.B) * rows * TGT_TILE * sizeof(float));
+    if (p.sk.np + p.sk.ns > 0) p.off_part = cv.take((size_t)(p.sk.TT + p.sk.B) * rows * TGT_TILE * sizeof(float));
+    if (p.sks.ns > 0) p.off_part_s = cv.take((size_t)(p.sks.TT + p.sks.B) * rows * TGT_TILE * sizeof(float));
     p.bytes = cv.off;
     return p;
 }
 
 template <bool G, bool C, bool S>
-static void launch_sweep(const SweepArgs& A, int B, cudaStream_t st)
+static void launch_sweep(const SweepArgs& A, int B, bool segments, cudaStream_t st)
 {
-    sweep_kernel<G, C, S><<<B, SWEEP_TPB, sweep_smem_bytes<G, C, S>(), st>>>(A);
+    if (segments)
+        sweep_kernel<G, C, S, SWEEP_SEGMENTS><<<B, SWEEP_TPB, sweep_smem_bytes<G, C, S>(), st>>>(A);
+    else
+        sweep_kernel<G, C, S, SWEEP_PARTICLES><<<B, SWEEP_TPB, sweep_smem_bytes<G, C, S>(), st>>>(A);
 }
 
 cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const float* src_pos, const float* src_str,
@@ -748,6 +817,7 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
     float4* ssrc = reinterpret_cast<float4*>(ws + p.off_ssrc);
     float4* sbox = reinterpret_cast<float4*>(ws + p.off_sbox);
     float* part = reinterpret_cast<float*>(ws + p.off_part);
+    float* part_s = reinterpret_cast<float*>(ws + p.off_part_s);
     if (p.SP > 0) {
         trace_launch();
         pack_particles_kernel<<<p.SP, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(src_pos),
@@ -758,11 +828,12 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
         trace_launch();
         pack_segments_kernel<<<p.SS, SRC_TILE, 0, st>>>(reinterpret_cast<const float4*>(seg_a),
                                                         reinterpret_cast<const float4*>(seg_b), p.m_seg, seg_core,
-                                                        vatistas_n, ssrc, sbox);
+                                                        vatistas_n, p.mixed ? 0 : 1, ssrc, sbox);
     }
     int* err = dev_err_ptr();
     if (p.SP + p.SS > 0) {
-        blocks_per_sm(p.grad, p.comp, p.stretch);  // ensures the shared-memory opt-in
+        if (p.sk.np + p.sk.ns > 0) blocks_per_sm(p.grad, p.comp, p.stretch, false);  // shared-memory opt-in
+        if (p.sks.ns > 0) blocks_per_sm(p.grad, p.comp, p.stretch, true);
         SweepArgs A;
         A.tgt = reinterpret_cast<const float4*>(tgt);
         A.tstr = p.stretch ? reinterpret_cast<const float4*>(out.str) : nullptr;
@@ -781,30 +852,37 @@ cudaError_t run_sweep(const SweepPlan& p, char* ws, const float* tgt, const floa
         A.nc.inv_s3 = (float)(1.0 / (s * s * s));
         A.nc.inv_s5 = (float)(1.0 / (s * s * s * s * s));
         A.nc.far2 = (float)((double)RHO_FAR * RHO_FAR * s * s);
-        A.part = part;
         A.dev_err = err;
-        const int B = p.sk.B;
-        TraceScope ts(p.grad ? VPM_TRACE_SWEEP : VPM_TRACE_SWEEP_VEL, st);
-        if (p.grad && p.stretch) {
-            if (p.comp)
-                launch_sweep<true, true, true>(A, B, st);
-            else
-                launch_sweep<true, false, true>(A, B, st);
-        } else if (p.grad) {
-            if (p.comp)
-                launch_sweep<true, true, false>(A, B, st);
-            else
-                launch_sweep<true, false, false>(A, B, st);
-        } else {
-            if (p.comp)
-                launch_sweep<false, true, false>(A, B, st);
-            else
-                launch_sweep<false, false, false>(A, B, st);
+        for (int kind = 0; kind < 2; ++kind) {
+            const bool seg = kind == 1;
+            if ((seg ? p.sks.ns : p.sk.np + p.sk.ns) == 0) continue;
+            TraceScope ts(seg ? VPM_TRACE_SEGMENTS : p.grad ? VPM_TRACE_SWEEP : VPM_TRACE_SWEEP_VEL, st);
+            A.sk = seg ? p.sks : p.sk;
+            A.part = seg ? part_s : part;
+            const int B = A.sk.B;
+            if (p.grad && p.stretch) {
+                if (p.comp)
+                    launch_sweep<true, true, true>(A, B, seg, st);
+                else
+                    launch_sweep<true, false, true>(A, B, seg, st);
+            } else if (p.grad) {
+                if (p.comp)
+                    launch_sweep<true, true, false>(A, B, seg, st);
+                else
+                    launch_sweep<true, false, false>(A, B, seg, st);
+            } else {
+                if (p.comp)
+                    launch_sweep<false, true, false>(A, B, seg, st);
+                else
+                    launch_sweep<false, false, false>(A, B, seg, st);
+            }
         }
     }
     EpiArgs E;
     E.sk = p.sk;
     E.part = part;
+    E.sks = p.sks;
+    E.part_s = part_s;
     E.n = p.n_tgt;
     E.ncomp = p.ncomp;
     E.comp = p.comp ? 1 : 0;

@@ -428,6 +428,23 @@ def random_segments(seed, m, box=1.0, length=0.1, gamma=1.0):
     return _f32(_pad4(a, g)), _f32(_pad4(b, 0.0))
 
 
+def random_rings(seed, n_rings, box=1.0, size=0.1, gamma=1.0):
+    """Closed four-sided vortex rings as segments (4 per ring, side k from corner k to
+    corner k + 1 mod 4, the ring's circulation on every side; end points shared bit
+    for bit): non-planar random quadrilaterals of about `size` in a cube `box`."""
+    rng = np.random.default_rng(seed)
+    centre = rng.uniform(-0.5 * box, 0.5 * box, size=(n_rings, 1, 3))
+    ang = np.sort(rng.uniform(0.0, 2.0 * np.pi, size=(n_rings, 4)), axis=1)
+    rad = size * rng.uniform(0.3, 0.7, size=(n_rings, 4))
+    c = np.stack([rad * np.cos(ang), rad * np.sin(ang), 0.2 * size * rng.normal(size=(n_rings, 4))], axis=2)
+    rot = np.linalg.qr(rng.normal(size=(n_rings, 3, 3)))[0]
+    corners = _f32(centre + np.einsum("rij,rkj->rki", rot, c))  # [n_rings, 4, 3]
+    g = np.repeat(rng.uniform(-gamma, gamma, size=n_rings), 4)
+    a = corners.reshape(-1, 3)
+    b = np.roll(corners, -1, axis=1).reshape(-1, 3)
+    return _f32(_pad4(a, g)), _f32(_pad4(b, 0.0))
+
+
 def sample_targets(seed, n, k):
     """k distinct target indices out of n, sorted (subsampled parity and oracle timing)."""
     rng = np.random.default_rng(seed + 1000)

@@ -114,6 +114,39 @@ def test_segments_of_zero_length(api):
         _check(u, g, ru, rJ, TOL_COMP)
 
 
+@pytest.mark.parametrize("vn", [1, 2])
+def test_segments_closed_rings(api, vn):
+    """Segment tiles made of closed four-sided rings are packed by corner (each corner
+    shared by two sides).  They must match the oracle for targets far away, inside the
+    core, on the sides, a few core radii from corners and exactly on corners (the
+    end-point guard), including a ring with a zero-length side; and match the same
+    segments taken one by one, which the library sees when the sides of every ring are
+    listed in reverse order (the tile is then not a chain of closed rings).  (Targets
+    much closer to a corner than the core radius lose the gradient to FP32 rounding in
+    either form, 2e-4 at 1e-5 of 0.05-long sides, and are left out.)"""
+    core = 0.02
+    sa, sb = synth.random_rings(7, 50, box=0.6, size=0.12)  # 200 segments: 128 + 72, both tiles closed
+    sb[20, :3] = sa[20, :3]  # ring 5, side 0 of zero length: corners 0 and 1 coincide
+    sa[21, :3] = sa[20, :3]
+    tgt, _ = synth.random_cloud(8, 1100, sigma=0.05)
+    tgt[:8, :3] = sa[:8, :3]  # on corners
+    tgt[8:16, :3] = 0.5 * (sa[8:16, :3] + sb[8:16, :3])  # mid-side
+    tgt[16:24, :3] = sa[16:24, :3] + np.float32(2e-3)  # a few core radii from corners
+    tgt[24:40, :3] = 0.3 * sa[24:40, :3] + 0.7 * sb[24:40, :3] + np.float32(3e-3)  # inside the core
+    tgt[576:, 0] += np.float32(1.5)  # whole warps of targets clear of every tile: the guard-free form
+    ru, rJ = oracle.segments(sa, sb, tgt, core, vn)
+    u, g = api.segments_induce(to_dev(sa), to_dev(sb), to_dev(tgt), core, vn)
+    torch.cuda.synchronize()
+    assert torch.isfinite(u).all() and torch.isfinite(g).all()
+    _check(u, g, ru, rJ, TOL_COMP, f"vn={vn}")
+    rev = np.concatenate([np.arange(4 * r + 3, 4 * r - 1, -1) for r in range(50)])
+    u2, g2 = api.segments_induce(to_dev(sa[rev]), to_dev(sb[rev]), to_dev(tgt), core, vn)
+    torch.cuda.synchronize()
+    for x, y in ((u, u2), (g, g2)):
+        x, y = x.double().cpu().numpy(), y.double().cpu().numpy()
+        assert np.linalg.norm(x - y) <= TOL_COMP * np.linalg.norm(y)
+
+
 @pytest.mark.parametrize("classic", [False, True])
 @pytest.mark.parametrize("compensated", [True, False])
 def test_rhs_config1(api, classic, compensated):
