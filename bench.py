@@ -42,8 +42,8 @@ TOL = {"compensated": 2e-6, "plain": 1e-4, "nu_t": {"compensated": 1e-5, "plain"
 # particle tiles, from one ncu capture of that launch per workload (profiles/sweep_kernel_*.md), keyed by
 # (particles, segments); valid only while the kernel's sources hash to SWEEP_SRC_SHA256,
 # else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = {(2_000_000, 7_680): 156_304_597_000 + 354_574_336}
-SWEEP_SRC_SHA256 = "62f6d7358d3cbd4cd8ffa46bcebdc3f6295c49c5cfde357ba15f135e6d13bf8c"
+SWEEP_TRAFFIC_BYTES = {(2_000_000, 7_680): 147_234_390_000 + 355_699_200}
+SWEEP_SRC_SHA256 = "8801ee600de47980de0a4c41efcbaba7df4051fc2ba0bb539a1eb12e7726c412"
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 
@@ -126,7 +126,7 @@ def run_part(args):
     """One component, repeated --steps times after --warmup: the AIC build + solve of the
     blade lattice, the conversion of 2,000 hover wake rows, the treecode (theta 0.5,
     order 4) on the 1,000,000-particle BVI wake (--particles to shrink it), or the
-    direct right-hand side (vpm_rhs, compensated: one sweep launch, Vreman,
+    direct right-hand side (vpm_rhs, compensated: the particle and segment sweeps, Vreman,
     stretching, PSE) of the --config workload."""
     import torch
 
