@@ -393,10 +393,10 @@ vpm_status vpm_induce_noalloc(const float* src_pos_d, const float* src_str_d, in
  * kind VPM_TRACE_ALL returns the total launch count of every kernel since the
  * last reset (and the summed time of all timed kinds).  Thread-safe. */
 #define VPM_TRACE_ALL 0
-#define VPM_TRACE_SWEEP 1     /* forward particle pair sweep with gradient */
+#define VPM_TRACE_SWEEP 1     /* forward particle pair sweep with gradient (small problems: with the segments) */
 #define VPM_TRACE_ADJOINT 2   /* adjoint pair sweep */
 #define VPM_TRACE_PSE 3       /* particle strength exchange */
-#define VPM_TRACE_SWEEP_VEL 4 /* forward particle pair sweep, velocity only */
+#define VPM_TRACE_SWEEP_VEL 4 /* forward particle pair sweep, velocity only (the same) */
 #define VPM_TRACE_SEGMENTS 5  /* forward segment pair sweep (its own launch; with or without gradient) */
 vpm_status vpm_trace_enable(int timing);
 vpm_status vpm_trace_reset(void);
