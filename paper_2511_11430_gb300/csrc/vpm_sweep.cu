@@ -469,9 +469,13 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= E.n) return;
     const int t = i / TGT_TILE, l = i % TGT_TILE;
-    double acc[17];
+    // The partial sums are folded in FP32 double-float arithmetic (hi by Knuth's
+    // two-sum, the low words added apart: about 48 bits) and converted to FP64 once
+    // per row; the FP64 pipe, a small fraction of the FP32 rate here, keeps only the
+    // per-target algebra below.
+    float H[17], Lw[17];
 #pragma unroll
-    for (int c = 0; c < 17; ++c) acc[c] = 0.0;
+    for (int c = 0; c < 17; ++c) H[c] = 0.f, Lw[c] = 0.f;
     // the partial sums of the particle launch, then those of the segment launch
     for (int launch = 0; launch < 2; ++launch) {
         const StreamK& sk = launch ? E.sks : E.sk;
@@ -489,15 +493,20 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
             if (tt != t || sk.unit_start(tt, kk) >= hi_b) continue;  // block b ran no unit of tile t
             const float* P = part + (size_t)(b + t) * rows * TGT_TILE + l;
 #pragma unroll
-            for (int c = 0; c < 17; ++c) {  // a constant bound keeps acc in registers
+            for (int c = 0; c < 17; ++c) {  // a constant bound keeps the sums in registers
                 if (c < E.ncomp) {
-                    double v = (double)P[(size_t)c * TGT_TILE];
-                    if (E.comp) v += (double)P[(size_t)(E.ncomp + c) * TGT_TILE];
-                    acc[c] += v;
+                    float sum, err;
+                    two_sum(H[c], P[(size_t)c * TGT_TILE], sum, err);
+                    H[c] = sum;
+                    Lw[c] = __fadd_rn(Lw[c], err);
+                    if (E.comp) Lw[c] = __fadd_rn(Lw[c], P[(size_t)(E.ncomp + c) * TGT_TILE]);
                 }
             }
         }
     }
+    double acc[17];
+#pragma unroll
+    for (int c = 0; c < 17; ++c) acc[c] = (double)H[c] + (double)Lw[c];
     const double f4pi = 0.079577471545947667884;  // 1/(4 pi)
     const EpilogueOut& o = E.o;
     const double u0 = acc[0] * f4pi, u1 = acc[1] * f4pi, u2 = acc[2] * f4pi;
@@ -531,19 +540,15 @@ __global__ void __launch_bounds__(256) epilogue_kernel(const EpiArgs E)
     // Right-hand side of Eq. 4-5 for particle i.
     const float4 G4 = reinterpret_cast<const float4*>(o.str)[i];
     const double Gm[3] = {G4.x, G4.y, G4.z};
-    // Vreman: alpha = J^T, beta = Delta^2 J J^T, Delta = sigma
-    double bt[3][3];
-    double aa = 0.0;
-    for (int p = 0; p < 3; ++p)
-        for (int q = 0; q < 3; ++q) {
-            double s = 0.0;
-            for (int m = 0; m < 3; ++m) s += J[3 * p + m] * J[3 * q + m];
-            bt[p][q] = s * (double)o.sigma * (double)o.sigma;
-        }
-    for (int c = 0; c < 9; ++c) aa += J[c] * J[c];
-    const double B = bt[0][0] * bt[1][1] - bt[0][1] * bt[0][1] + bt[0][0] * bt[2][2] - bt[0][2] * bt[0][2] +
-                     bt[1][1] * bt[2][2] - bt[1][2] * bt[1][2];
-    const double nut = (aa > 0.0 && B > 0.0) ? (double)o.c_v * sqrt(B / aa) : 0.0;
+    // Vreman: alpha = J^T, beta = Delta^2 g with g = J J^T (symmetric), Delta = sigma, so
+    // B_beta = Delta^4 B_g and alpha:alpha = trace g: nu_t = c_V Delta^2 sqrt(B_g / trace g).
+    auto dot3 = [&](int p, int q) { return J[3 * p] * J[3 * q] + J[3 * p + 1] * J[3 * q + 1] + J[3 * p + 2] * J[3 * q + 2]; };
+    const double g00 = dot3(0, 0), g11 = dot3(1, 1), g22 = dot3(2, 2);
+    const double g01 = dot3(0, 1), g02 = dot3(0, 2), g12 = dot3(1, 2);
+    const double aa = g00 + g11 + g22;
+    const double B = g00 * g11 - g01 * g01 + g00 * g22 - g02 * g02 + g11 * g22 - g12 * g12;
+    const double nut =
+        (aa > 0.0 && B > 0.0) ? (double)o.c_v * ((double)o.sigma * (double)o.sigma) * sqrt(B / aa) : 0.0;
     double s[3];
     if (E.ncomp == 17) {  // transposed stretching accumulated per target
         s[0] = acc[14] * f4pi;
