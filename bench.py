@@ -42,8 +42,8 @@ TOL = {"compensated": 2e-6, "plain": 1e-4, "nu_t": {"compensated": 1e-5, "plain"
 # particle tiles, from one ncu capture of that launch per workload (profiles/sweep_kernel_*.md), keyed by
 # (particles, segments); valid only while the kernel's sources hash to SWEEP_SRC_SHA256,
 # else the bench reports traffic null.
-SWEEP_TRAFFIC_BYTES = {(2_000_000, 7_680): 147_234_390_000 + 355_699_200}
-SWEEP_SRC_SHA256 = "8801ee600de47980de0a4c41efcbaba7df4051fc2ba0bb539a1eb12e7726c412"
+SWEEP_TRAFFIC_BYTES = {(2_000_000, 7_680): 142_549_244_000 + 355_496_960}
+SWEEP_SRC_SHA256 = "554c12209b1a3bebcca23b4f0ce95552fb9362a866002d2d20a1288ac8c463fe"
 SWEEP_SRC = ["paper_2511_11430_gb300/csrc/vpm_sweep.cu", "paper_2511_11430_gb300/csrc/vpm_kernel.cuh",
              "paper_2511_11430_gb300/csrc/vpm_common.cuh"]
 

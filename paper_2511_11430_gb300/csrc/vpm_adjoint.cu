@@ -262,9 +262,10 @@ __global__ void __launch_bounds__(256) adjoint_epilogue_kernel(const AdjEpiArgs 
     if (i >= E.n) return;
     const StreamK& sk = E.sk;
     const int t = i / ADJ_TILE, l = i % ADJ_TILE;
-    double acc[A_NC];
+    // partial sums folded in FP32 double-float (two-sum), converted to FP64 once per row
+    float H[A_NC], Lw[A_NC];
 #pragma unroll
-    for (int c = 0; c < A_NC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < A_NC; ++c) H[c] = 0.f, Lw[c] = 0.f;
     if (sk.np > 0) {
         const int b0 = sk.block_of(sk.unit_start(t, 0));
         const int b1 = sk.block_of(sk.unit_start(t, sk.np - 1));
@@ -278,12 +279,17 @@ __global__ void __launch_bounds__(256) adjoint_epilogue_kernel(const AdjEpiArgs 
             const float* P = E.part + (size_t)(b + t) * rows * ADJ_TILE + l;
 #pragma unroll
             for (int c = 0; c < A_NC; ++c) {
-                double v = (double)P[(size_t)c * ADJ_TILE];
-                if (E.comp) v += (double)P[(size_t)(A_NC + c) * ADJ_TILE];
-                acc[c] += v;
+                float sum, err;
+                two_sum(H[c], P[(size_t)c * ADJ_TILE], sum, err);
+                H[c] = sum;
+                Lw[c] = __fadd_rn(Lw[c], err);
+                if (E.comp) Lw[c] = __fadd_rn(Lw[c], P[(size_t)(A_NC + c) * ADJ_TILE]);
             }
         }
     }
+    double acc[A_NC];
+#pragma unroll
+    for (int c = 0; c < A_NC; ++c) acc[c] = (double)H[c] + (double)Lw[c];
     const double f4pi = 0.079577471545947667884;
     const float4 g = E.str[i];
     const double Gx = g.x, Gy = g.y, Gz = g.z;
