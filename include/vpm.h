@@ -241,11 +241,16 @@ vpm_status aic_build(const float* rings_d, const float* colloc_d, const float* n
                      int vatistas_n, const float* v_rel_d, const float* w_ind_d, float* A_d, double* b_d,
                      void* stream);
 
-/* Solves A x = b with A factored once in FP32 (partial pivoting) and iterative
- * refinement whose residual r = b - A x is formed in FP64 from the FP32 matrix.
- * Stops when the normwise backward error ||b - A x||_inf / (||A||_inf ||x||_inf +
- * ||b||_inf) <= tol, or after max_iter corrections (then VPM_ERR_NOT_CONVERGED with
- * the best x written).  Synchronises `stream` once per refinement step.
+/* Solves A x = b with A factored once in FP32 and iterative refinement whose residual
+ * r = b - A x is formed in FP64 from the FP32 matrix.  The factorisation runs without
+ * row exchanges first (for a matrix strictly diagonally dominant by rows, such as the
+ * blade systems, elimination keeps every pivot nonzero and the growth at most 2); the
+ * dominance test (FP64 row sums) is read with the first residual, and any other matrix
+ * is then factored again with partial pivoting.  Stops when the normwise backward error
+ * ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol, or after max_iter
+ * corrections (then VPM_ERR_NOT_CONVERGED with the best x written); a zero pivot of the
+ * pivoted factorisation also returns VPM_ERR_NOT_CONVERGED.  Synchronises `stream` once
+ * per refinement step (once more for a matrix that is not row-dominant).
  *   A_d [n][n] float row-major (not modified); b_d, x_d [n] double;
  *   iters_out, berr_out host pointers or NULL. */
 vpm_status aic_solve(const float* A_d, const double* b_d, double* x_d, int n, double tol, int max_iter,
