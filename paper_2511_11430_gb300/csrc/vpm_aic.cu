@@ -539,14 +539,20 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
 // thread per column) in parallel over the whole panel; lu_update_kernel follows.
 // ---------------------------------------------------------------------------
 
-// flag |= 1 when some row is not strictly diagonally dominant (one warp per row, FP64 sums).
-__global__ void __launch_bounds__(256) lu_dominance_kernel(const float* __restrict__ A, int n, int* __restrict__ flag)
+// LU = A, and flag |= 1 when some row is not strictly diagonally dominant (one warp
+// per row, FP64 sums): the copy the factorisation works on and the test in one pass.
+__global__ void __launch_bounds__(256) lu_dominance_kernel(const float* __restrict__ A, int n,
+                                                           float* __restrict__ LU, int* __restrict__ flag)
 {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     double s = 0.0;
-    for (int c = lane; c < n; c += 32) s += fabs((double)A[(size_t)i * n + c]);
+    for (int c = lane; c < n; c += 32) {
+        const float a = A[(size_t)i * n + c];
+        LU[(size_t)i * n + c] = a;
+        s += fabs((double)a);
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const double d = fabs((double)A[(size_t)i * n + i]);
@@ -608,7 +614,8 @@ __global__ void __launch_bounds__(NP_THREADS) lu_np_panel_kernel(float* __restri
         for (int c = 0; c < NB; ++c) v[c] = D[lane][c];
 #pragma unroll
         for (int j = 0; j < NB - 1; ++j) {
-            const float l = v[j] / __shfl_sync(0xffffffffu, v[j], j);
+            // one correctly rounded reciprocal of the pivot per step instead of a division
+            const float l = v[j] * __frcp_rn(__shfl_sync(0xffffffffu, v[j], j));
 #pragma unroll
             for (int c = j + 1; c < NB; ++c) {
                 const float u = __shfl_sync(0xffffffffu, v[c], j);  // the pivot row's entry
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__(NP_THREADS) lu_np_panel_kernel(float* __restri
         }
 #pragma unroll
         for (int c = 0; c < NB; ++c) D[lane][c] = v[c];
-        Rinv[lane] = 1.0f / D[lane][lane];  // this lane's own diagonal entry
+        Rinv[lane] = __frcp_rn(D[lane][lane]);  // this lane's own diagonal entry
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
@@ -642,11 +649,11 @@ __global__ void __launch_bounds__(NP_THREADS) lu_np_panel_kernel(float* __restri
         if (tid < rows) {
             float x[NB];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                float v = W[tid][j];
+            for (int j = 0; j < NB; ++j) {  // four interleaved partial sums: shorter chains
+                float v[4] = {W[tid][j], 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int p = 0; p < j; ++p) v = fmaf(-x[p], D[p][j], v);
-                x[j] = v * Rinv[j];
+                for (int p = 0; p < j; ++p) v[p & 3] = fmaf(-x[p], D[p][j], v[p & 3]);
+                x[j] = ((v[0] + v[1]) + (v[2] + v[3])) * Rinv[j];
             }
 #pragma unroll
             for (int j = 0; j < NB; ++j) W[tid][j] = x[j];
@@ -658,9 +665,12 @@ __global__ void __launch_bounds__(NP_THREADS) lu_np_panel_kernel(float* __restri
         }
     } else if (col_ok) {  // columns of U12: y = L11^-1 a (unit lower), coalesced across the threads
 #pragma unroll
-        for (int i = 1; i < NB; ++i)
+        for (int i = 1; i < NB; ++i) {
+            float v[4] = {y[i], 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int p = 0; p < i; ++p) y[i] = fmaf(-D[i][p], y[p], y[i]);
+            for (int p = 0; p < i; ++p) v[p & 3] = fmaf(-D[i][p], y[p], v[p & 3]);
+            y[i] = (v[0] + v[1]) + (v[2] + v[3]);
+        }
 #pragma unroll
         for (int i = 0; i < NB; ++i)
             if (i < nb) A[(size_t)(k0 + i) * n + col] = y[i];
@@ -987,7 +997,6 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
             return VPM_ERR_CUDA;                           \
         }                                                  \
     } while (0)
-    VPM_CU(cudaMemcpyAsync(LU, A, (size_t)n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
     VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)PANEL_SMEM_MAX));
     VPM_CU(cudaFuncSetAttribute(lu_panel_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1080,7 +1089,7 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     };
     VPM_CU(cudaMemsetAsync(dflag, 0, sizeof(int), st));
     trace_launch();
-    lu_dominance_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, n, dflag);
+    lu_dominance_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, n, LU, dflag);
     VPM_CU(factor(false));
     bool pivoted = false;
     double h[6];
