@@ -97,7 +97,8 @@ typedef struct vpm_params {
 /* Message of the last error returned on the calling host thread ("" if none). */
 const char* vpm_last_error(void);
 
-/* ABI version (major * 10000 + minor * 100 + patch). */
+/* ABI version (major * 10000 + minor * 100 + patch).  1.1: vpm_rk3_stage,
+ * VPM_OP_STAGE and the segment trace kind VPM_TRACE_SEGMENTS. */
 int vpm_version(void);
 
 /* Reads and clears the device error word of the current device (synchronises the

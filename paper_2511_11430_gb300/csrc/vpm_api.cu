@@ -135,7 +135,7 @@ extern "C" {
 
 const char* vpm_last_error(void) { return g_last_error.c_str(); }
 
-int vpm_version(void) { return 10000; }
+int vpm_version(void) { return 10100; }
 
 vpm_status vpm_device_error(int* code)
 {

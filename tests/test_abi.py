@@ -47,7 +47,7 @@ def test_binding_signatures_cover_header(lib):
 def test_version_and_invalid_arguments_without_gpu(lib):
     from paper_2511_11430_gb300 import _lib
 
-    assert lib.vpm_version() == 10000
+    assert lib.vpm_version() == 10100
     # sigma <= 0 is rejected before anything touches the device
     st = lib.vpm_induce(None, None, 10, None, 10, ctypes.c_float(-1.0), 0, None, None, None, 0, None)
     assert st == _lib.VPM_ERR_INVALID_ARG
