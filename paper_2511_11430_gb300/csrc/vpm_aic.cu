@@ -471,6 +471,16 @@ __global__ void __launch_bounds__(ROWS_THREADS, 4) lu_rows_kernel(float* __restr
         if (i < nb) A[(size_t)(k0 + i) * n + c] = x[i];
 }
 
+// The row-dominant LU's panel and update kernels are launched as programmatic dependents
+// of the kernel before them: each lets the next one be scheduled at once and waits,
+// before touching the matrix, until the previous grid has completed and its writes
+// are visible (griddepcontrol; without the launch attribute both are no-ops).
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // A22 -= L21 U12 over rows [k0+nb, n) and columns [cb, ce): 64x64 output tile per
 // block, 4x4 per thread.
 __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, int n, int k0, int nb, int cb, int ce,
@@ -478,6 +488,7 @@ __global__ void __launch_bounds__(256) lu_update_kernel(float* __restrict__ A, i
 {
     __shared__ float Ls[64][NB + 1];
     __shared__ float Us[NB][64 + 1];
+    pdl_enter();
     if (dsrc && blockIdx.x == 0 && blockIdx.y == 0)  // the panel's factored diagonal block, into place
         for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
             const int i = e / nb, c = e - i * nb;
@@ -576,6 +587,7 @@ __global__ void __launch_bounds__(NP_THREADS) lu_np_panel_kernel(float* __restri
     __shared__ float D[NB][NB + 1];
     __shared__ float Rinv[NB];
     __shared__ float W[NP_THREADS][NB + 1];
+    pdl_enter();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool head = blockIdx.x == 0 && blockIdx.y == 0;
     if (head && k0 == 0) {
@@ -683,6 +695,7 @@ __global__ void __launch_bounds__(256) lu_transpose_kernel(const float* __restri
                                                            int n)
 {
     __shared__ float t[32][33];
+    pdl_enter();
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int r = by + k, c = bx + threadIdx.x;
@@ -727,6 +740,7 @@ __global__ void __launch_bounds__(SB) lu_diag_inv_kernel(const float* __restrict
     __shared__ float M[SB][SB + 1];
     __shared__ float Iv[2][32][33];  // inverses of the two diagonal sub-blocks
     __shared__ float Tm[32][33];
+    pdl_enter();
     const int k = blockIdx.x, w = blockIdx.y, tid = threadIdx.x, nblk = gridDim.x;
     const int lane = tid & 31, h = tid >> 5;
     const int b0 = SB * k, nb = min(SB, n - b0);
@@ -805,8 +819,10 @@ __global__ void __launch_bounds__(SB) lu_diag_inv_kernel(const float* __restrict
 __global__ void __cluster_dims__(SOLVE_CL, 1, 1) __launch_bounds__(SOLVE_T)
     lu_solve_cluster_kernel(const float* __restrict__ T, const float* __restrict__ Dinv,
                             const int* __restrict__ perm, int n, const double* __restrict__ rhs,
-                            double* __restrict__ out, int accumulate)
+                            double* __restrict__ out, int accumulate, double* __restrict__ norms)
 {
+    pdl_enter();
+    if (norms && blockIdx.x == 0 && threadIdx.x < 4) norms[threadIdx.x] = 0.0;  // for the residual that follows
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) float y[];  // n entries and SB zeros
     cg::cluster_group cl = cg::this_cluster();
@@ -892,13 +908,15 @@ __global__ void __cluster_dims__(SOLVE_CL, 1, 1) __launch_bounds__(SOLVE_T)
 // maxima of |r_i| (+inf where r_i or x_i is not finite), |x_i|, |b_i| and the row sums
 // are folded into out[0..3], zeroed before the launch, by atomic max on their bit
 // patterns (non-negative doubles order as their unsigned 64-bit patterns); out[4] and
-// out[5] receive the zero-pivot status and the dominance flag.
+// out[5] receive the zero-pivot status and the dominance flag.  (The solve before it
+// zeroes out[0..3].)
 __global__ void __launch_bounds__(256) residual_kernel(const float* __restrict__ A, const double* __restrict__ b,
                                                        const double* __restrict__ x, int n, double* __restrict__ r,
                                                        double* __restrict__ rowabs, int first,
                                                        const int* __restrict__ info, double* __restrict__ out)
 {
     __shared__ double red[4][8];
+    pdl_enter();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     double m[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1048,20 +1066,39 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     // residual: any other matrix is then factored again with partial pivoting.  The
     // zero-pivot status is read at the same synchronisation.
     int* dflag = info + 1;
+    // Kernels after the first are launched as programmatic dependents (pdl_enter).
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    auto cfg = [&](dim3 g, dim3 b, size_t smem = 0) {
+        cudaLaunchConfig_t c = {};
+        c.gridDim = g;
+        c.blockDim = b;
+        c.dynamicSmemBytes = smem;
+        c.stream = st;
+        c.attrs = pdl;
+        c.numAttrs = 1;
+        return c;
+    };
     auto factor = [&](bool pivot) -> cudaError_t {
         for (int k0 = 0; !pivot && k0 < n; k0 += NB) {
             const int nb = n - k0 < NB ? n - k0 : NB;
             const int rest = n - k0 - nb;
             trace_launch();
-            if (rest > 0)
-                lu_np_panel_kernel<<<dim3((rest + NP_THREADS - 1) / NP_THREADS, 2), NP_THREADS, 0, st>>>(
-                    LU, n, k0, nb, info, perm, dblk);
-            else
-                lu_np_panel_kernel<<<dim3(1, 1), NP_THREADS, 0, st>>>(LU, n, k0, nb, info, perm, nullptr);
+            cudaError_t e;
+            if (rest > 0) {
+                const cudaLaunchConfig_t c = cfg(dim3((rest + NP_THREADS - 1) / NP_THREADS, 2), dim3(NP_THREADS));
+                e = cudaLaunchKernelEx(&c, lu_np_panel_kernel, LU, n, k0, nb, info, perm, dblk);
+            } else {
+                const cudaLaunchConfig_t c = cfg(dim3(1, 1), dim3(NP_THREADS));
+                e = cudaLaunchKernelEx(&c, lu_np_panel_kernel, LU, n, k0, nb, info, perm, (float*)nullptr);
+            }
+            if (e != cudaSuccess) return e;
             if (rest > 0) {
                 trace_launch();
-                lu_update_kernel<<<dim3((rest + 63) / 64, (rest + 63) / 64), 256, 0, st>>>(LU, n, k0, nb, k0 + nb,
-                                                                                           n, dblk);
+                const cudaLaunchConfig_t c = cfg(dim3((rest + 63) / 64, (rest + 63) / 64), dim3(256));
+                e = cudaLaunchKernelEx(&c, lu_update_kernel, LU, n, k0, nb, k0 + nb, n, (const float*)dblk);
+                if (e != cudaSuccess) return e;
             }
         }
         for (int k0 = 0; pivot && k0 < n; k0 += NB) {
@@ -1079,13 +1116,22 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
                                                                                            n, nullptr);
             }
         }
-        trace_launch();
-        lu_transpose_kernel<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(LU, T, n);
-        trace_launch();
-        lu_diag_inv_kernel<<<dim3((n + SB - 1) / SB, 2), SB, 0, st>>>(LU, n, dinv);
-        trace_launch();
-        lu_solve_cluster_kernel<<<SOLVE_CL, SOLVE_T, solve_smem, st>>>(T, dinv, perm, n, b, x, 0);
-        return cudaGetLastError();
+        trace_launch(3);
+        cudaError_t e;
+        {
+            const cudaLaunchConfig_t c = cfg(dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 8));
+            if ((e = cudaLaunchKernelEx(&c, lu_transpose_kernel, (const float*)LU, T, n)) != cudaSuccess) return e;
+        }
+        {
+            const cudaLaunchConfig_t c = cfg(dim3((n + SB - 1) / SB, 2), dim3(SB));
+            if ((e = cudaLaunchKernelEx(&c, lu_diag_inv_kernel, (const float*)LU, n, dinv)) != cudaSuccess) return e;
+        }
+        {
+            const cudaLaunchConfig_t c = cfg(dim3(SOLVE_CL), dim3(SOLVE_T), solve_smem);
+            e = cudaLaunchKernelEx(&c, lu_solve_cluster_kernel, (const float*)T, (const float*)dinv, (const int*)perm,
+                                   n, b, x, 0, norms);
+        }
+        return e != cudaSuccess ? e : cudaGetLastError();
     };
     VPM_CU(cudaMemsetAsync(dflag, 0, sizeof(int), st));
     trace_launch();
@@ -1095,9 +1141,12 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
     double h[6];
     double best = INFINITY;
     for (int it = 0;; ++it) {
-        VPM_CU(cudaMemsetAsync(norms, 0, 4 * sizeof(double), st));
         trace_launch();
-        residual_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(A, b, x, n, r, rowabs, it == 0, info, norms);
+        {
+            const cudaLaunchConfig_t c = cfg(dim3((n * 32 + 255) / 256), dim3(256));
+            VPM_CU(cudaLaunchKernelEx(&c, residual_kernel, A, (const double*)b, (const double*)x, n, r, rowabs,
+                                      it == 0 ? 1 : 0, (const int*)info, norms));
+        }
         VPM_CU(cudaGetLastError());
         VPM_CU(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, st));
         VPM_CU(cudaStreamSynchronize(st));
@@ -1132,7 +1181,11 @@ vpm_status run_aic_solve(const float* A, const double* b, double* x, int n, doub
             return VPM_ERR_NOT_CONVERGED;
         }
         trace_launch();
-        lu_solve_cluster_kernel<<<SOLVE_CL, SOLVE_T, solve_smem, st>>>(T, dinv, perm, n, r, x, 1);
+        {
+            const cudaLaunchConfig_t c = cfg(dim3(SOLVE_CL), dim3(SOLVE_T), solve_smem);
+            VPM_CU(cudaLaunchKernelEx(&c, lu_solve_cluster_kernel, (const float*)T, (const float*)dinv,
+                                      (const int*)perm, n, (const double*)r, x, 1, norms));
+        }
     }
 #undef VPM_CU
 }
